@@ -1,0 +1,148 @@
+"""Method-of-lines problems y' = f^S(y) + f^N(y) with linear stiff part f^S = D y (Section II, eq. (ode)).
+
+Each problem gives, in plain FP64 numpy:
+  fN(y)         the explicit (non-stiff) term f^N,
+  D(y)          the stiff term f^S(y) = D y, with D = nu * L per species (centred
+                second differences, as in Section IV),
+  solve(r, dt)  the exact solution y of (I - dt D) y = r  (eq. (imex_diffusion)).
+
+Grids and boundary ghosts (the paper treats 1D periodic and 1D Dirichlet problems; the
+2D cell-centred conventions are readings):
+  * 1D periodic: x_i = i h, h = 1/N, neighbours wrap around.
+  * 2D Neumann:  cell centres (i + 1/2) h, even ghost u_{-1} = u_0, u_N = u_{N-1}.
+  * 2D Dirichlet: cell centres, odd ghost u_{-1} = -u_0, u_N = -u_{N-1} (zero on the wall).
+Arrays are [x] in 1D and [species][y][x] in 2D.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft
+import scipy.linalg
+
+
+class AdvDiff1DPeriodic:
+    """u_t + a u_x = nu u_xx on periodic [0,1): f^N = -a (u_{i+1} - u_{i-1}) / (2h), D = nu L."""
+
+    def __init__(self, n: int, a: float, nu: float):
+        self.n, self.a, self.nu = n, float(a), float(nu)
+        self.h = 1.0 / n
+        self._lu: dict[float, tuple] = {}
+
+    def fN(self, u: np.ndarray) -> np.ndarray:
+        return -self.a * (np.roll(u, -1) - np.roll(u, 1)) / (2.0 * self.h)
+
+    def D(self, u: np.ndarray) -> np.ndarray:
+        return self.nu * (np.roll(u, -1) - 2.0 * u + np.roll(u, 1)) / self.h ** 2
+
+    def matrix_D(self) -> np.ndarray:
+        n = self.n
+        L = np.zeros((n, n))
+        for i in range(n):
+            L[i, i] = -2.0
+            L[i, (i + 1) % n] += 1.0
+            L[i, (i - 1) % n] += 1.0
+        return self.nu * L / self.h ** 2
+
+    def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
+        # dense LU with partial pivoting of the circulant I - dt D, factored once per dt
+        if dt not in self._lu:
+            self._lu[dt] = scipy.linalg.lu_factor(np.eye(self.n) - dt * self.matrix_D())
+        return scipy.linalg.lu_solve(self._lu[dt], r)
+
+
+def _pad(u: np.ndarray, odd: bool) -> np.ndarray:
+    """Pad the last two axes by one ghost cell: even (Neumann) or odd (Dirichlet) reflection."""
+    p = np.pad(u, [(0, 0)] * (u.ndim - 2) + [(1, 1), (1, 1)], mode="edge")
+    if odd:
+        p[..., 0, :] *= -1.0
+        p[..., -1, :] *= -1.0
+        p[..., :, 0] *= -1.0
+        p[..., :, -1] *= -1.0
+    return p
+
+
+def _lap2d(u: np.ndarray, h: float, odd: bool) -> np.ndarray:
+    p = _pad(u, odd)
+    return (p[..., 2:, 1:-1] + p[..., :-2, 1:-1] + p[..., 1:-1, 2:] + p[..., 1:-1, :-2]
+            - 4.0 * u) / h ** 2
+
+
+def _eig_neumann(n: int, h: float) -> np.ndarray:
+    """Eigenvalues of the 1D Neumann cell-centred Laplacian, cosine modes k = 0..n-1."""
+    k = np.arange(n)
+    return -(4.0 / h ** 2) * np.sin(np.pi * k / (2 * n)) ** 2
+
+
+def _eig_dirichlet(n: int, h: float) -> np.ndarray:
+    """Eigenvalues of the 1D Dirichlet cell-centred Laplacian, sine modes k = 1..n."""
+    k = np.arange(1, n + 1)
+    return -(4.0 / h ** 2) * np.sin(np.pi * k / (2 * n)) ** 2
+
+
+class _Separable2D:
+    """Shared pieces of the two 2D problems: D = nu_s L with L the 5-point Laplacian."""
+    odd = False
+
+    def __init__(self, n: int, nu):
+        self.n = n
+        self.nu = np.asarray(nu, dtype=np.float64)
+        self.h = 1.0 / n
+        lam = _eig_dirichlet(n, self.h) if self.odd else _eig_neumann(n, self.h)
+        self._lam2 = lam[:, None] + lam[None, :]          # [ky][kx]
+
+    def D(self, y: np.ndarray) -> np.ndarray:
+        return self.nu[:, None, None] * _lap2d(y, self.h, self.odd)
+
+    def _fwd(self, y):
+        f = scipy.fft.dstn if self.odd else scipy.fft.dctn
+        return f(y, type=2, norm="ortho", axes=(-2, -1))
+
+    def _inv(self, y):
+        f = scipy.fft.idstn if self.odd else scipy.fft.idctn
+        return f(y, type=2, norm="ortho", axes=(-2, -1))
+
+    def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
+        # (I - dt nu_s L) is diagonal in the orthonormal cosine (Neumann) or sine
+        # (Dirichlet) basis of type II: divide each mode by 1 - dt nu_s (lam_ky + lam_kx).
+        den = 1.0 - dt * self.nu[:, None, None] * self._lam2[None]
+        return self._inv(self._fwd(r) / den)
+
+
+class GrayScott2DNeumann(_Separable2D):
+    """u_t = Du lap u - u v^2 + F (1 - u),  v_t = Dv lap v + u v^2 - (F + k) v, zero-flux walls."""
+    odd = False
+
+    def __init__(self, n: int, Du: float, Dv: float, F: float, k: float):
+        super().__init__(n, (Du, Dv))
+        self.F, self.k = float(F), float(k)
+
+    def fN(self, y: np.ndarray) -> np.ndarray:
+        u, v = y[0], y[1]
+        uvv = u * v * v
+        return np.stack([-uvv + self.F * (1.0 - u), uvv - (self.F + self.k) * v])
+
+
+class AdvDiff2DDirichlet(_Separable2D):
+    """u_t + a u_x + b u_y = nu lap u, u = 0 on the walls; central advection differences."""
+    odd = True
+
+    def __init__(self, n: int, a: float, b: float, nu: float):
+        super().__init__(n, (nu,))
+        self.a, self.b = float(a), float(b)
+
+    def fN(self, y: np.ndarray) -> np.ndarray:
+        p = _pad(y, odd=True)
+        ux = (p[..., 1:-1, 2:] - p[..., 1:-1, :-2]) / (2.0 * self.h)
+        uy = (p[..., 2:, 1:-1] - p[..., :-2, 1:-1]) / (2.0 * self.h)
+        return -self.a * ux - self.b * uy
+
+
+def from_workload(w) -> object:
+    """Build the oracle problem for an inputs.Workload."""
+    if w.kind == "adv_diff_1d_periodic":
+        return AdvDiff1DPeriodic(w.n, w.a, w.nu[0])
+    if w.kind == "gray_scott_2d_neumann":
+        return GrayScott2DNeumann(w.n, w.nu[0], w.nu[1], w.F, w.k)
+    if w.kind == "adv_diff_2d_dirichlet":
+        return AdvDiff2DDirichlet(w.n, w.a, w.b, w.nu[0])
+    raise KeyError(w.kind)
