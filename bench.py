@@ -1,0 +1,312 @@
+"""Benchmark: RIDC-4 on 2048x2048 Gray-Scott, mixed BF16x3 solves, cell-updates per second.
+
+One bench step is one whole integration: every level is reset to the initial field and the
+pipeline advances until the most corrected level has taken 1000 steps of dt = 0.5 (start-up
+and drain included), i.e. 2048^2 * 1000 cell-updates. `value` times that on the device with
+inputs resident in HBM; `e2e` times the same through the C ABI with host buffers (initial
+field copied in, solution copied out inside the timed region).
+
+Also reported: the dominant kernel's roofline (CUDA events around every launch inside the
+timed region), the FP64 GPU form of the same workload on a truncated run together with the
+mixed path's relative L2 difference to it, SM clocks sampled during the timed region, and the
+CPU oracle on a bounded sample of the workload (reference arm: --impl reference).
+
+Multi-GPU (torchrun): the integration does not shard; every rank runs an independent replica
+and `value` sums the ranks' cell-updates over the slowest rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RIDC-4 cell-updates/s, 2048² Gray-Scott: mixed vs FP64 GPU at <=1e-8 rel L2"
+UNIT = "cell-updates/s"
+N, NT, ORDER, NREF = 2048, 1000, 4, 2
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while active."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[4:]))
+            except ValueError:
+                continue
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3][1:5])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows), "samples": len(loaded),
+                "power_w_max": max(r[2] for r in rows), "reasons": reasons}
+
+
+def cpu_baseline(steps: int = 6):
+    """The FP64 oracle (sequential classic-IDC order, numpy/scipy) on 2048^2 Gray-Scott."""
+    import inputs
+    import oracle
+    w = inputs.gray_scott_2d(n=N, nsteps=steps)
+    prob = oracle.from_workload(w)
+    t0 = time.perf_counter()
+    oracle.ridc_sequential(prob, w.u0, w.dt, steps, ORDER)
+    dt = time.perf_counter() - t0
+    return {"value": N * N * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RIDC-4 steps of the 2048^2 Gray-Scott workload "
+                      f"({dt:.1f} s, numpy/scipy FP64, single thread)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.ref_steps)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.ref_steps))
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * N * N * args.ref_steps / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "gray_scott_2048_ridc4", "grid": N, "order": ORDER,
+                       "steps_per_sample": args.ref_steps, "dt": 0.5},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nt", type=int, default=NT, help="top-level steps per integration")
+    ap.add_argument("--ref-steps", type=int, default=6)
+    ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import inputs
+    from paper_1209_4297_gb300 import Integrator
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    w = inputs.gray_scott_2d(n=N, nsteps=args.nt)
+    u0_dev = torch.from_numpy(w.u0).cuda()
+    u0_host = torch.from_numpy(w.u0).pin_memory()
+    out_host = torch.empty_like(u0_host).pin_memory()
+    it = Integrator.from_workload(w, precision="mixed_bf16x3", n_refine=NREF,
+                                  stream=stream.cuda_stream)
+
+    def one_run():
+        it.set_initial(u0_dev)
+        it.advance(args.nt)
+
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs --------------------------------------------
+    it.set_profiling(True)
+    launches0 = it.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one_run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = it.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    stats = {k: it.kernel_stats(k) for k in ("rhs", "gemm_tc", "residual", "finalize")}
+    it.set_profiling(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    cells = float(N * N * args.nt)
+    value = ws * cells * args.steps / (ms_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers ----------------------------------
+    e2e_runs = max(1, min(args.steps, 2))
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_runs):
+        it.set_initial(u0_host.numpy())
+        it.advance(args.nt)
+        it.solution(out_host.numpy())
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = ws * cells * e2e_runs / float(te.item())
+    mixed_final = out_host.numpy().copy()
+
+    # ---- FP64 GPU form on a truncated run; accuracy of the mixed path against it ---------
+    fp64 = None
+    if rank == 0 and args.fp64_steps > 0:
+        k = args.fp64_steps
+        with Integrator.from_workload(w, precision="fp64", stream=stream.cuda_stream) as it64:
+            it64.set_initial(u0_dev)
+            it64.advance(2)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            it64.advance(k - 2)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ref64 = it64.solution()
+            fp64_rate = N * N * (k - 2) / (a0.elapsed_time(a1) * 1e-3)
+        it.set_initial(u0_dev)
+        it.advance(k)
+        mix = it.solution()
+        rel = float(np.linalg.norm(mix - ref64) / np.linalg.norm(ref64))
+        fp64 = {"value": fp64_rate, "unit": UNIT, "sample": f"steps 3..{k} of the same run "
+                f"(steady pipeline), FP64 DFMA fast-diagonalisation GEMMs",
+                "mixed_rel_l2_vs_fp64": rel, "at_step": k}
+    it.close()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = _peaks()
+    # dominant kernel: the split-precision GEMM (see the design doc for the per-launch figures)
+    n_tc, ms_tc = stats["gemm_tc"]
+    planes_full = ORDER * 2
+    # every launch contracts (planes x N) x N by N with 3 BF16 products; average the planes
+    # over the launches actually made (start-up and drain steps run fewer levels)
+    total_gemm_flops = 0.0
+    # count launches per plane count from the schedule
+    from paper_1209_4297_gb300 import schedule_plan
+    masks = schedule_plan(ORDER, args.nt)
+    for m in masks:
+        planes = 2 * bin(int(m)).count("1")
+        total_gemm_flops += 4 * (NREF + 1) * 3 * 2.0 * planes * N * N * N
+    total_gemm_flops *= args.steps
+    achieved_tf = total_gemm_flops / (ms_tc * 1e-3) / 1e12 if ms_tc > 0 else None
+    peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    roof = {"bound": "tensor", "kernel": "gemm_tc_kernel (BF16x3 tcgen05 fast-diagonalisation)",
+            "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": (achieved_tf / peak_tf) if achieved_tf else None,
+            "peak_source": f"{peak_src} bf16_tflops_sustained",
+            "flops_per_launch_full": 3 * 2.0 * planes_full * N ** 3,
+            "useful_tflops": achieved_tf / 3 if achieved_tf else None,
+            "avg_launch_ms": ms_tc / n_tc if n_tc else None,
+            "traffic": None}
+    share = {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16x3(fp32 acc)",
+        "data": "synthetic",
+        "config": {"workload": "gray_scott_2048_ridc4_mixed", "grid": N, "species": 2,
+                   "order": ORDER, "top_level_steps": args.nt, "dt": 0.5, "n_refine": NREF,
+                   "l2": "inputs larger than L2 (about 2.6 GB of rings and work buffers)",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(w.u0.nbytes),
+                "d2h_bytes_per_step": int(w.u0.nbytes), "runs": e2e_runs},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernel_ms": share,
+        "fp64_gpu": fp64,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args.ref_steps)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
