@@ -135,6 +135,27 @@ const char* ridc_error_string(int code);
 int ridc_solve_planes(ridc_handle h, const double* r, double* delta, int nplanes,
                       int on_device);
 
+/* Batched FP64 solve that allocates nothing. The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library allocate device memory -- for example a
+ * simulation code that reserves all device memory for its own pool at start-up (a cudaMalloc
+ * here would fail or upset its budget), or a time-critical loop that cannot afford
+ * cudaMalloc/cudaFree, which may synchronise the device.
+ * It computes the same (I - dt nu_s L) delta = r as ridc_solve_planes with the FP64
+ * fast-diagonalisation GEMMs, without a handle:
+ *   kind    : RIDC_GRAY_SCOTT_2D_NEUMANN (nu[0], nu[1]; plane p uses species p % 2) or
+ *             RIDC_ADV_DIFF_2D_DIRICHLET (nu[0]).
+ *   r, delta: device pointers to nplanes*n*n FP64 values, [plane][y][x]; they may alias.
+ *   stream  : cudaStream_t (NULL: legacy default stream). Returns after launching.
+ * Its tables and intermediates live in one fixed device array inside libridc.so (2.5 MiB,
+ * held on every GPU that loads the library until the process exits). Limits: 4 <= n <= 128
+ * and 1 <= nplanes <= 8; larger requests return RIDC_ERR_UNSUPPORTED. Every call rewrites
+ * the whole array, so calls that overlap on the GPU (concurrent streams, other threads) race
+ * and must be serialised by the caller. The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and should therefore come before any stream capture.
+ * No cudaMalloc, cudaFree or other allocating routine is called.                           */
+int ridc_solve_planes_fixed(int kind, int n, const double* nu, double dt, const double* r,
+                            double* delta, int nplanes, void* stream);
+
 /* ---- host-only helpers (no GPU needed) ----------------------------------------------------- */
 
 /* The lock-step schedule of a fresh run of `nsteps` top-level steps: for each pipeline
