@@ -72,8 +72,8 @@ typedef struct {
 
 typedef struct {
     int dim;              /* 1 or 2; must match the kind                                     */
-    int n;                /* grid points per side: 1D n >= 8; 2D FP64 n >= 4;
-                             2D mixed: n a multiple of 256                                    */
+    int n;                /* grid points per side: 1D n >= 8; 2D FP64 4 <= n <= 16384;
+                             2D mixed: n a multiple of 256, at most 4096                      */
 } ridc_grid;
 
 typedef struct ridc_ctx* ridc_handle;   /* opaque; owned by the library                      */

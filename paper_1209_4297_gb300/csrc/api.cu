@@ -288,7 +288,7 @@ static int build_tables_1d(Ctx* c) {
 static void free_all(Ctx* c) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   for (int j = 0; j < kMaxOrder; ++j) { f(c->eta[j]); f(c->fN[j]); f(c->Fq[j]); }
-  f(c->r); f(c->delta); f(c->t1); f(c->t2); f(c->xh); f(c->xl); f(c->yh); f(c->yl);
+  f(c->r); f(c->delta); f(c->delta2); f(c->dinc); f(c->t1); f(c->t2); f(c->xh); f(c->xl); f(c->yh); f(c->yl);
   f(c->Q); f(c->Qt); f(c->inv_den); f(c->lam_f); f(c->Qh); f(c->Ql); f(c->Qth); f(c->Qtl);
   f(c->tri); f(c->sched_dev); f(c->p_dev); f(c->err_dev);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -336,6 +336,8 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
       RIDC_CUDA(cudaMalloc((void**)&c->t1, (size_t)order * pb));
       RIDC_CUDA(cudaMalloc((void**)&c->t2, (size_t)order * pb));
     } else {
+      RIDC_CUDA(cudaMalloc((void**)&c->delta2, (size_t)order * pb));
+      RIDC_CUDA(cudaMalloc((void**)&c->dinc, (size_t)order * c->plane * sizeof(float)));
       const size_t hb = (size_t)order * c->plane * sizeof(__nv_bfloat16);
       RIDC_CUDA(cudaMalloc((void**)&c->xh, hb));
       RIDC_CUDA(cudaMalloc((void**)&c->xl, hb));
@@ -377,7 +379,8 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
     if ((2L * order + 3) * g->n > 25600) return RIDC_ERR_UNSUPPORTED;   // shared-memory bound
   } else {
     if (g->dim != 2 || g->n < 4) return RIDC_ERR_ARG;
-    if (pr->precision == RIDC_MIXED_BF16X3 && (g->n % 256) != 0) return RIDC_ERR_UNSUPPORTED;
+    if (pr->precision == RIDC_MIXED_BF16X3 && ((g->n % 256) != 0 || g->n > 4096))
+      return RIDC_ERR_UNSUPPORTED;
     if (g->n > 16384) return RIDC_ERR_UNSUPPORTED;
   }
   Ctx* c = new (std::nothrow) Ctx();
@@ -438,7 +441,7 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
     fa.b2h = c->b / (2.0 * c->h);
     fa.gsF = c->gsF;
     fa.gsk = c->gsk;
-    fa.lv[0] = {c->eta[0], nullptr, c->eta[0], c->fN[0], c->Fq[0]};
+    fa.lv[0] = {c->eta[0], nullptr, nullptr, c->eta[0], c->fN[0], c->Fq[0]};
     RIDC_TRY(launch_finalize(c, fa));
   } else {
     RIDC_CUDA(cudaMemsetAsync(c->p_dev, 0, kMaxOrder * sizeof(long), c->stream));
@@ -462,25 +465,37 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
 // Fast diagonalisation: delta = Q ((Q^T R Q) ./ den) Q^T, den = 1 - dt nu_s (lam_ky + lam_kx).
 // Each GEMM contracts the contiguous axis of every plane and stores its result transposed,
 // so four identical "rows x Q" products realise the two-sided transform.
-static int solve_planes_dev(Ctx* c, int nplanes, bool rhs_split_done) {
+// The mixed form: pass 0 solves from the split right-hand side; every refinement pass forms
+// the FP64 residual of the running total (ping-pong buffers, so neighbours read a consistent
+// total) and solves for the next FP32 increment. The result stays split as total + increment.
+static int solve_planes_dev(Ctx* c, int nplanes, bool rhs_split_done, DeltaParts* out) {
   if (c->prec == RIDC_FP64) {
     RIDC_TRY(launch_gemm_f64(c, c->r, c->Qt, c->t1, nplanes, EPI_STORE));
     RIDC_TRY(launch_gemm_f64(c, c->t1, c->Qt, c->t2, nplanes, EPI_SCALE_DEN));
     RIDC_TRY(launch_gemm_f64(c, c->t2, c->Q, c->t1, nplanes, EPI_STORE));
     RIDC_TRY(launch_gemm_f64(c, c->t1, c->Q, c->delta, nplanes, EPI_DELTA));
+    *out = {c->delta, nullptr};
     return RIDC_OK;
   }
+  const double* total = nullptr;
   for (int pass = 0; pass <= c->n_refine; ++pass) {
-    if (pass > 0 || !rhs_split_done) RIDC_TRY(launch_residual(c, nplanes, pass == 0));
+    if (pass == 0) {
+      if (!rhs_split_done) RIDC_TRY(launch_residual(c, nplanes, nullptr, nullptr, nullptr));
+    } else {
+      double* dst = (total == c->delta) ? c->delta2 : c->delta;
+      RIDC_TRY(launch_residual(c, nplanes, total, c->dinc, dst));
+      total = dst;
+    }
     RIDC_TRY(launch_gemm_tc(c, &c->tm_xh, &c->tm_xl, &c->tm_Qth, &c->tm_Qtl, nplanes, EPI_STORE,
-                            c->yh, c->yl, nullptr, 0));
+                            c->yh, c->yl, nullptr));
     RIDC_TRY(launch_gemm_tc(c, &c->tm_yh, &c->tm_yl, &c->tm_Qth, &c->tm_Qtl, nplanes,
-                            EPI_SCALE_DEN, c->xh, c->xl, nullptr, 0));
+                            EPI_SCALE_DEN, c->xh, c->xl, nullptr));
     RIDC_TRY(launch_gemm_tc(c, &c->tm_xh, &c->tm_xl, &c->tm_Qh, &c->tm_Ql, nplanes, EPI_STORE,
-                            c->yh, c->yl, nullptr, 0));
+                            c->yh, c->yl, nullptr));
     RIDC_TRY(launch_gemm_tc(c, &c->tm_yh, &c->tm_yl, &c->tm_Qh, &c->tm_Ql, nplanes, EPI_DELTA,
-                            nullptr, nullptr, c->delta, pass > 0));
+                            nullptr, nullptr, c->dinc));
   }
+  *out = {total, c->dinc};
   return RIDC_OK;
 }
 
@@ -494,9 +509,16 @@ extern "C" int ridc_solve_planes(ridc_handle h, const double* r, double* delta, 
   const size_t bytes = (size_t)nplanes * nn * sizeof(double);
   RIDC_CUDA(cudaMemcpyAsync(c->r, r, bytes, on_device ? cudaMemcpyDeviceToDevice
                                                        : cudaMemcpyHostToDevice, c->stream));
-  RIDC_TRY(solve_planes_dev(c, nplanes, false));
-  RIDC_CUDA(cudaMemcpyAsync(delta, c->delta, bytes, on_device ? cudaMemcpyDeviceToDevice
-                                                               : cudaMemcpyDeviceToHost, c->stream));
+  DeltaParts parts;
+  RIDC_TRY(solve_planes_dev(c, nplanes, false, &parts));
+  const double* src = parts.d64;
+  if (parts.d32) {   // fold the FP32 increment into an FP64 buffer the solve no longer needs
+    double* dst = (parts.d64 == c->delta) ? c->delta2 : c->delta;
+    RIDC_TRY(launch_combine(c, parts.d64, parts.d32, dst, (long)nplanes * nn));
+    src = dst;
+  }
+  RIDC_CUDA(cudaMemcpyAsync(delta, src, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyDeviceToHost, c->stream));
   RIDC_CUDA(cudaStreamSynchronize(c->stream));
   int err = 0;
   RIDC_CUDA(cudaMemcpy(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
@@ -549,7 +571,8 @@ static int step_2d(Ctx* c, unsigned mask) {
     }
     FinLevel& Fl = fa.lv[na];
     Fl.base = base;
-    Fl.delta = c->delta + (size_t)na * c->plane;
+    Fl.d64 = nullptr;   // set after the solve, which decides where delta lives
+    Fl.d32 = nullptr;
     Fl.eta = slot_ptr(c, c->eta[j], j, n + 1);
     Fl.fN = slot_ptr(c, c->fN[j], j, n + 1);
     Fl.F = c->Fq[j] ? slot_ptr(c, c->Fq[j], j, n + 1) : nullptr;
@@ -564,7 +587,12 @@ static int step_2d(Ctx* c, unsigned mask) {
   ra.r_lo = (c->prec == RIDC_MIXED_BF16X3) ? c->xl : nullptr;
   fa.nlev = na;
   RIDC_TRY(launch_rhs(c, ra));
-  RIDC_TRY(solve_planes_dev(c, na * c->S, true));
+  DeltaParts parts;
+  RIDC_TRY(solve_planes_dev(c, na * c->S, true, &parts));
+  for (int q = 0; q < na; ++q) {
+    fa.lv[q].d64 = parts.d64 ? parts.d64 + (size_t)q * c->plane : nullptr;
+    fa.lv[q].d32 = parts.d32 ? parts.d32 + (size_t)q * c->plane : nullptr;
+  }
   RIDC_TRY(launch_finalize(c, fa));
   for (int j = 0; j < P; ++j)
     if (mask & (1u << j)) c->p[j]++;

@@ -5,13 +5,14 @@
 //   The result is stored transposed per plane, out[plane][m][row % N], so the next GEMM again
 //   contracts a contiguous axis; four such products give Q ((Q^T R Q) ./ den) Q^T.
 //
-// Per CTA: one 128 x 256 output tile, K consumed in 64-wide blocks. A producer thread moves
-// Ah, Al, Bh, Bl tiles (128B-swizzled) into a 2-stage shared-memory ring with TMA; one thread
-// issues 3 x 4 tcgen05.mma (M=128, N=256, K=16) per block into a TMEM accumulator; four
+// Output tiles are 128 x 256, K consumed in 64-wide blocks. A producer thread moves Ah, Al,
+// Bh, Bl tiles (128B-swizzled) into a 2-stage shared-memory ring with TMA; one thread issues
+// 3 x 4 tcgen05.mma (M=128, N=256, K=16) per block into one of two TMEM accumulators; four
 // epilogue warps read TMEM with tcgen05.ld and apply the epilogue:
 //   EPI_STORE      re-split to BF16 hi/lo for the next GEMM,
 //   EPI_SCALE_DEN  multiply by 1 / (1 - dt nu_s (lam_kx + lam_ky)) first,
-//   EPI_DELTA      write (or add to) the FP64 solution increment delta.
+//   EPI_DELTA      write the FP32 solution increment of this pass (the refinement residual
+//                  kernel folds it into the FP64 total, so the epilogue reads nothing).
 // Every mbarrier wait is bounded by a 2 s %globaltimer budget; on expiry the kernel records an
 // error flag, lets its copies and MMAs drain, frees its TMEM and returns.
 #include <cudaTypedefs.h>
@@ -24,16 +25,17 @@ constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 2;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;                  // 16 KB
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;                  // 32 KB
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 96 KB
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 1024;
+constexpr int TC_MAX_N = 4096;   // eigenvalue staging in shared memory
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 1024 + TC_MAX_N * 4;
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 struct TcArgs {
-  int n, rows, epi, accumulate, S;
+  int n, rows, epi, S;
   __nv_bfloat16* oh;
   __nv_bfloat16* ol;
-  double* o64;
+  float* o32;
   const float* lam;
   float dtnu[kMaxSpecies];
   int* err;
@@ -133,6 +135,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Persistent: one CTA per SM walks the output tiles t = blockIdx.x + i * gridDim.x (n-tile
+// fastest, so CTAs running together share A rows in L2). The TMA producer and the MMA issuer
+// run ahead across tile boundaries; two TMEM accumulators (256 columns each) let the four
+// epilogue warps drain tile i while the tensor cores compute tile i+1.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                    const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
@@ -141,29 +147,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * TC_STAGE_BYTES);
-  // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 1);
+  // full[S], empty[S], acc_full[2], acc_empty[2], mma_done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
+  float* lam_s = reinterpret_cast<float*>(smem + TC_STAGES * TC_STAGE_BYTES + 1024);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM;
   const int KB = a.n / TC_BK;
+  const int ntn = a.n / TC_BN;
+  const int ntiles = (a.rows / TC_BM) * ntn;
+  volatile int* errv = a.err;
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + TC_STAGES + s); };
-  const uint32_t accf = smem_u32(bars + 2 * TC_STAGES);
+  auto accf = [&](int b) { return smem_u32(bars + 2 * TC_STAGES + b); };
+  auto acce = [&](int b) { return smem_u32(bars + 2 * TC_STAGES + 2 + b); };
+  const uint32_t mma_done = smem_u32(bars + 2 * TC_STAGES + 4);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf(b), 1);
+      mbar_init(acce(b), 4);   // one arrival per epilogue warp
+    }
+    mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tAh)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tAl)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tBh)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tBl)) : "memory");
   }
+  if (a.epi == EPI_SCALE_DEN)
+    for (int i = threadIdx.x; i < a.n; i += TC_THREADS) lam_s[i] = a.lam[i];
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(TC_TMEM_COLS)
+                 "r"(2 * TC_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -174,72 +193,105 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
-    int issued = 0;
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % TC_STAGES, it = kb / TC_STAGES;
-      if (kb >= TC_STAGES && !mbar_wait(empty(s), (it - 1) & 1, a.err)) break;
-      if (*((volatile int*)a.err)) break;
-      uint8_t* st = smem + s * TC_STAGE_BYTES;
-      mbar_expect_tx(full(s), TC_STAGE_BYTES);
-      tma_load_2d(smem_u32(st), &tAh, full(s), kb * TC_BK, m0);
-      tma_load_2d(smem_u32(st + TC_A_BYTES), &tAl, full(s), kb * TC_BK, m0);
-      tma_load_2d(smem_u32(st + 2 * TC_A_BYTES), &tBh, full(s), kb * TC_BK, n0);
-      tma_load_2d(smem_u32(st + 2 * TC_A_BYTES + TC_B_BYTES), &tBl, full(s), kb * TC_BK, n0);
-      ++issued;
+    long issued = 0;   // K blocks issued so far (stage ring position)
+    for (int t = blockIdx.x; t < ntiles && !*errv; t += gridDim.x) {
+      const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
+      bool ok = true;
+      for (int kb = 0; kb < KB; ++kb, ++issued) {
+        const int s = (int)(issued % TC_STAGES);
+        const long it = issued / TC_STAGES;
+        if (issued >= TC_STAGES && !mbar_wait(empty(s), (uint32_t)((it - 1) & 1), a.err)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * TC_STAGE_BYTES;
+        mbar_expect_tx(full(s), TC_STAGE_BYTES);
+        tma_load_2d(smem_u32(st), &tAh, full(s), kb * TC_BK, m0);
+        tma_load_2d(smem_u32(st + TC_A_BYTES), &tAl, full(s), kb * TC_BK, m0);
+        tma_load_2d(smem_u32(st + 2 * TC_A_BYTES), &tBh, full(s), kb * TC_BK, n0);
+        tma_load_2d(smem_u32(st + 2 * TC_A_BYTES + TC_B_BYTES), &tBl, full(s), kb * TC_BK, n0);
+      }
+      if (!ok) break;
     }
-    // make sure none of our copies is still in flight when the CTA retires
-    for (int kb = issued - 1; kb >= 0 && kb >= issued - TC_STAGES; --kb)
-      mbar_wait(full(kb % TC_STAGES), (kb / TC_STAGES) & 1, a.err);
+    // none of our copies may still be in flight when the CTA retires
+    for (long q = issued - 1; q >= 0 && q >= issued - TC_STAGES; --q)
+      mbar_wait(full((int)(q % TC_STAGES)), (uint32_t)((q / TC_STAGES) & 1), a.err);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    for (int kb = 0; kb < KB; ++kb) {
-      const int s = kb % TC_STAGES, it = kb / TC_STAGES;
-      if (!mbar_wait(full(s), it & 1, a.err)) break;
+    long consumed = 0;
+    int local = 0;
+    for (int t = blockIdx.x; t < ntiles && !*errv; t += gridDim.x, ++local) {
+      const int b = local & 1;
+      const int use = local >> 1;   // how often accumulator b was used before
+      if (use > 0 && !mbar_wait(acce(b), (uint32_t)((use - 1) & 1), a.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(smem + s * TC_STAGE_BYTES);
-      const uint64_t ah = sdesc(st), al = sdesc(st + TC_A_BYTES);
-      const uint64_t bh = sdesc(st + 2 * TC_A_BYTES), bl = sdesc(st + 2 * TC_A_BYTES + TC_B_BYTES);
+      const uint32_t acc = tmem + (uint32_t)(b * TC_TMEM_COLS);
+      bool ok = true;
+      for (int kb = 0; kb < KB; ++kb, ++consumed) {
+        const int s = (int)(consumed % TC_STAGES);
+        if (!mbar_wait(full(s), (uint32_t)((consumed / TC_STAGES) & 1), a.err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(smem + s * TC_STAGE_BYTES);
+        const uint64_t ah = sdesc(st), al = sdesc(st + TC_A_BYTES);
+        const uint64_t bh = sdesc(st + 2 * TC_A_BYTES), bl = sdesc(st + 2 * TC_A_BYTES + TC_B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk) {
-        const uint64_t adv = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
-        mma_bf16(tmem, ah + adv, bh + adv, (kb | kk) != 0);
-        mma_bf16(tmem, ah + adv, bl + adv, 1);
-        mma_bf16(tmem, al + adv, bh + adv, 1);
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          const uint64_t adv = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
+          mma_bf16(acc, ah + adv, bh + adv, (kb | kk) != 0);
+          mma_bf16(acc, ah + adv, bl + adv, 1);
+          mma_bf16(acc, al + adv, bh + adv, 1);
+        }
+        mma_commit(empty(s));
       }
-      mma_commit(empty(s));
+      if (!ok) break;
+      mma_commit(accf(b));
     }
-    mma_commit(accf);   // also on an early exit: arrives once every issued MMA has finished
+    // every MMA issued by this CTA completes before TMEM is released
+    mma_commit(mma_done);
+    mbar_wait(mma_done, 0, a.err);
   } else if (warp >= 2) {
     // ---- epilogue: TMEM -> registers -> global, transposed per plane ----
     const int q = warp & 3;   // TMEM lane quarter this warp may access
-    const bool ok = mbar_wait(accf, 0, a.err);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && !*((volatile int*)a.err)) {
+    const int n = a.n;
+    int local = 0;
+    for (int t = blockIdx.x; t < ntiles && !*errv; t += gridDim.x, ++local) {
+      const int b = local & 1;
+      if (!mbar_wait(accf(b), (uint32_t)((local >> 1) & 1), a.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m0 = (t / ntn) * TC_BM, n0 = (t % ntn) * TC_BN;
       const int row = m0 + q * 32 + lane;
-      const int n = a.n;
       const int plane = row / n, rl = row - plane * n;
       const int s = plane % a.S;
-      const float lam_r = (a.epi == EPI_SCALE_DEN) ? a.lam[rl] : 0.f;
+      // den = 1 - dt nu_s (lam_kx + lam_ky) = den_r + den_m
       const float dtnu = a.dtnu[s];
+      const float den_r = (a.epi == EPI_SCALE_DEN) ? 1.0f - dtnu * lam_s[rl] : 0.f;
+      const uint32_t acc = tmem + (uint32_t)(b * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16);
       for (int c0 = 0; c0 < TC_BN; c0 += 16) {
         uint32_t v[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld16(acc + (uint32_t)c0, v);
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int m = n0 + c0 + jj;
           float val = __uint_as_float(v[jj]);
           const size_t idx = ((size_t)plane * n + m) * n + rl;
           if (a.epi == EPI_DELTA) {
-            const double d = (double)val;
-            a.o64[idx] = a.accumulate ? a.o64[idx] + d : d;
+            a.o32[idx] = val;
           } else {
-            if (a.epi == EPI_SCALE_DEN) val = val / (1.0f - dtnu * (lam_r + a.lam[m]));
+            if (a.epi == EPI_SCALE_DEN) val *= __frcp_rn(fmaf(-dtnu, lam_s[m], den_r));
             const __nv_bfloat16 h = __float2bfloat16_rn(val);
             a.oh[idx] = h;
             a.ol[idx] = __float2bfloat16_rn(val - __bfloat162float(h));
           }
         }
       }
+      // accumulator b may be overwritten once all four warps have read it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(b)) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -247,7 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TC_TMEM_COLS)
+                 "r"(2 * TC_TMEM_COLS)
                  : "memory");
   }
 }
@@ -275,7 +327,7 @@ int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int
 
 int launch_gemm_tc(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                    const CUtensorMap* bl, int nplanes, int epi, __nv_bfloat16* oh,
-                   __nv_bfloat16* ol, double* o64, int accumulate) {
+                   __nv_bfloat16* ol, float* o32) {
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -289,15 +341,23 @@ int launch_gemm_tc(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const C
   a.n = n;
   a.rows = nplanes * n;
   a.epi = epi;
-  a.accumulate = accumulate;
   a.S = c->S;
   a.oh = oh;
   a.ol = ol;
-  a.o64 = o64;
+  a.o32 = o32;
   a.lam = c->lam_f;
   for (int s = 0; s < c->S; ++s) a.dtnu[s] = (float)(c->dt * c->nu[s]);
   a.err = c->err_dev;
-  dim3 grid(n / TC_BN, a.rows / TC_BM);
+  if (n > TC_MAX_N) return RIDC_ERR_UNSUPPORTED;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int ntiles = (a.rows / TC_BM) * (n / TC_BN);
+  dim3 grid(ntiles < sms ? ntiles : sms);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_TC, &e0);
   gemm_tc_kernel<<<grid, TC_THREADS, TC_SMEM, c->stream>>>(*ah, *al, *bh, *bl, a);

@@ -10,40 +10,81 @@
 
 namespace ridc {
 
+// GB300 executes FP64 arithmetic and FP64<->FP32 conversions on its narrow FP64 pipe (about
+// 2 operations per clock per SM), so the kernels below do format conversions and ghost-cell
+// sign flips with integer bit operations, which run on the full-rate integer pipes.
+
+// FP64 -> FP32, round to nearest even, from the IEEE-754 formats: keep the top 23 of the 52
+// mantissa bits; a carry out of the mantissa bumps the exponent. Magnitudes below the FP32
+// normal range become signed zero (they are below 1.2e-38, far under every tolerance here);
+// magnitudes above it become infinity and NaN stays NaN, so a blow-up stays visible.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ef = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u | ((ef == 1151 && m) ? 0x400000u : 0u));
+  const unsigned long long mr = m + 0xFFFFFFFull + ((m >> 29) & 1ull);
+  return __uint_as_float(sign | (unsigned)(((unsigned long long)ef << 23) + (mr >> 29)));
+}
+
+// FP32 -> FP64, exact for normal values; FP32 subnormals (below 1.2e-38) become signed zero.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ed = (e == 255) ? 2047ull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+__device__ __forceinline__ double flip_sign(double v, bool neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+
 // BF16 hi/lo split of an FP64 value: x ~= hi + lo with |x - hi - lo| <= 2^-17 |x| (about).
 __device__ __forceinline__ void split2(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  const float f = (float)x;
+  const float f = f64_to_f32(x);
   hi = __float2bfloat16_rn(f);
   lo = __float2bfloat16_rn(f - __bfloat162float(hi));
 }
 
 // ---------------------------------------------------------------------------------------------
-// right-hand side: one level per blockIdx.y, S*N*N values, two per thread per iteration
+// right-hand side: one level per blockIdx.y, S*N*N values, two per thread per iteration.
+// The quadrature has exactly NODES terms per level (a switch picks the instantiation): on
+// GB300 a predicated-off FP64 instruction still occupies the FP64 pipe, so no FP64 work may
+// be issued for absent nodes.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArgs a) {
-  const RhsLevel& L = a.lv[blockIdx.y];
+template <int NODES>
+__device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, long out_off) {
   const long half = a.plane >> 1;
-  const long out_off = (long)blockIdx.y * a.plane;
-  const double2* Fn[kMaxOrder];
-  const int nn = L.nnodes;
+  const double2* Fn[NODES];
+  double w[NODES];
 #pragma unroll
-  for (int k = 0; k < kMaxOrder; ++k) Fn[k] = (k < nn) ? (const double2*)L.Fn[k] : nullptr;
+  for (int k = 0; k < NODES; ++k) {
+    Fn[k] = (const double2*)L.Fn[k];
+    w[k] = L.w[k];
+  }
+  const bool corr = L.eta_j != nullptr;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < half;
        i += (long)gridDim.x * blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    if (L.eta_j) {
+    double2 acc;
+    if (corr) {
       const double2 e = ((const double2*)L.eta_j)[i], ep = ((const double2*)L.eta_pn)[i];
       const double2 f = ((const double2*)L.fN_j)[i], fp = ((const double2*)L.fN_p)[i];
       acc.x = fma(a.dt, f.x - fp.x, e.x - ep.x);
       acc.y = fma(a.dt, f.y - fp.y, e.y - ep.y);
-    }
 #pragma unroll
-    for (int k = 0; k < kMaxOrder; ++k) {
-      if (k < nn) {
+      for (int k = 0; k < NODES; ++k) {
         const double2 F = __ldg(Fn[k] + i);
-        acc.x = fma(L.w[k], F.x, acc.x);
-        acc.y = fma(L.w[k], F.y, acc.y);
+        acc.x = fma(w[k], F.x, acc.x);
+        acc.y = fma(w[k], F.y, acc.y);
       }
+    } else {
+      const double2 F = __ldg(Fn[0] + i);
+      acc.x = w[0] * F.x;
+      acc.y = w[0] * F.y;
     }
     ((double2*)(a.r + out_off))[i] = acc;
     if (a.r_hi) {
@@ -56,6 +97,25 @@ __global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArg
       ((__nv_bfloat162*)(a.r_hi + out_off))[i] = hv;
       ((__nv_bfloat162*)(a.r_lo + out_off))[i] = lv;
     }
+  }
+}
+
+__global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArgs a) {
+  const RhsLevel& L = a.lv[blockIdx.y];
+  const long out_off = (long)blockIdx.y * a.plane;
+  switch (L.nnodes) {
+    case 1: rhs_level<1>(a, L, out_off); break;
+    case 2: rhs_level<2>(a, L, out_off); break;
+    case 3: rhs_level<3>(a, L, out_off); break;
+    case 4: rhs_level<4>(a, L, out_off); break;
+    case 5: rhs_level<5>(a, L, out_off); break;
+    case 6: rhs_level<6>(a, L, out_off); break;
+    case 7: rhs_level<7>(a, L, out_off); break;
+    case 8: rhs_level<8>(a, L, out_off); break;
+    case 9: rhs_level<9>(a, L, out_off); break;
+    case 10: rhs_level<10>(a, L, out_off); break;
+    case 11: rhs_level<11>(a, L, out_off); break;
+    default: rhs_level<12>(a, L, out_off); break;
   }
 }
 
@@ -77,22 +137,25 @@ int launch_rhs(Ctx* c, const RhsArgs& a) {
 // ---------------------------------------------------------------------------------------------
 constexpr int TX = 32, TY = 8;
 
-// Fills tile[TY+2][TX+2] with (x + d) around (x0, y0), ghosts by reflection with `sign`.
+// tile[TY+2][TX+2] = (x + d64 + d32) around (x0, y0); ghost cells take the mirrored value,
+// negated for the odd continuation (ODD). Absent addends are nullptr.
+template <bool ODD>
 __device__ __forceinline__ void load_tile(double (*tile)[TX + 2], const double* __restrict__ x,
-                                          const double* __restrict__ d, int n, int x0, int y0,
-                                          double sign) {
+                                          const double* __restrict__ d64,
+                                          const float* __restrict__ d32, int n, int x0, int y0) {
   for (int idx = threadIdx.y * TX + threadIdx.x; idx < (TY + 2) * (TX + 2); idx += TX * TY) {
-    const int ly = idx / (TX + 2), lx = idx % (TX + 2);
+    const int ly = idx / (TX + 2), lx = idx - ly * (TX + 2);
     int gy = y0 + ly - 1, gx = x0 + lx - 1;
-    double sg = 1.0;
-    if (gy < 0) { gy = 0; sg *= sign; }
-    if (gy >= n) { gy = n - 1; sg *= sign; }
-    if (gx < 0) { gx = 0; sg *= sign; }
-    if (gx >= n) { gx = n - 1; sg *= sign; }
+    bool neg = false;
+    if (gy < 0) { gy = 0; neg = !neg; }
+    if (gy >= n) { gy = n - 1; neg = !neg; }
+    if (gx < 0) { gx = 0; neg = !neg; }
+    if (gx >= n) { gx = n - 1; neg = !neg; }
     const long o = (long)gy * n + gx;
-    double v = x[o];
-    if (d) v += d[o];
-    tile[ly][lx] = sg * v;
+    double v = x ? x[o] : 0.0;
+    if (d64) v = x ? v + d64[o] : d64[o];
+    if (d32) v = (x || d64) ? v + f32_to_f64(d32[o]) : f32_to_f64(d32[o]);
+    tile[ly][lx] = ODD ? flip_sign(v, neg) : v;
   }
 }
 
@@ -102,7 +165,7 @@ __device__ __forceinline__ void load_tile(double (*tile)[TX + 2], const double* 
 template <int KIND>
 __global__ void __launch_bounds__(TX * TY) finalize_kernel(const __grid_constant__ FinArgs a) {
   constexpr int S = (KIND == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
-  constexpr double sign = (KIND == RIDC_ADV_DIFF_2D_DIRICHLET) ? -1.0 : 1.0;
+  constexpr bool ODD = (KIND == RIDC_ADV_DIFF_2D_DIRICHLET);
   __shared__ double tile[S][TY + 2][TX + 2];
   const FinLevel& L = a.lv[blockIdx.z];
   const int n = a.n;
@@ -110,19 +173,16 @@ __global__ void __launch_bounds__(TX * TY) finalize_kernel(const __grid_constant
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
 #pragma unroll
   for (int s = 0; s < S; ++s)
-    load_tile(tile[s], L.base + s * nn, L.delta ? L.delta + s * nn : nullptr, n, x0, y0, sign);
+    load_tile<ODD>(tile[s], L.base + s * nn, L.d64 ? L.d64 + s * nn : nullptr,
+                   L.d32 ? L.d32 + s * nn : nullptr, n, x0, y0);
   __syncthreads();
   const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
   const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
   if (gx >= n || gy >= n) return;
   const long o = (long)gy * n + gx;
-  double u[S], lap[S], fn[S];
+  double u[S], fn[S];
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    u[s] = tile[s][ty][tx];
-    lap[s] = ((tile[s][ty - 1][tx] + tile[s][ty + 1][tx]) + (tile[s][ty][tx - 1] + tile[s][ty][tx + 1]))
-             - 4.0 * u[s];
-  }
+  for (int s = 0; s < S; ++s) u[s] = tile[s][ty][tx];
   if (KIND == RIDC_GRAY_SCOTT_2D_NEUMANN) {
     const double uvv = u[0] * u[S - 1] * u[S - 1];
     fn[0] = fma(a.gsF, 1.0 - u[0], -uvv);
@@ -131,11 +191,17 @@ __global__ void __launch_bounds__(TX * TY) finalize_kernel(const __grid_constant
     fn[0] = -a.a2h * (tile[0][ty][tx + 1] - tile[0][ty][tx - 1])
             - a.b2h * (tile[0][ty + 1][tx] - tile[0][ty - 1][tx]);
   }
+  const bool new_state = L.d64 || L.d32;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    if (L.delta) L.eta[s * nn + o] = u[s];
+    if (new_state) L.eta[s * nn + o] = u[s];
     L.fN[s * nn + o] = fn[s];
-    if (L.F) L.F[s * nn + o] = fma(a.c_lap[s], lap[s], fn[s]);
+    if (L.F) {
+      // f = f^N + c (N + S + W + E - 4 u),  c = nu_s / h^2
+      const double sum = (tile[s][ty - 1][tx] + tile[s][ty + 1][tx]) +
+                         (tile[s][ty][tx - 1] + tile[s][ty][tx + 1]);
+      L.F[s * nn + o] = fma(a.c_lap[s], sum, fma(-4.0 * a.c_lap[s], u[s], fn[s]));
+    }
   }
 }
 
@@ -153,18 +219,22 @@ int launch_finalize(Ctx* c, const FinArgs& a) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// refinement residual of the mixed solve: r' = r - delta + dt nu_s L delta, split to BF16
+// refinement residual of the mixed solve:
+//   d = dprev + inc  (written to dout),   r' = r - (I - c_s L) d = r - (1 + 4 c_s) d + c_s (N+S+W+E)
+// with c_s = dt nu_s / h^2, then r' split to BF16 hi/lo. Without dprev and inc: r' = r.
 // ---------------------------------------------------------------------------------------------
 struct ResArgs {
   const double* r;
-  const double* delta;      // nullptr on the first pass: r' = r
+  const double* dprev;
+  const float* inc;
+  double* dout;
   __nv_bfloat16* hi;
   __nv_bfloat16* lo;
   int n, S;
-  double c[kMaxSpecies];    // dt nu_s / h^2
-  double sign;
+  double c[kMaxSpecies];
 };
 
+template <bool ODD>
 __global__ void __launch_bounds__(TX * TY) residual_kernel(const __grid_constant__ ResArgs a) {
   __shared__ double tile[TY + 2][TX + 2];
   const int n = a.n;
@@ -173,41 +243,67 @@ __global__ void __launch_bounds__(TX * TY) residual_kernel(const __grid_constant
   const long off = (long)p * nn;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-  double v;
-  if (a.delta) {
-    load_tile(tile, a.delta + off, nullptr, n, x0, y0, a.sign);
+  const bool has_d = a.dprev || a.inc;
+  if (has_d) {
+    load_tile<ODD>(tile, nullptr, a.dprev ? a.dprev + off : nullptr, a.inc ? a.inc + off : nullptr,
+                   n, x0, y0);
     __syncthreads();
-    if (gx >= n || gy >= n) return;
+  }
+  if (gx >= n || gy >= n) return;
+  const long o = off + (long)gy * n + gx;
+  double v = a.r[o];
+  if (has_d) {
     const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
     const double d = tile[ty][tx];
-    const double lap = ((tile[ty - 1][tx] + tile[ty + 1][tx]) + (tile[ty][tx - 1] + tile[ty][tx + 1]))
-                       - 4.0 * d;
-    v = fma(a.c[p % a.S], lap, a.r[off + (long)gy * n + gx] - d);
-  } else {
-    if (gx >= n || gy >= n) return;
-    v = a.r[off + (long)gy * n + gx];
+    const double cs = a.c[p % a.S];
+    const double sum = (tile[ty - 1][tx] + tile[ty + 1][tx]) + (tile[ty][tx - 1] + tile[ty][tx + 1]);
+    v = fma(cs, sum, fma(-(1.0 + 4.0 * cs), d, v));
+    a.dout[o] = d;
   }
   __nv_bfloat16 h, l;
   split2(v, h, l);
-  a.hi[off + (long)gy * n + gx] = h;
-  a.lo[off + (long)gy * n + gx] = l;
+  a.hi[o] = h;
+  a.lo[o] = l;
 }
 
-int launch_residual(Ctx* c, int nplanes, int first) {
+int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, double* dout) {
   ResArgs a{};
   a.r = c->r;
-  a.delta = first ? nullptr : c->delta;
+  a.dprev = dprev;
+  a.inc = inc;
+  a.dout = dout;
   a.hi = c->xh;
   a.lo = c->xl;
   a.n = c->n;
   a.S = c->S;
   for (int s = 0; s < c->S; ++s) a.c[s] = c->dt * c->nu[s] / (c->h * c->h);
-  a.sign = (c->kind == RIDC_ADV_DIFF_2D_DIRICHLET) ? -1.0 : 1.0;
   dim3 grid((c->n + TX - 1) / TX, (c->n + TY - 1) / TY, nplanes);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_RESIDUAL, &e0);
-  residual_kernel<<<grid, dim3(TX, TY), 0, c->stream>>>(a);
+  if (c->kind == RIDC_ADV_DIFF_2D_DIRICHLET)
+    residual_kernel<true><<<grid, dim3(TX, TY), 0, c->stream>>>(a);
+  else
+    residual_kernel<false><<<grid, dim3(TX, TY), 0, c->stream>>>(a);
   prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
+  return cuda_status(cudaGetLastError());
+}
+
+// out = d64 + d32 (either part may be absent)
+__global__ void combine_kernel(const double* __restrict__ d64, const float* __restrict__ d32,
+                               double* __restrict__ out, long count) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count;
+       i += (long)gridDim.x * blockDim.x) {
+    double v = d64 ? d64[i] : 0.0;
+    if (d32) v = d64 ? v + f32_to_f64(d32[i]) : f32_to_f64(d32[i]);
+    out[i] = v;
+  }
+}
+
+int launch_combine(Ctx* c, const double* d64, const float* d32, double* out, long count) {
+  long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  combine_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(d64, d32, out, count);
+  c->launches++;
   return cuda_status(cudaGetLastError());
 }
 

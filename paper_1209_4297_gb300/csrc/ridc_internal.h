@@ -41,13 +41,22 @@ struct RhsArgs {
   __nv_bfloat16* r_lo;
 };
 
-// New state of one advancing level: eta = base + delta, then f^N(eta) and F = f^N + D eta.
+// New state of one advancing level: eta = base + d64 + d32, then f^N(eta) and
+// F = f^N + D eta. The solve's increment arrives as an FP64 part and/or an FP32 part (the
+// last tensor-core pass); nullptr parts are absent (both absent: eta = base).
 struct FinLevel {
   const double* base;     // [S][N][N]
-  const double* delta;    // [S][N][N]  (nullptr: eta = base)
+  const double* d64;      // [S][N][N] or nullptr
+  const float* d32;       // [S][N][N] or nullptr
   double* eta;            // outputs, [S][N][N]
   double* fN;
   double* F;              // nullptr when no consumer needs f of this level
+};
+
+// Where a batched solve left delta: delta = d64 + d32 (either may be nullptr).
+struct DeltaParts {
+  const double* d64;
+  const float* d32;
 };
 
 struct FinArgs {
@@ -86,7 +95,9 @@ struct Ctx {
   // work buffers
   long plane = 0;            // S * N^dim
   double* r = nullptr;       // [P*S][N][N]
-  double* delta = nullptr;   // [P*S][N][N]
+  double* delta = nullptr;   // [P*S][N][N]  FP64 solution increment (ping)
+  double* delta2 = nullptr;  // [P*S][N][N]  (pong, refinement passes)
+  float* dinc = nullptr;     // [P*S][N][N]  FP32 increment of the latest tensor-core pass
   double* t1 = nullptr;      // FP64 GEMM intermediates
   double* t2 = nullptr;
   __nv_bfloat16* xh = nullptr;   // split operands, ping
@@ -135,11 +146,16 @@ unsigned plan_step(int P, const long* p, long target_top);
 // ---- kernel launchers (each returns RIDC_OK or an error code) -------------------------------------
 int launch_rhs(Ctx* c, const RhsArgs& a);
 int launch_finalize(Ctx* c, const FinArgs& a);
-int launch_residual(Ctx* c, int nplanes, int first);
+// r' = r - (I - dt nu_s L)(dprev + inc), split to BF16 hi/lo into xh/xl; the new total
+// dprev + inc is written to dout. dprev, inc may be nullptr (absent); with both absent the
+// kernel only splits r.
+int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, double* dout);
+// out = d64 + d32 elementwise over count values (either part may be nullptr)
+int launch_combine(Ctx* c, const double* d64, const float* d32, double* out, long count);
 int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi);
 int launch_gemm_tc(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                    const CUtensorMap* bl, int nplanes, int epi, __nv_bfloat16* oh,
-                   __nv_bfloat16* ol, double* o64, int accumulate);
+                   __nv_bfloat16* ol, float* o32);
 int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
 int launch_1d(Ctx* c, long nsteps_pipe, int init_only);
 int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);

@@ -160,3 +160,38 @@ def test_invalid_arguments_raise():
             it.advance(1)                                       # no initial state yet
         with pytest.raises(RidcError):
             it.set_initial(np.zeros(10))
+
+
+# ---------------------------------------------------------------- larger grids (persistent GEMM
+# with several tiles per CTA) and the full-size workloads on truncated runs
+def test_mixed_batched_solve_1024_many_tiles_per_cta():
+    need_cuda()
+    n = 1024
+    g = np.random.default_rng(3)
+    w = inputs.gray_scott_2d(n=n, nsteps=1)
+    prob = oracle.from_workload(w)
+    x = (np.arange(n) + 0.5) / n
+    r = np.sin(5 * x)[None, :, None] * np.cos(3 * x)[None, None, :] + 1e-3 * g.standard_normal((8, n, n))
+    with Integrator.from_workload(w, precision="mixed_bf16x3", n_refine=2) as it:
+        got = it.solve_planes(r)
+    for p in range(8):
+        want = prob.solve(np.stack([r[p]] * 2), w.dt)[p % 2]
+        assert rel_l2(got[p], want) <= 1e-9, p
+
+
+def test_gray_scott_1024_fp64_full_size_truncated():
+    """The 1024^2 FP64 workload through start-up and into the steady pipeline."""
+    w = inputs.gray_scott_2d(n=1024, nsteps=12)
+    got, levels, _ = _run(w)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4, all_levels=True)
+    for j in range(4):
+        assert rel_l2(levels[j][0], ref[j]) <= 1e-12, j
+
+
+def test_gray_scott_2048_mixed_full_size_truncated():
+    """The 2048^2 mixed workload (the benchmark's) against the oracle, start-up included."""
+    w = inputs.gray_scott_2d(n=2048, nsteps=8)
+    got, levels, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4, all_levels=True)
+    for j in range(4):
+        assert rel_l2(levels[j][0], ref[j]) <= 1e-8, j
