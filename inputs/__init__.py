@@ -89,6 +89,20 @@ def gray_scott_2d(n: int = 1024, seed: int = 0, nsteps: int = 2000, dt: float = 
                     F=F, k=k, meta={"centre": (float(cx), float(cy))})
 
 
+def gray_scott_smooth(n: int = 256, seed: int = 0, nsteps: int = 16, dt: float = 1.0,
+                      order: int = 4, Du: float = 2e-5, Dv: float = 1e-5, F: float = 0.04,
+                      k: float = 0.06, width2: float = 0.02) -> Workload:
+    """Smooth Gray-Scott data for convergence-order checks: a Gaussian bump
+    g = exp(-|x - c|^2 / width2), centre uniform in [0.4, 0.6]^2; u = 1 - g/2, v = g/4."""
+    g = _rng(seed)
+    cx, cy = g.uniform(0.4, 0.6, 2)
+    x = (np.arange(n, dtype=np.float64) + 0.5) / n
+    bump = np.exp(-((x[:, None] - cy) ** 2 + (x[None, :] - cx) ** 2) / width2)
+    y0 = np.stack([1.0 - 0.5 * bump, 0.25 * bump])
+    return Workload("gray_scott_2d_neumann", n, dt, nsteps, order, (Du, Dv), np.ascontiguousarray(y0),
+                    F=F, k=k, meta={"centre": (float(cx), float(cy))})
+
+
 def _sine_field(n: int, coef: np.ndarray) -> np.ndarray:
     """sum_{ky,kx} coef[ky-1, kx-1] sin(pi kx x) sin(pi ky y) on the cell centres."""
     kmax = coef.shape[0]

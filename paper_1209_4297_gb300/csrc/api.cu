@@ -415,6 +415,19 @@ static int ensure_pinned(Ctx* c, size_t count) {
   return RIDC_OK;
 }
 
+// constants of the finalize kernel, computed once in FP64 on the host
+static void fill_fin_consts(Ctx* c, FinArgs* fa) {
+  for (int s = 0; s < c->S; ++s) {
+    fa->c_lap[s] = c->nu[s] / (c->h * c->h);
+    fa->c_lap4[s] = -4.0 * fa->c_lap[s];
+  }
+  fa->a2h = c->a / (2.0 * c->h);
+  fa->b2h = c->b / (2.0 * c->h);
+  fa->gsF = c->gsF;
+  fa->gsk = c->gsk;
+  fa->gsFk = -(c->gsF + c->gsk);
+}
+
 // ------------------------------------------------------------------------------------------
 // initial state
 // ------------------------------------------------------------------------------------------
@@ -436,11 +449,7 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
     fa.nlev = 1;
     fa.n = c->n;
     fa.kind = c->kind;
-    for (int s = 0; s < c->S; ++s) fa.c_lap[s] = c->nu[s] / (c->h * c->h);
-    fa.a2h = c->a / (2.0 * c->h);
-    fa.b2h = c->b / (2.0 * c->h);
-    fa.gsF = c->gsF;
-    fa.gsk = c->gsk;
+    fill_fin_consts(c, &fa);
     fa.lv[0] = {c->eta[0], nullptr, nullptr, c->eta[0], c->fN[0], c->Fq[0]};
     RIDC_TRY(launch_finalize(c, fa));
   } else {
@@ -537,11 +546,7 @@ static int step_2d(Ctx* c, unsigned mask) {
   FinArgs fa{};
   fa.n = c->n;
   fa.kind = c->kind;
-  for (int s = 0; s < c->S; ++s) fa.c_lap[s] = c->nu[s] / (c->h * c->h);
-  fa.a2h = c->a / (2.0 * c->h);
-  fa.b2h = c->b / (2.0 * c->h);
-  fa.gsF = c->gsF;
-  fa.gsk = c->gsk;
+  fill_fin_consts(c, &fa);
   const int P = c->P;
   int na = 0;
   for (int j = 0; j < P; ++j) {

@@ -135,7 +135,9 @@ int launch_rhs(Ctx* c, const RhsArgs& a) {
 // ---------------------------------------------------------------------------------------------
 // tile loader with reflecting ghosts: even (Neumann) or odd (Dirichlet) continuation
 // ---------------------------------------------------------------------------------------------
-constexpr int TX = 32, TY = 8;
+// A 256-thread block (32 x 8) covers a 32 x 32 tile, four rows per thread; the one-cell halo
+// costs 34*34/(32*32) = 1.13 loads per cell.
+constexpr int TX = 32, TY = 32, BY = 8, RPT = TY / BY;
 
 // tile[TY+2][TX+2] = (x + d64 + d32) around (x0, y0); ghost cells take the mirrored value,
 // negated for the odd continuation (ODD). Absent addends are nullptr.
@@ -143,7 +145,7 @@ template <bool ODD>
 __device__ __forceinline__ void load_tile(double (*tile)[TX + 2], const double* __restrict__ x,
                                           const double* __restrict__ d64,
                                           const float* __restrict__ d32, int n, int x0, int y0) {
-  for (int idx = threadIdx.y * TX + threadIdx.x; idx < (TY + 2) * (TX + 2); idx += TX * TY) {
+  for (int idx = threadIdx.y * TX + threadIdx.x; idx < (TY + 2) * (TX + 2); idx += TX * BY) {
     const int ly = idx / (TX + 2), lx = idx - ly * (TX + 2);
     int gy = y0 + ly - 1, gx = x0 + lx - 1;
     bool neg = false;
@@ -163,7 +165,7 @@ __device__ __forceinline__ void load_tile(double (*tile)[TX + 2], const double* 
 // new state of every advancing level: eta = base + delta, f^N(eta), f = f^N + nu L eta
 // ---------------------------------------------------------------------------------------------
 template <int KIND>
-__global__ void __launch_bounds__(TX * TY) finalize_kernel(const __grid_constant__ FinArgs a) {
+__global__ void __launch_bounds__(TX * BY) finalize_kernel(const __grid_constant__ FinArgs a) {
   constexpr int S = (KIND == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
   constexpr bool ODD = (KIND == RIDC_ADV_DIFF_2D_DIRICHLET);
   __shared__ double tile[S][TY + 2][TX + 2];
@@ -176,38 +178,43 @@ __global__ void __launch_bounds__(TX * TY) finalize_kernel(const __grid_constant
     load_tile<ODD>(tile[s], L.base + s * nn, L.d64 ? L.d64 + s * nn : nullptr,
                    L.d32 ? L.d32 + s * nn : nullptr, n, x0, y0);
   __syncthreads();
-  const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-  const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-  if (gx >= n || gy >= n) return;
-  const long o = (long)gy * n + gx;
-  double u[S], fn[S];
-#pragma unroll
-  for (int s = 0; s < S; ++s) u[s] = tile[s][ty][tx];
-  if (KIND == RIDC_GRAY_SCOTT_2D_NEUMANN) {
-    const double uvv = u[0] * u[S - 1] * u[S - 1];
-    fn[0] = fma(a.gsF, 1.0 - u[0], -uvv);
-    fn[S - 1] = fma(-(a.gsF + a.gsk), u[S - 1], uvv);
-  } else {
-    fn[0] = -a.a2h * (tile[0][ty][tx + 1] - tile[0][ty][tx - 1])
-            - a.b2h * (tile[0][ty + 1][tx] - tile[0][ty - 1][tx]);
-  }
+  const int tx = threadIdx.x + 1;
+  const int gx = x0 + threadIdx.x;
+  if (gx >= n) return;
   const bool new_state = L.d64 || L.d32;
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    if (new_state) L.eta[s * nn + o] = u[s];
-    L.fN[s * nn + o] = fn[s];
-    if (L.F) {
-      // f = f^N + c (N + S + W + E - 4 u),  c = nu_s / h^2
-      const double sum = (tile[s][ty - 1][tx] + tile[s][ty + 1][tx]) +
-                         (tile[s][ty][tx - 1] + tile[s][ty][tx + 1]);
-      L.F[s * nn + o] = fma(a.c_lap[s], sum, fma(-4.0 * a.c_lap[s], u[s], fn[s]));
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int ty = threadIdx.y + rr * BY + 1, gy = y0 + ty - 1;
+    if (gy >= n) break;
+    const long o = (long)gy * n + gx;
+    double u[S], fn[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] = tile[s][ty][tx];
+    if (KIND == RIDC_GRAY_SCOTT_2D_NEUMANN) {
+      const double uvv = u[0] * u[S - 1] * u[S - 1];
+      fn[0] = fma(a.gsF, 1.0 - u[0], -uvv);
+      fn[S - 1] = fma(a.gsFk, u[S - 1], uvv);
+    } else {
+      fn[0] = -a.a2h * (tile[0][ty][tx + 1] - tile[0][ty][tx - 1])
+              - a.b2h * (tile[0][ty + 1][tx] - tile[0][ty - 1][tx]);
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      if (new_state) L.eta[s * nn + o] = u[s];
+      L.fN[s * nn + o] = fn[s];
+      if (L.F) {
+        // f = f^N + c (N + S + W + E) - 4 c u,  c = nu_s / h^2
+        const double sum = (tile[s][ty - 1][tx] + tile[s][ty + 1][tx]) +
+                           (tile[s][ty][tx - 1] + tile[s][ty][tx + 1]);
+        L.F[s * nn + o] = fma(a.c_lap[s], sum, fma(a.c_lap4[s], u[s], fn[s]));
+      }
     }
   }
 }
 
 int launch_finalize(Ctx* c, const FinArgs& a) {
   dim3 grid((a.n + TX - 1) / TX, (a.n + TY - 1) / TY, a.nlev);
-  dim3 block(TX, TY);
+  dim3 block(TX, BY);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_FINALIZE, &e0);
   if (a.kind == RIDC_GRAY_SCOTT_2D_NEUMANN)
@@ -231,39 +238,46 @@ struct ResArgs {
   __nv_bfloat16* hi;
   __nv_bfloat16* lo;
   int n, S;
-  double c[kMaxSpecies];
+  double c[kMaxSpecies];    // c_s
+  double c1[kMaxSpecies];   // -(1 + 4 c_s)
 };
 
 template <bool ODD>
-__global__ void __launch_bounds__(TX * TY) residual_kernel(const __grid_constant__ ResArgs a) {
+__global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant__ ResArgs a) {
   __shared__ double tile[TY + 2][TX + 2];
   const int n = a.n;
   const long nn = (long)n * n;
   const int p = blockIdx.z;
   const long off = (long)p * nn;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+  const int gx = x0 + threadIdx.x;
   const bool has_d = a.dprev || a.inc;
   if (has_d) {
     load_tile<ODD>(tile, nullptr, a.dprev ? a.dprev + off : nullptr, a.inc ? a.inc + off : nullptr,
                    n, x0, y0);
     __syncthreads();
   }
-  if (gx >= n || gy >= n) return;
-  const long o = off + (long)gy * n + gx;
-  double v = a.r[o];
-  if (has_d) {
-    const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-    const double d = tile[ty][tx];
-    const double cs = a.c[p % a.S];
-    const double sum = (tile[ty - 1][tx] + tile[ty + 1][tx]) + (tile[ty][tx - 1] + tile[ty][tx + 1]);
-    v = fma(cs, sum, fma(-(1.0 + 4.0 * cs), d, v));
-    a.dout[o] = d;
+  if (gx >= n) return;
+  const int sp = p % a.S;
+  const double cs = a.c[sp], c1 = a.c1[sp];
+#pragma unroll
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int ty = threadIdx.y + rr * BY + 1, gy = y0 + ty - 1;
+    if (gy >= n) break;
+    const long o = off + (long)gy * n + gx;
+    double v = a.r[o];
+    if (has_d) {
+      const int tx = threadIdx.x + 1;
+      const double d = tile[ty][tx];
+      const double sum = (tile[ty - 1][tx] + tile[ty + 1][tx]) + (tile[ty][tx - 1] + tile[ty][tx + 1]);
+      v = fma(cs, sum, fma(c1, d, v));
+      a.dout[o] = d;
+    }
+    __nv_bfloat16 h, l;
+    split2(v, h, l);
+    a.hi[o] = h;
+    a.lo[o] = l;
   }
-  __nv_bfloat16 h, l;
-  split2(v, h, l);
-  a.hi[o] = h;
-  a.lo[o] = l;
 }
 
 int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, double* dout) {
@@ -276,14 +290,17 @@ int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, 
   a.lo = c->xl;
   a.n = c->n;
   a.S = c->S;
-  for (int s = 0; s < c->S; ++s) a.c[s] = c->dt * c->nu[s] / (c->h * c->h);
+  for (int s = 0; s < c->S; ++s) {
+    a.c[s] = c->dt * c->nu[s] / (c->h * c->h);
+    a.c1[s] = -(1.0 + 4.0 * a.c[s]);
+  }
   dim3 grid((c->n + TX - 1) / TX, (c->n + TY - 1) / TY, nplanes);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_RESIDUAL, &e0);
   if (c->kind == RIDC_ADV_DIFF_2D_DIRICHLET)
-    residual_kernel<true><<<grid, dim3(TX, TY), 0, c->stream>>>(a);
+    residual_kernel<true><<<grid, dim3(TX, BY), 0, c->stream>>>(a);
   else
-    residual_kernel<false><<<grid, dim3(TX, TY), 0, c->stream>>>(a);
+    residual_kernel<false><<<grid, dim3(TX, BY), 0, c->stream>>>(a);
   prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
   return cuda_status(cudaGetLastError());
 }

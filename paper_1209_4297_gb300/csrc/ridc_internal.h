@@ -65,8 +65,10 @@ struct FinArgs {
   int n;
   int kind;
   double c_lap[kMaxSpecies];   // nu_s / h^2
+  double c_lap4[kMaxSpecies];  // -4 nu_s / h^2
   double a2h, b2h;             // a / (2h), b / (2h)
   double gsF, gsk;             // Gray-Scott rates
+  double gsFk;                 // -(F + k)
 };
 
 // ---- the handle -----------------------------------------------------------------------------

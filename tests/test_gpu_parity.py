@@ -195,3 +195,11 @@ def test_gray_scott_2048_mixed_full_size_truncated():
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4, all_levels=True)
     for j in range(4):
         assert rel_l2(levels[j][0], ref[j]) <= 1e-8, j
+
+
+def test_dirichlet_4096_mixed_full_size_truncated():
+    """The 4096^2 Dirichlet advection-diffusion workload (mixed) against the oracle."""
+    w = inputs.adv_diff_2d(n=4096, nsteps=5)
+    got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4)
+    assert rel_l2(got, ref) <= 1e-8
