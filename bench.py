@@ -147,6 +147,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args):
+    """The 512-instance ensemble (uneven Dirichlet advection-diffusion, FP32 solves with one
+    FP64-residual refinement pass) advanced 256 steps by one persistent launch; the autotuner
+    picks the launch configuration first. Not the default line: a per-config measurement."""
+    import torch
+
+    import inputs
+    from paper_1209_4297_gb300 import Batch
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ws = inputs.ensemble(512, nsteps=256)
+    u0s = [torch.from_numpy(w.u0[0].copy()).cuda() for w in ws]
+    b = Batch(ws, n_refine=args.ens_refine, stream=stream.cuda_stream)
+    b.set_initial(u0s)
+    choice, tune_ms = b.autotune(8)
+    cells = b.cells()
+    for _ in range(args.warmup):
+        b.set_initial(u0s)
+        b.advance(256)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        b.set_initial(u0s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.advance(256)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    b.close()
+    ms = statistics.median(times)
+    line = {"metric": "ensemble cell-updates/s (sum over instances of side^2 x 256 steps)",
+            "value": cells * 256 / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f64+fp32 solves", "data": "synthetic",
+            "config": {"workload": "ensemble_512_dirichlet_adv_diff", "instances": 512,
+                       "steps": 256, "n_refine": args.ens_refine, "autotune_choice": choice,
+                       "cells_per_step": cells}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -157,9 +199,13 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=6)
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="gray_scott_2048", choices=["gray_scott_2048", "ensemble"])
+    ap.add_argument("--ens-refine", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
 
     import torch
     import torch.distributed as dist

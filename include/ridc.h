@@ -58,7 +58,11 @@ typedef enum {
     /* 2D solves by BF16 hi/lo split-precision GEMMs on the tensor cores (FP32 accumulation)
        plus n_refine refinement passes against the FP64 residual; right-hand sides,
        quadrature sums and solution accumulation stay FP64                                   */
-    RIDC_MIXED_BF16X3 = 1
+    RIDC_MIXED_BF16X3 = 1,
+    /* batched ensembles only: solves in FP32 on the CUDA cores, right-hand sides, quadrature
+       sums and solution accumulation in FP64, plus n_refine refinement passes against the
+       FP64 residual                                                                         */
+    RIDC_FP32_SOLVE = 2
 } ridc_precision;
 
 typedef struct {
@@ -155,6 +159,44 @@ int ridc_solve_planes(ridc_handle h, const double* r, double* delta, int nplanes
  * No cudaMalloc, cudaFree or other allocating routine is called.                           */
 int ridc_solve_planes_fixed(int kind, int n, const double* nu, double dt, const double* r,
                             double* delta, int nplanes, void* stream);
+
+/* ---- batched ensembles ----------------------------------------------------------------------- */
+
+/* Many independent instances of RIDC_ADV_DIFF_2D_DIRICHLET (uneven grid sides 8..512, orders
+ * 1..4, own a, b, nu and dt) advanced together by one persistent kernel launch: each CTA
+ * integrates whole instances, largest first. Solves run in FP32 (problem.precision must be
+ * RIDC_FP32_SOLVE); everything else is FP64, as in ridc_create (the benchmark spec batching pattern;
+ * the paper runs one instance at a time).
+ *   count      : number of instances; problems, grids, nu, dt, order are arrays of `count`.
+ *   n_refine   : must be the same for all instances (0..4 refinement passes).
+ * Device memory belongs to the library (rings per instance, per-CTA workspace).            */
+typedef struct ridc_batch_ctx* ridc_batch;
+int ridc_batch_create(int count, const ridc_problem* problems, const ridc_grid* grids,
+                      const double* nu, const double* dt, const int* order, void* stream,
+                      ridc_batch* out);
+
+/* u0[i] points to instance i's n_i*n_i initial values (all on the host or all on the device).
+ * Rewinds every instance to t_0. Synchronises the stream.                                   */
+int ridc_batch_set_initial(ridc_batch b, const double* const* u0, int on_device);
+
+/* Advance every instance until its most corrected level has taken `nsteps` more steps
+ * (one kernel launch). Stream-ordered; returns after launching.                            */
+int ridc_batch_advance(ridc_batch b, long nsteps);
+
+/* Copy instance i's most corrected level (n_i*n_i values). Synchronises the stream.       */
+int ridc_batch_get_solution(ridc_batch b, int i, double* out, size_t count, int out_on_device);
+
+/* Sum over instances of n_i^2: the cell-updates one top-level step performs.               */
+long ridc_batch_cells(ridc_batch b);
+
+/* Autotuner: times each launch configuration (GEMM register tile 4x4 or 8x4, one or two CTAs
+ * per SM) on `nsteps` pipeline steps of this batch and keeps the fastest for later advances.
+ * Requires an initial state and leaves the state undefined: call ridc_batch_set_initial
+ * afterwards. *choice = tile variant + 2 * (CTAs per SM - 1); *best_ms = its time.          */
+int ridc_batch_autotune(ridc_batch b, long nsteps, int* choice, float* best_ms);
+
+/* Release everything the batch holds (synchronises its stream). NULL is ok.                */
+void ridc_batch_destroy(ridc_batch b);
 
 /* ---- host-only helpers (no GPU needed) ----------------------------------------------------- */
 

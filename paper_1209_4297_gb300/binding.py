@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libridc.so")
 
 KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dirichlet": 2}
-PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1}
+PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1, "fp32_solve": 2}
 KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5}
 
 
@@ -67,6 +67,14 @@ def lib() -> ctypes.CDLL:
         "ridc_set_profiling": (i, [vp, i]),
         "ridc_get_kernel_stats": (i, [vp, i, POINTER(lg), POINTER(d)]),
         "ridc_launch_count": (lg, [vp]),
+        "ridc_batch_create": (i, [i, POINTER(Problem), POINTER(Grid), POINTER(c_double),
+                                  POINTER(c_double), POINTER(c_int), vp, POINTER(vp)]),
+        "ridc_batch_set_initial": (i, [vp, POINTER(vp), i]),
+        "ridc_batch_advance": (i, [vp, lg]),
+        "ridc_batch_get_solution": (i, [vp, i, vp, sz, i]),
+        "ridc_batch_cells": (lg, [vp]),
+        "ridc_batch_autotune": (i, [vp, lg, POINTER(c_int), POINTER(ctypes.c_float)]),
+        "ridc_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -224,3 +232,74 @@ class Integrator:
 
     def launch_count(self) -> int:
         return lib().ridc_launch_count(self._h)
+
+
+class Batch:
+    """An ensemble of independent 2D Dirichlet advection-diffusion instances (include/ridc.h,
+    ridc_batch_*), advanced together by one persistent kernel launch per advance."""
+
+    def __init__(self, workloads, n_refine: int = 0, stream=None):
+        L = lib()
+        self._h = c_void_p(None)
+        n = len(workloads)
+        probs = (Problem * n)(*[Problem(KINDS[w.kind], w.a, w.b, 0.0, 0.0, PRECISIONS["fp32_solve"],
+                                        n_refine, 0) for w in workloads])
+        grids = (Grid * n)(*[Grid(2, w.n) for w in workloads])
+        nu = (c_double * n)(*[w.nu[0] for w in workloads])
+        dt = (c_double * n)(*[w.dt for w in workloads])
+        order = (c_int * n)(*[w.order for w in workloads])
+        if stream is None:
+            stream = _current_stream()
+        self.stream = stream
+        self.sides = [w.n for w in workloads]
+        _check(L.ridc_batch_create(n, probs, grids, nu, dt, order, c_void_p(stream),
+                                   byref(self._h)), "ridc_batch_create")
+
+    def close(self) -> None:
+        if self._h:
+            lib().ridc_batch_destroy(self._h)
+            self._h = c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_initial(self, u0s) -> None:
+        ptrs, dev = [], None
+        for u in u0s:
+            p, count, d = _ptr(u)
+            dev = d if dev is None else dev
+            if d != dev:
+                raise ValueError("all initial fields on the host or all on the device")
+            ptrs.append(p)
+        arr = (c_void_p * len(ptrs))(*ptrs)
+        _check(lib().ridc_batch_set_initial(self._h, arr, dev), "ridc_batch_set_initial")
+
+    def advance(self, nsteps: int) -> None:
+        _check(lib().ridc_batch_advance(self._h, nsteps), "ridc_batch_advance")
+
+    def solution(self, i: int, out=None):
+        if out is None:
+            out = np.empty((self.sides[i], self.sides[i]))
+        p, count, dev = _ptr(out)
+        _check(lib().ridc_batch_get_solution(self._h, i, c_void_p(p), count, dev),
+               "ridc_batch_get_solution")
+        return out
+
+    def cells(self) -> int:
+        return lib().ridc_batch_cells(self._h)
+
+    def autotune(self, nsteps: int = 4) -> tuple[int, float]:
+        choice = c_int(0)
+        ms = ctypes.c_float(0)
+        _check(lib().ridc_batch_autotune(self._h, nsteps, byref(choice), byref(ms)),
+               "ridc_batch_autotune")
+        return choice.value, ms.value

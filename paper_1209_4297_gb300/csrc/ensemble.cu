@@ -1,0 +1,702 @@
+// Batched ensemble: many independent RIDC instances (2D Dirichlet advection-diffusion of
+// uneven grid sizes, orders and coefficients) advanced by one persistent launch.
+//
+// Each CTA takes instances from a shared counter, largest work first (a longest-processing-
+// time order fixed at creation), and integrates its instance through every pipeline step of
+// the advance call before taking the next, so CTAs never wait on one another. Per pipeline
+// step of an instance, for every advancing level (Section III, eq. (pred) / eq. (corr)):
+//   1. right-hand side in delta form, FP64 (defect + Lagrange quadrature, Section III-C);
+//   2. (I - dt nu L) delta = r by fast diagonalisation in FP32: four FP32 SIMT GEMMs with the
+//      sine eigenvectors of the cell-centred Dirichlet Laplacian (one per side class);
+//   3. optional refinement: FP64 residual r - (I - dt nu L) delta, FP32 solve, FP64 update;
+//   4. eta = base + delta in FP64, then f^N = -a u_x - b u_y and f = f^N + nu L eta (FP64).
+// FP64 work uses the integer-based conversions and sign flips of the single-instance kernels
+// (the FP64 pipe of GB300 is narrow). Workspace is per CTA, sized for the largest instance.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "ridc_internal.h"
+
+namespace ridc {
+
+namespace {
+
+constexpr int EMaxP = 4;           // orders of the ensemble: 1..4
+constexpr int ENS_THREADS = 256;
+
+__device__ __forceinline__ float e_f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ef = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u | ((ef == 1151 && m) ? 0x400000u : 0u));
+  const unsigned long long mr = m + 0xFFFFFFFull + ((m >> 29) & 1ull);
+  return __uint_as_float(sign | (unsigned)(((unsigned long long)ef << 23) + (mr >> 29)));
+}
+
+__device__ __forceinline__ double e_f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ed = (e == 255) ? 2047ull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double(
+      (long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+// value of field x at (gy, gx) with the odd (Dirichlet) reflection for one ghost layer
+__device__ __forceinline__ double odd_at(const double* __restrict__ x, int s, int gy, int gx) {
+  bool neg = false;
+  if (gy < 0) { gy = 0; neg = !neg; }
+  if (gy >= s) { gy = s - 1; neg = !neg; }
+  if (gx < 0) { gx = 0; neg = !neg; }
+  if (gx >= s) { gx = s - 1; neg = !neg; }
+  const double v = x[gy * s + gx];
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+
+}  // namespace
+
+struct EnsInst {
+  double* eta[EMaxP];
+  double* fN[EMaxP];
+  double* F[EMaxP];
+  int cap[EMaxP];
+  int s, P, cls;
+  double dt, a2h, b2h, c_lap, c_lap4, cres, cres1;   // see ens_fill_consts
+  float dtnu;
+  long p[EMaxP];
+};
+
+struct EnsClass {
+  const float* Q;    // [s][s]  Q[x][k]
+  const float* Qt;   // [s][s]
+  const float* lam;  // [s]
+  int s;
+};
+
+struct EnsArgs {
+  EnsInst* inst;
+  int ninst;
+  const int* order;
+  int* next;
+  const EnsClass* cls;
+  const unsigned* masks[EMaxP + 1];
+  int nmask[EMaxP + 1];
+  const double* wq;   // [kMaxOrder][kMaxOrder][kMaxOrder]
+  double* r_ws;       // per CTA: [EMaxP][s_max^2] FP64
+  double* d_ws;       // per CTA: [EMaxP][s_max^2] FP64 (refinement total)
+  float* f_ws;        // per CTA: 3 x [EMaxP][s_max^2] FP32 (operand, two intermediates)
+  long ws_plane;
+  int nref;
+};
+
+// ---- block-level FP32 GEMM: C[row][m] = sum_k A[row][k] B[m][k], rows = np * s,
+// stored transposed per plane out[plane][m][row % s], optionally times
+// 1 / (1 - dtnu (lam[row % s] + lam[m])). Block tile (16 * MT) x 64, MT x 4 per thread.
+template <int MT>
+__device__ void block_sgemm(const float* __restrict__ A, const float* __restrict__ B,
+                            float* __restrict__ out, int s, int rows, const float* lam,
+                            float dtnu, bool scale, float (*As)[16 * MT + 4], float (*Bs)[64 + 4]) {
+  constexpr int BM = 16 * MT, BN = 64;
+  const int t = threadIdx.x;
+  const int tr = t & 15, tc = t >> 4;
+  const int nrt = (rows + BM - 1) / BM, nct = (s + BN - 1) / BN;
+  for (int tile = 0; tile < nrt * nct; ++tile) {
+    const int row0 = (tile / nct) * BM, col0 = (tile % nct) * BN;
+    float acc[MT][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < s; k0 += 16) {
+      __syncthreads();
+      for (int e = t; e < BM * 16; e += ENS_THREADS) {
+        const int lr = e >> 4, lk = e & 15;
+        const int gr = row0 + lr, k = k0 + lk;
+        As[lk][lr] = (gr < rows && k < s) ? A[(long)gr * s + k] : 0.f;
+      }
+      for (int e = t; e < BN * 16; e += ENS_THREADS) {
+        const int lr = e >> 4, lk = e & 15;
+        const int gc = col0 + lr, k = k0 + lk;
+        Bs[lk][lr] = (gc < s && k < s) ? B[(long)gc * s + k] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        float av[MT], bv[4];
+#pragma unroll
+        for (int i = 0; i < MT; ++i) av[i] = As[kk][tr * MT + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tc * 4 + j];
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+      const int gr = row0 + tr * MT + i;
+      if (gr >= rows) continue;
+      const int plane = gr / s, rl = gr - plane * s;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = col0 + tc * 4 + j;
+        if (m >= s) continue;
+        float v = acc[i][j];
+        if (scale) v *= __frcp_rn(1.0f - dtnu * (lam[rl] + lam[m]));
+        out[((long)plane * s + m) * s + rl] = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// FP32 fast-diagonalisation solve of np planes: df = Q ((Q^T rf Q) ./ den) Q^T
+template <int MT>
+__device__ void block_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf,
+                            float* t1, float* t2, float* df, float (*As)[16 * MT + 4],
+                            float (*Bs)[64 + 4]) {
+  const int s = C.s, rows = np * s;
+  block_sgemm<MT>(rf, C.Qt, t1, s, rows, C.lam, I.dtnu, false, As, Bs);
+  block_sgemm<MT>(t1, C.Qt, t2, s, rows, C.lam, I.dtnu, true, As, Bs);
+  block_sgemm<MT>(t2, C.Q, t1, s, rows, C.lam, I.dtnu, false, As, Bs);
+  block_sgemm<MT>(t1, C.Q, df, s, rows, C.lam, I.dtnu, false, As, Bs);
+}
+
+template <int MT>
+__global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_constant__ EnsArgs a) {
+  __shared__ float As[16][16 * MT + 4];
+  __shared__ float Bs[16][64 + 4];
+  __shared__ int item;
+  const long wp = a.ws_plane;
+  double* r = a.r_ws + (long)blockIdx.x * EMaxP * wp;
+  double* dt_tot = a.d_ws + (long)blockIdx.x * EMaxP * wp;
+  float* rf = a.f_ws + (long)blockIdx.x * 3 * EMaxP * wp;
+  float* t1 = rf + EMaxP * wp;
+  float* t2 = t1 + EMaxP * wp;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item = atomicAdd(a.next, 1);
+    __syncthreads();
+    const int w = item;
+    if (w >= a.ninst) break;
+    const int id = a.order[w];
+    EnsInst& Ig = a.inst[id];
+    const EnsInst I = Ig;
+    const EnsClass C = a.cls[I.cls];
+    const int s = I.s, P = I.P;
+    const long ss = (long)s * s;
+    long p[EMaxP];
+#pragma unroll
+    for (int j = 0; j < EMaxP; ++j) p[j] = I.p[j];
+    const unsigned* masks = a.masks[P];
+    const int nm = a.nmask[P];
+    for (int st = 0; st < nm; ++st) {
+      const unsigned mask = masks[st];
+      int lev[EMaxP], na = 0;
+#pragma unroll
+      for (int j = 0; j < EMaxP; ++j)
+        if (j < P && (mask & (1u << j))) lev[na++] = j;
+      // 1. right-hand sides (FP64) and their FP32 copies
+      for (int q = 0; q < na; ++q) {
+        const int j = lev[q];
+        const long n = p[j];
+        double* rq = r + q * ss;
+        float* fq = rf + q * ss;
+        if (j == 0) {
+          const double* F0 = I.F[0] + (n % I.cap[0]) * ss;
+          for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
+            const double v = I.dt * F0[i];
+            rq[i] = v;
+            fq[i] = e_f64_to_f32(v);
+          }
+        } else {
+          const double* ej = I.eta[j] + (n % I.cap[j]) * ss;
+          const double* fj = I.fN[j] + (n % I.cap[j]) * ss;
+          const double* ep = I.eta[j - 1] + ((n + 1) % I.cap[j - 1]) * ss;
+          const double* fp = I.fN[j - 1] + (n % I.cap[j - 1]) * ss;
+          const long b = (n + 1 - j > 0) ? n + 1 - j : 0;
+          const int m = (int)(n - b);
+          const double* w = a.wq + ((long)j * kMaxOrder + m) * kMaxOrder;
+          const double* Fb[EMaxP];
+          double wd[EMaxP];
+#pragma unroll
+          for (int k = 0; k < EMaxP; ++k) {
+            Fb[k] = (k <= j) ? I.F[j - 1] + ((b + k) % I.cap[j - 1]) * ss : nullptr;
+            wd[k] = (k <= j) ? I.dt * w[k] : 0.0;
+          }
+          for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
+            double acc = fma(I.dt, fj[i] - fp[i], ej[i] - ep[i]);
+            acc = fma(wd[0], Fb[0][i], acc);
+            acc = fma(wd[1], Fb[1][i], acc);
+            if (j >= 2) acc = fma(wd[2], Fb[2][i], acc);
+            if (j >= 3) acc = fma(wd[3], Fb[3][i], acc);
+            rq[i] = acc;
+            fq[i] = e_f64_to_f32(acc);
+          }
+        }
+      }
+      __syncthreads();
+      // 2./3. FP32 solve (the increment overwrites rf, free after the first GEMM), then
+      // refinement passes against the FP64 residual
+      const float* df = rf;
+      block_solve<MT>(C, I, na, rf, t1, t2, rf, As, Bs);
+      for (int pass = 1; pass <= a.nref; ++pass) {
+        for (long e = threadIdx.x; e < na * ss; e += ENS_THREADS)
+          dt_tot[e] = (pass == 1) ? e_f32_to_f64(df[e]) : dt_tot[e] + e_f32_to_f64(df[e]);
+        __syncthreads();
+        for (long e = threadIdx.x; e < na * ss; e += ENS_THREADS) {
+          const long q = e / ss, i = e - q * ss;
+          const int gy = (int)(i / s), gx = (int)(i - (long)gy * s);
+          const double* d = dt_tot + q * ss;
+          const double sum = (odd_at(d, s, gy - 1, gx) + odd_at(d, s, gy + 1, gx)) +
+                             (odd_at(d, s, gy, gx - 1) + odd_at(d, s, gy, gx + 1));
+          const double v = fma(I.cres, sum, fma(I.cres1, d[i], r[e]));
+          rf[e] = e_f64_to_f32(v);   // safe: df was folded into dt_tot above
+        }
+        __syncthreads();
+        block_solve<MT>(C, I, na, rf, t1, t2, rf, As, Bs);
+      }
+      // 4a. new states eta = base + delta (FP64)
+      for (int q = 0; q < na; ++q) {
+        const int j = lev[q];
+        const long n = p[j];
+        const double* base = (j == 0) ? I.eta[0] + (n % I.cap[0]) * ss
+                                      : I.eta[j - 1] + ((n + 1) % I.cap[j - 1]) * ss;
+        double* out = I.eta[j] + ((n + 1) % I.cap[j]) * ss;
+        const float* dq = df + q * ss;
+        const double* tq = dt_tot + q * ss;
+        for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
+          double d = e_f32_to_f64(dq[i]);
+          if (a.nref > 0) d += tq[i];
+          out[i] = base[i] + d;
+        }
+      }
+      __syncthreads();
+      // 4b. f^N and f of the new states
+      for (int q = 0; q < na; ++q) {
+        const int j = lev[q];
+        const long slot = ((p[j] + 1) % I.cap[j]) * ss;
+        const double* e = I.eta[j] + slot;
+        double* fN = I.fN[j] + slot;
+        double* F = I.F[j] ? I.F[j] + slot : nullptr;
+        for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
+          const int gy = (int)(i / s), gx = (int)(i - (long)gy * s);
+          const double xe = odd_at(e, s, gy, gx + 1), xw = odd_at(e, s, gy, gx - 1);
+          const double yn = odd_at(e, s, gy + 1, gx), ys = odd_at(e, s, gy - 1, gx);
+          const double fn = -I.a2h * (xe - xw) - I.b2h * (yn - ys);
+          fN[i] = fn;
+          if (F) F[i] = fma(I.c_lap, (xe + xw) + (yn + ys), fma(I.c_lap4, e[i], fn));
+        }
+      }
+      __syncthreads();
+      for (int q = 0; q < na; ++q) p[lev[q]]++;
+    }
+    if (threadIdx.x == 0)
+      for (int j = 0; j < EMaxP; ++j) Ig.p[j] = p[j];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+struct BatchCtx {
+  int n = 0;
+  cudaStream_t stream = nullptr;
+  int nref = 0;
+  std::vector<EnsInst> inst;           // host mirror (progress kept in sync on the host)
+  std::vector<int> cls_of_side;        // side -> class index
+  std::vector<EnsClass> cls;
+  std::vector<void*> allocs;
+  EnsInst* inst_dev = nullptr;
+  EnsClass* cls_dev = nullptr;
+  int* order_dev = nullptr;
+  int* next_dev = nullptr;
+  double* wq_dev = nullptr;
+  unsigned* masks_dev[EMaxP + 1] = {nullptr};
+  size_t masks_cap[EMaxP + 1] = {0};
+  double *r_ws = nullptr, *d_ws = nullptr;
+  float* f_ws = nullptr;
+  long ws_plane = 0;
+  int grid = 0, variant = 0;   // autotuned launch configuration
+  int sms = 0;
+  bool initialised = false;
+  long cells_per_step = 0;
+};
+
+static int b_alloc(BatchCtx* b, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return cuda_status(e);
+  b->allocs.push_back(*p);
+  return RIDC_OK;
+}
+
+static void b_free(BatchCtx* b) {
+  for (void* p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+}
+
+static int launch_variant(BatchCtx* b, const EnsArgs& a, int variant, int grid) {
+  if (variant == 0)
+    ensemble_kernel<4><<<grid, ENS_THREADS, 0, b->stream>>>(a);
+  else
+    ensemble_kernel<8><<<grid, ENS_THREADS, 0, b->stream>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+// plan the lock-step schedule of every order class for `nsteps` more top-level steps
+static int batch_run(BatchCtx* b, long nsteps, int variant, int grid) {
+  EnsArgs a{};
+  a.inst = b->inst_dev;
+  a.ninst = b->n;
+  a.order = b->order_dev;
+  a.next = b->next_dev;
+  a.cls = b->cls_dev;
+  a.wq = b->wq_dev;
+  a.r_ws = b->r_ws;
+  a.d_ws = b->d_ws;
+  a.f_ws = b->f_ws;
+  a.ws_plane = b->ws_plane;
+  a.nref = b->nref;
+  long newp[EMaxP + 1][EMaxP] = {{0}};
+  bool have[EMaxP + 1] = {false};
+  for (const EnsInst& I : b->inst) {
+    if (have[I.P]) continue;
+    have[I.P] = true;
+    long p[kMaxOrder] = {0};
+    for (int j = 0; j < I.P; ++j) p[j] = I.p[j];
+    const long target = p[I.P - 1] + nsteps;
+    std::vector<unsigned> masks;
+    for (;;) {
+      const unsigned m = plan_step(I.P, p, target);
+      if (!m) break;
+      masks.push_back(m);
+      for (int j = 0; j < I.P; ++j)
+        if (m & (1u << j)) p[j]++;
+    }
+    if (masks.size() > b->masks_cap[I.P]) {
+      if (b->masks_dev[I.P]) cudaFree(b->masks_dev[I.P]);
+      b->masks_dev[I.P] = nullptr;
+      b->masks_cap[I.P] = 0;
+      cudaError_t e = cudaMalloc((void**)&b->masks_dev[I.P], (masks.size() + 1) * sizeof(unsigned));
+      if (e != cudaSuccess) return cuda_status(e);
+      b->masks_cap[I.P] = masks.size();
+    }
+    if (!masks.empty()) {
+      cudaError_t e = cudaMemcpyAsync(b->masks_dev[I.P], masks.data(), masks.size() * sizeof(unsigned),
+                                      cudaMemcpyHostToDevice, b->stream);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    a.masks[I.P] = b->masks_dev[I.P];
+    a.nmask[I.P] = (int)masks.size();
+    for (int j = 0; j < I.P; ++j) newp[I.P][j] = p[j];
+  }
+  cudaError_t e = cudaMemsetAsync(b->next_dev, 0, sizeof(int), b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int rc = launch_variant(b, a, variant, grid);
+  if (rc != RIDC_OK) return rc;
+  for (EnsInst& I : b->inst)
+    for (int j = 0; j < I.P; ++j) I.p[j] = newp[I.P][j];
+  return RIDC_OK;
+}
+
+}  // namespace ridc
+
+using namespace ridc;
+
+extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const ridc_grid* grids,
+                                 const double* nu, const double* dt, const int* order, void* stream,
+                                 ridc_batch* out) {
+  if (count < 1 || !problems || !grids || !nu || !dt || !order || !out) return RIDC_ERR_ARG;
+  int nref = -1;
+  for (int i = 0; i < count; ++i) {
+    const ridc_problem& pr = problems[i];
+    if (pr.kind != RIDC_ADV_DIFF_2D_DIRICHLET) return RIDC_ERR_UNSUPPORTED;
+    if (pr.precision != RIDC_FP32_SOLVE) return RIDC_ERR_UNSUPPORTED;
+    if (pr.restart_every != 0) return RIDC_ERR_UNSUPPORTED;
+    if (pr.n_refine < 0 || pr.n_refine > 4) return RIDC_ERR_ARG;
+    if (nref >= 0 && pr.n_refine != nref) return RIDC_ERR_ARG;   // one setting per batch
+    nref = pr.n_refine;
+    if (grids[i].dim != 2 || grids[i].n < 8 || grids[i].n > 512) return RIDC_ERR_ARG;
+    if (order[i] < 1 || order[i] > EMaxP) return RIDC_ERR_UNSUPPORTED;
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i]) || !(nu[i] > 0.0) || !std::isfinite(nu[i]))
+      return RIDC_ERR_ARG;
+  }
+  BatchCtx* b = new (std::nothrow) BatchCtx();
+  if (!b) return RIDC_ERR_OOM;
+  b->n = count;
+  b->stream = (cudaStream_t)stream;
+  b->nref = nref;
+  int rc = RIDC_OK;
+  auto fail = [&](int code) {
+    b_free(b);
+    for (int p = 0; p <= EMaxP; ++p)
+      if (b->masks_dev[p]) cudaFree(b->masks_dev[p]);
+    delete b;
+    return code;
+  };
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (b->sms <= 0) b->sms = 1;
+  // side classes and their FP32 eigenvector tables
+  std::vector<int> sides;
+  for (int i = 0; i < count; ++i) sides.push_back(grids[i].n);
+  std::sort(sides.begin(), sides.end());
+  sides.erase(std::unique(sides.begin(), sides.end()), sides.end());
+  const double pi = 3.14159265358979323846;
+  int smax = 0;
+  for (int s : sides) {
+    smax = std::max(smax, s);
+    std::vector<float> Q((size_t)s * s), Qt((size_t)s * s), lam(s);
+    for (int k = 0; k < s; ++k) {
+      const long K = k + 1;
+      const double c = (K == s) ? std::sqrt(1.0 / s) : std::sqrt(2.0 / s);
+      const double sk = std::sin(pi * (double)K / (2.0 * s));
+      lam[k] = (float)(-4.0 * (double)s * s * sk * sk);
+      for (int x = 0; x < s; ++x) {
+        const long t = (K * (2L * x + 1)) % (4L * s);
+        const double q = c * std::sin(pi * (double)t / (2.0 * s));
+        Q[(size_t)x * s + k] = (float)q;
+        Qt[(size_t)k * s + x] = (float)q;
+      }
+    }
+    EnsClass C{};
+    C.s = s;
+    void* p;
+    if ((rc = b_alloc(b, &p, Q.size() * 4)) != RIDC_OK) return fail(rc);
+    cudaMemcpy(p, Q.data(), Q.size() * 4, cudaMemcpyHostToDevice);
+    C.Q = (const float*)p;
+    if ((rc = b_alloc(b, &p, Qt.size() * 4)) != RIDC_OK) return fail(rc);
+    cudaMemcpy(p, Qt.data(), Qt.size() * 4, cudaMemcpyHostToDevice);
+    C.Qt = (const float*)p;
+    if ((rc = b_alloc(b, &p, lam.size() * 4)) != RIDC_OK) return fail(rc);
+    cudaMemcpy(p, lam.data(), lam.size() * 4, cudaMemcpyHostToDevice);
+    C.lam = (const float*)p;
+    b->cls.push_back(C);
+  }
+  // instances: rings and constants
+  b->inst.resize(count);
+  for (int i = 0; i < count; ++i) {
+    EnsInst& I = b->inst[i];
+    memset(&I, 0, sizeof(I));
+    const int s = grids[i].n, P = order[i];
+    const double h = 1.0 / s;
+    I.s = s;
+    I.P = P;
+    I.cls = (int)(std::lower_bound(sides.begin(), sides.end(), s) - sides.begin());
+    I.dt = dt[i];
+    I.a2h = problems[i].a / (2.0 * h);
+    I.b2h = problems[i].b / (2.0 * h);
+    I.c_lap = nu[i] / (h * h);
+    I.c_lap4 = -4.0 * I.c_lap;
+    I.cres = dt[i] * nu[i] / (h * h);
+    I.cres1 = -(1.0 + 4.0 * I.cres);
+    I.dtnu = (float)(dt[i] * nu[i]);
+    const size_t pb = (size_t)s * s * sizeof(double);
+    for (int j = 0; j < P; ++j) {
+      I.cap[j] = (j < P - 1) ? j + 3 : 2;
+      void* p;
+      if ((rc = b_alloc(b, &p, I.cap[j] * pb)) != RIDC_OK) return fail(rc);
+      I.eta[j] = (double*)p;
+      if ((rc = b_alloc(b, &p, I.cap[j] * pb)) != RIDC_OK) return fail(rc);
+      I.fN[j] = (double*)p;
+      if (j < P - 1 || j == 0) {
+        if ((rc = b_alloc(b, &p, I.cap[j] * pb)) != RIDC_OK) return fail(rc);
+        I.F[j] = (double*)p;
+      }
+    }
+    b->cells_per_step += (long)s * s;
+  }
+  // work order: largest (order x side^3) first
+  std::vector<int> ord(count);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    const double wx = (double)order[x] * grids[x].n * grids[x].n * (double)grids[x].n;
+    const double wy = (double)order[y] * grids[y].n * grids[y].n * (double)grids[y].n;
+    return wx > wy;
+  });
+  void* p;
+  if ((rc = b_alloc(b, &p, count * sizeof(int))) != RIDC_OK) return fail(rc);
+  b->order_dev = (int*)p;
+  cudaMemcpy(p, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+  if ((rc = b_alloc(b, &p, sizeof(int))) != RIDC_OK) return fail(rc);
+  b->next_dev = (int*)p;
+  if ((rc = b_alloc(b, &p, b->cls.size() * sizeof(EnsClass))) != RIDC_OK) return fail(rc);
+  b->cls_dev = (EnsClass*)p;
+  cudaMemcpy(p, b->cls.data(), b->cls.size() * sizeof(EnsClass), cudaMemcpyHostToDevice);
+  if ((rc = b_alloc(b, &p, count * sizeof(EnsInst))) != RIDC_OK) return fail(rc);
+  b->inst_dev = (EnsInst*)p;
+  std::vector<double> wq((size_t)kMaxOrder * kMaxOrder * kMaxOrder, 0.0);
+  {
+    std::vector<double> w4((size_t)EMaxP * EMaxP * EMaxP);
+    if (ridc_quadrature_weights(EMaxP, w4.data(), w4.size()) != RIDC_OK) return fail(RIDC_ERR_ARG);
+    for (int j = 0; j < EMaxP; ++j)
+      for (int m = 0; m < EMaxP; ++m)
+        for (int i = 0; i < EMaxP; ++i)
+          wq[((size_t)j * kMaxOrder + m) * kMaxOrder + i] = w4[((size_t)j * EMaxP + m) * EMaxP + i];
+  }
+  if ((rc = b_alloc(b, &p, wq.size() * sizeof(double))) != RIDC_OK) return fail(rc);
+  b->wq_dev = (double*)p;
+  cudaMemcpy(p, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice);
+  // per-CTA workspace for at most 2 CTAs per SM
+  b->ws_plane = (long)smax * smax;
+  const long ctas = 2L * b->sms;
+  if ((rc = b_alloc(b, &p, (size_t)ctas * EMaxP * b->ws_plane * sizeof(double))) != RIDC_OK) return fail(rc);
+  b->r_ws = (double*)p;
+  if ((rc = b_alloc(b, &p, (size_t)ctas * EMaxP * b->ws_plane * sizeof(double))) != RIDC_OK) return fail(rc);
+  b->d_ws = (double*)p;
+  if ((rc = b_alloc(b, &p, (size_t)ctas * 3 * EMaxP * b->ws_plane * sizeof(float))) != RIDC_OK) return fail(rc);
+  b->f_ws = (float*)p;
+  b->grid = std::min(count, b->sms);
+  b->variant = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  *out = reinterpret_cast<ridc_batch>(b);
+  return RIDC_OK;
+}
+
+static BatchCtx* bctx(ridc_batch h) { return reinterpret_cast<BatchCtx*>(h); }
+
+extern "C" void ridc_batch_destroy(ridc_batch h) {
+  BatchCtx* b = bctx(h);
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  b_free(b);
+  for (int p = 0; p <= EMaxP; ++p)
+    if (b->masks_dev[p]) cudaFree(b->masks_dev[p]);
+  delete b;
+}
+
+// f^N and F of instance i's level-0 slot 0 (initial state), by a 1-step-free launch of the
+// same kernel machinery: a small dedicated kernel keeps it simple.
+__global__ void ens_init_kernel(EnsInst* inst, int ninst) {
+  const int i = blockIdx.y;
+  if (i >= ninst) return;
+  const EnsInst I = inst[i];
+  const int s = I.s;
+  const long ss = (long)s * s;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < ss; e += (long)gridDim.x * blockDim.x) {
+    const int gy = (int)(e / s), gx = (int)(e - (long)gy * s);
+    const double* u = I.eta[0];
+    const double xe = odd_at(u, s, gy, gx + 1), xw = odd_at(u, s, gy, gx - 1);
+    const double yn = odd_at(u, s, gy + 1, gx), ys = odd_at(u, s, gy - 1, gx);
+    const double fn = -I.a2h * (xe - xw) - I.b2h * (yn - ys);
+    const double F = fma(I.c_lap, (xe + xw) + (yn + ys), fma(I.c_lap4, u[e], fn));
+    for (int j = 0; j < I.P; ++j) {
+      if (j > 0) I.eta[j][e] = u[e];
+      I.fN[j][e] = fn;
+      if (I.F[j]) I.F[j][e] = F;
+    }
+  }
+}
+
+extern "C" int ridc_batch_set_initial(ridc_batch h, const double* const* u0, int on_device) {
+  BatchCtx* b = bctx(h);
+  if (!b || !u0) return RIDC_ERR_ARG;
+  for (int i = 0; i < b->n; ++i) {
+    if (!u0[i]) return RIDC_ERR_ARG;
+    EnsInst& I = b->inst[i];
+    const size_t bytes = (size_t)I.s * I.s * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(I.eta[0], u0[i], bytes,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int j = 0; j < EMaxP; ++j) I.p[j] = 0;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->inst_dev, b->inst.data(), b->n * sizeof(EnsInst),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  ens_init_kernel<<<dim3(64, b->n), 256, 0, b->stream>>>(b->inst_dev, b->n);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamSynchronize(b->stream);   // host sources may be reused on return
+  if (e != cudaSuccess) return cuda_status(e);
+  b->initialised = true;
+  return RIDC_OK;
+}
+
+extern "C" int ridc_batch_advance(ridc_batch h, long nsteps) {
+  BatchCtx* b = bctx(h);
+  if (!b || nsteps < 0 || !b->initialised) return RIDC_ERR_ARG;
+  if (nsteps == 0) return RIDC_OK;
+  return batch_run(b, nsteps, b->variant, b->grid);
+}
+
+extern "C" int ridc_batch_get_solution(ridc_batch h, int i, double* out, size_t count,
+                                       int out_on_device) {
+  BatchCtx* b = bctx(h);
+  if (!b || !out || i < 0 || i >= b->n || !b->initialised) return RIDC_ERR_ARG;
+  const EnsInst& I = b->inst[i];
+  if (count != (size_t)I.s * I.s) return RIDC_ERR_ARG;
+  const int top = I.P - 1;
+  const double* src = I.eta[top] + (I.p[top] % I.cap[top]) * (long)I.s * I.s;
+  cudaError_t e = cudaMemcpyAsync(out, src, count * sizeof(double),
+                                  out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!out_on_device)
+    for (size_t k = 0; k < count; ++k)
+      if (!std::isfinite(out[k])) return RIDC_ERR_NONFINITE;
+  return RIDC_OK;
+}
+
+extern "C" long ridc_batch_cells(ridc_batch h) {
+  BatchCtx* b = bctx(h);
+  return b ? b->cells_per_step : -1;
+}
+
+// Times every launch configuration (GEMM register tile 4x4 or 8x4; one or two CTAs per SM)
+// on `nsteps` pipeline steps of the real batch, keeps the fastest and reports it in *choice
+// (variant + 2 * (CTAs per SM - 1)). The state is scrambled: call ridc_batch_set_initial after.
+extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float* best_ms) {
+  BatchCtx* b = bctx(h);
+  if (!b || nsteps < 1) return RIDC_ERR_ARG;
+  if (!b->initialised) return RIDC_ERR_ARG;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bv = 0, bg = b->grid;
+  const std::vector<EnsInst> saved = b->inst;
+  for (int per_sm = 1; per_sm <= 2; ++per_sm) {
+    for (int v = 0; v < 2; ++v) {
+      const int grid = std::min(b->n, per_sm * b->sms);
+      b->inst = saved;
+      int rc = batch_run(b, nsteps, v, grid);   // warm-up
+      if (rc != RIDC_OK) return rc;
+      b->inst = saved;
+      cudaMemcpyAsync(b->inst_dev, b->inst.data(), b->n * sizeof(EnsInst), cudaMemcpyHostToDevice,
+                      b->stream);
+      cudaEventRecord(e0, b->stream);
+      rc = batch_run(b, nsteps, v, grid);
+      if (rc != RIDC_OK) return rc;
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bv = v; bg = grid; }
+      b->inst = saved;
+      cudaMemcpyAsync(b->inst_dev, b->inst.data(), b->n * sizeof(EnsInst), cudaMemcpyHostToDevice,
+                      b->stream);
+    }
+  }
+  cudaStreamSynchronize(b->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = bv;
+  b->grid = bg;
+  b->initialised = false;
+  if (choice) *choice = bv + 2 * (bg > b->sms ? 1 : 0);
+  if (best_ms) *best_ms = best;
+  return RIDC_OK;
+}
