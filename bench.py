@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -60,11 +61,11 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="ridc_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}",
@@ -189,6 +190,54 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def run_single(args):
+    """One of the other single-instance workloads, timed like the default line (whole
+    integrations, CUDA events, inputs resident): the 1D periodic workload (512 steps, FP64),
+    1024^2 Gray-Scott in FP64 (a truncated run: its 2000 steps take minutes) or the 4096^2
+    Dirichlet workload (512 steps, mixed BF16x3 with 2 refinement passes)."""
+    import torch
+
+    import inputs
+    from paper_1209_4297_gb300 import Integrator
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    if args.workload == "adv_diff_1d":
+        w, prec, nt = inputs.adv_diff_1d(), "fp64", 512
+    elif args.workload == "gray_scott_1024_fp64":
+        w, prec, nt = inputs.gray_scott_2d(n=1024, nsteps=2000), "fp64", args.nt_truncate
+    else:
+        w, prec, nt = inputs.adv_diff_2d(n=4096, nsteps=512), "mixed_bf16x3", 512
+    u0 = torch.from_numpy(w.u0).cuda()
+    it = Integrator.from_workload(w, precision=prec, n_refine=2, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        it.set_initial(u0)
+        it.advance(nt)
+    torch.cuda.synchronize()
+    times = []
+    launches0 = it.launch_count()
+    for _ in range(args.steps):
+        it.set_initial(u0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it.advance(nt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = it.launch_count() - launches0
+    it.close()
+    ms = statistics.median(times)
+    cells = (w.n if w.dim == 1 else w.n * w.n) * nt
+    line = {"metric": f"RIDC-{w.order} cell-updates/s", "value": cells / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "us_per_pipeline_step": 1e3 * ms / (nt + w.order * (w.order - 1) // 2),
+            "higher_is_better": True, "dtype": "f64" if prec == "fp64" else "f64+bf16x3(fp32 acc)",
+            "data": "synthetic", "gpu_launches": int(launches),
+            "config": {"workload": args.workload, "grid": w.n, "order": w.order,
+                       "top_level_steps": nt, "full_steps": w.nsteps, "dt": w.dt}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,13 +248,18 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=6)
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="gray_scott_2048", choices=["gray_scott_2048", "ensemble"])
+    ap.add_argument("--workload", default="gray_scott_2048",
+                    choices=["gray_scott_2048", "ensemble", "adv_diff_1d", "gray_scott_1024_fp64",
+                             "adv_diff_4096"])
     ap.add_argument("--ens-refine", type=int, default=1)
+    ap.add_argument("--nt-truncate", type=int, default=60)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload != "gray_scott_2048":
+        return run_single(args)
 
     import torch
     import torch.distributed as dist

@@ -162,11 +162,11 @@ int ridc_solve_planes_fixed(int kind, int n, const double* nu, double dt, const 
 
 /* ---- batched ensembles ----------------------------------------------------------------------- */
 
-/* Many independent instances of RIDC_ADV_DIFF_2D_DIRICHLET (uneven grid sides 8..512, orders
- * 1..4, own a, b, nu and dt) advanced together by one persistent kernel launch: each CTA
- * integrates whole instances, largest first. Solves run in FP32 (problem.precision must be
- * RIDC_FP32_SOLVE); everything else is FP64, as in ridc_create (the benchmark spec batching pattern;
- * the paper runs one instance at a time).
+/* Many independent instances of RIDC_ADV_DIFF_2D_DIRICHLET (uneven grid sides 16..512, each a
+ * multiple of 16; orders 1..4; own a, b, nu and dt) advanced together by one persistent kernel
+ * launch: each CTA integrates whole instances, largest first. Solves run in FP32
+ * (problem.precision must be RIDC_FP32_SOLVE); everything else is FP64, as in ridc_create.
+ * The paper integrates one instance at a time; batching many is this library's addition.
  *   count      : number of instances; problems, grids, nu, dt, order are arrays of `count`.
  *   n_refine   : must be the same for all instances (0..4 refinement passes).
  * Device memory belongs to the library (rings per instance, per-CTA workspace).            */

@@ -98,15 +98,25 @@ struct EnsArgs {
 
 // ---- block-level FP32 GEMM: C[row][m] = sum_k A[row][k] B[m][k], rows = np * s,
 // stored transposed per plane out[plane][m][row % s], optionally times
-// 1 / (1 - dtnu (lam[row % s] + lam[m])). Block tile (16 * MT) x 64, MT x 4 per thread.
+// 1 / (1 - dtnu (lam[row % s] + lam[m])). Block tile (16 * MT) x 64, MT x 4 per thread,
+// 16-deep K slices: the next slice is fetched into registers (float4) while the current one is
+// multiplied out of shared memory (two buffers). s must be a multiple of 16.
+template <int MT>
+struct SgemmSmem {
+  float A[2][16][16 * MT + 4];
+  float B[2][16][64 + 4];
+};
+
 template <int MT>
 __device__ void block_sgemm(const float* __restrict__ A, const float* __restrict__ B,
                             float* __restrict__ out, int s, int rows, const float* lam,
-                            float dtnu, bool scale, float (*As)[16 * MT + 4], float (*Bs)[64 + 4]) {
+                            float dtnu, bool scale, SgemmSmem<MT>& sm) {
   constexpr int BM = 16 * MT, BN = 64;
+  constexpr int AV = BM * 4 / ENS_THREADS;   // float4 loads of A per thread and slice
   const int t = threadIdx.x;
   const int tr = t & 15, tc = t >> 4;
-  const int nrt = (rows + BM - 1) / BM, nct = (s + BN - 1) / BN;
+  const int nrt = (rows + BM - 1) / BM, nct = s / BN + ((s % BN) ? 1 : 0);
+  const int KT = s / 16;
   for (int tile = 0; tile < nrt * nct; ++tile) {
     const int row0 = (tile / nct) * BM, col0 = (tile % nct) * BN;
     float acc[MT][4];
@@ -114,31 +124,58 @@ __device__ void block_sgemm(const float* __restrict__ A, const float* __restrict
     for (int i = 0; i < MT; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < s; k0 += 16) {
-      __syncthreads();
-      for (int e = t; e < BM * 16; e += ENS_THREADS) {
-        const int lr = e >> 4, lk = e & 15;
-        const int gr = row0 + lr, k = k0 + lk;
-        As[lk][lr] = (gr < rows && k < s) ? A[(long)gr * s + k] : 0.f;
+    float4 ra[AV], rb;
+    auto fetch = [&](int kt) {
+#pragma unroll
+      for (int v = 0; v < AV; ++v) {
+        const int e = t + v * ENS_THREADS;
+        const int lr = e >> 2, q = e & 3;
+        const int gr = row0 + lr;
+        ra[v] = (gr < rows) ? *reinterpret_cast<const float4*>(A + (long)gr * s + kt * 16 + q * 4)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      for (int e = t; e < BN * 16; e += ENS_THREADS) {
-        const int lr = e >> 4, lk = e & 15;
-        const int gc = col0 + lr, k = k0 + lk;
-        Bs[lk][lr] = (gc < s && k < s) ? B[(long)gc * s + k] : 0.f;
+      const int lr = t >> 2, q = t & 3;
+      const int gc = col0 + lr;
+      rb = (gc < s) ? *reinterpret_cast<const float4*>(B + (long)gc * s + kt * 16 + q * 4)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int v = 0; v < AV; ++v) {
+        const int e = t + v * ENS_THREADS;
+        const int lr = e >> 2, q = e & 3;
+        sm.A[buf][q * 4 + 0][lr] = ra[v].x;
+        sm.A[buf][q * 4 + 1][lr] = ra[v].y;
+        sm.A[buf][q * 4 + 2][lr] = ra[v].z;
+        sm.A[buf][q * 4 + 3][lr] = ra[v].w;
       }
-      __syncthreads();
+      const int lr = t >> 2, q = t & 3;
+      sm.B[buf][q * 4 + 0][lr] = rb.x;
+      sm.B[buf][q * 4 + 1][lr] = rb.y;
+      sm.B[buf][q * 4 + 2][lr] = rb.z;
+      sm.B[buf][q * 4 + 3][lr] = rb.w;
+    };
+    __syncthreads();
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    for (int kt = 0; kt < KT; ++kt) {
+      const int buf = kt & 1;
+      if (kt + 1 < KT) fetch(kt + 1);
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
         float av[MT], bv[4];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) av[i] = As[kk][tr * MT + i];
+        for (int i = 0; i < MT; ++i) av[i] = sm.A[buf][kk][tr * MT + i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tc * 4 + j];
+        for (int j = 0; j < 4; ++j) bv[j] = sm.B[buf][kk][tc * 4 + j];
 #pragma unroll
         for (int i = 0; i < MT; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
+      if (kt + 1 < KT) stash(buf ^ 1);
+      __syncthreads();
     }
 #pragma unroll
     for (int i = 0; i < MT; ++i) {
@@ -161,19 +198,17 @@ __device__ void block_sgemm(const float* __restrict__ A, const float* __restrict
 // FP32 fast-diagonalisation solve of np planes: df = Q ((Q^T rf Q) ./ den) Q^T
 template <int MT>
 __device__ void block_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf,
-                            float* t1, float* t2, float* df, float (*As)[16 * MT + 4],
-                            float (*Bs)[64 + 4]) {
+                            float* t1, float* t2, float* df, SgemmSmem<MT>& sm) {
   const int s = C.s, rows = np * s;
-  block_sgemm<MT>(rf, C.Qt, t1, s, rows, C.lam, I.dtnu, false, As, Bs);
-  block_sgemm<MT>(t1, C.Qt, t2, s, rows, C.lam, I.dtnu, true, As, Bs);
-  block_sgemm<MT>(t2, C.Q, t1, s, rows, C.lam, I.dtnu, false, As, Bs);
-  block_sgemm<MT>(t1, C.Q, df, s, rows, C.lam, I.dtnu, false, As, Bs);
+  block_sgemm<MT>(rf, C.Qt, t1, s, rows, C.lam, I.dtnu, false, sm);
+  block_sgemm<MT>(t1, C.Qt, t2, s, rows, C.lam, I.dtnu, true, sm);
+  block_sgemm<MT>(t2, C.Q, t1, s, rows, C.lam, I.dtnu, false, sm);
+  block_sgemm<MT>(t1, C.Q, df, s, rows, C.lam, I.dtnu, false, sm);
 }
 
 template <int MT>
 __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_constant__ EnsArgs a) {
-  __shared__ float As[16][16 * MT + 4];
-  __shared__ float Bs[16][64 + 4];
+  __shared__ SgemmSmem<MT> sm;
   __shared__ int item;
   const long wp = a.ws_plane;
   double* r = a.r_ws + (long)blockIdx.x * EMaxP * wp;
@@ -232,22 +267,31 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
             Fb[k] = (k <= j) ? I.F[j - 1] + ((b + k) % I.cap[j - 1]) * ss : nullptr;
             wd[k] = (k <= j) ? I.dt * w[k] : 0.0;
           }
-          for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
-            double acc = fma(I.dt, fj[i] - fp[i], ej[i] - ep[i]);
-            acc = fma(wd[0], Fb[0][i], acc);
-            acc = fma(wd[1], Fb[1][i], acc);
-            if (j >= 2) acc = fma(wd[2], Fb[2][i], acc);
-            if (j >= 3) acc = fma(wd[3], Fb[3][i], acc);
-            rq[i] = acc;
-            fq[i] = e_f64_to_f32(acc);
+          // exactly j+1 quadrature terms: no predicated-off FP64 work (it still costs pipe time)
+#define ENS_RHS_LOOP(EXTRA)                                          \
+  for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {             \
+    double acc = fma(I.dt, fj[i] - fp[i], ej[i] - ep[i]);            \
+    acc = fma(wd[0], Fb[0][i], acc);                                 \
+    acc = fma(wd[1], Fb[1][i], acc);                                 \
+    EXTRA                                                            \
+    rq[i] = acc;                                                     \
+    fq[i] = e_f64_to_f32(acc);                                       \
+  }
+          if (j == 1) {
+            ENS_RHS_LOOP()
+          } else if (j == 2) {
+            ENS_RHS_LOOP(acc = fma(wd[2], Fb[2][i], acc);)
+          } else {
+            ENS_RHS_LOOP(acc = fma(wd[2], Fb[2][i], acc); acc = fma(wd[3], Fb[3][i], acc);)
           }
+#undef ENS_RHS_LOOP
         }
       }
       __syncthreads();
       // 2./3. FP32 solve (the increment overwrites rf, free after the first GEMM), then
       // refinement passes against the FP64 residual
       const float* df = rf;
-      block_solve<MT>(C, I, na, rf, t1, t2, rf, As, Bs);
+      block_solve<MT>(C, I, na, rf, t1, t2, rf, sm);
       for (int pass = 1; pass <= a.nref; ++pass) {
         for (long e = threadIdx.x; e < na * ss; e += ENS_THREADS)
           dt_tot[e] = (pass == 1) ? e_f32_to_f64(df[e]) : dt_tot[e] + e_f32_to_f64(df[e]);
@@ -262,7 +306,7 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
           rf[e] = e_f64_to_f32(v);   // safe: df was folded into dt_tot above
         }
         __syncthreads();
-        block_solve<MT>(C, I, na, rf, t1, t2, rf, As, Bs);
+        block_solve<MT>(C, I, na, rf, t1, t2, rf, sm);
       }
       // 4a. new states eta = base + delta (FP64)
       for (int q = 0; q < na; ++q) {
@@ -424,7 +468,8 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     if (pr.n_refine < 0 || pr.n_refine > 4) return RIDC_ERR_ARG;
     if (nref >= 0 && pr.n_refine != nref) return RIDC_ERR_ARG;   // one setting per batch
     nref = pr.n_refine;
-    if (grids[i].dim != 2 || grids[i].n < 8 || grids[i].n > 512) return RIDC_ERR_ARG;
+    if (grids[i].dim != 2 || grids[i].n < 16 || grids[i].n > 512) return RIDC_ERR_ARG;
+    if (grids[i].n % 16 != 0) return RIDC_ERR_UNSUPPORTED;   // 16-deep float4 K slices
     if (order[i] < 1 || order[i] > EMaxP) return RIDC_ERR_UNSUPPORTED;
     if (!(dt[i] > 0.0) || !std::isfinite(dt[i]) || !(nu[i] > 0.0) || !std::isfinite(nu[i]))
       return RIDC_ERR_ARG;
