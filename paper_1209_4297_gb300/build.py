@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libridc.so")
-UNITS = ["api.cu", "k_1d.cu", "k_2d.cu", "gemm_tc.cu", "ensemble.cu", "solve_fixed.cu"]
+UNITS = ["api.cu", "k_1d.cu", "k_2d.cu", "gemm_sym.cu", "ensemble.cu", "solve_fixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -229,14 +229,24 @@ static int build_tables_2d(Ctx* c) {
           inv[((size_t)s * n + ky) * n + kx] = 1.0 / (1.0 - c->dt * c->nu[s] * (lam[ky] + lam[kx]));
     RIDC_TRY(upload(c, &c->inv_den, inv));
   } else {
+    // parity split: Q[n-1-x][k] = (-1)^k Q[x][k]; Qe[x'][k'] = Q[x'][2k'], Qo[x'][k'] = Q[x'][2k'+1]
+    const int H = n / 2;
+    std::vector<double> bf((size_t)n * H), bb((size_t)n * H);
+    for (int g = 0; g < 2; ++g)
+      for (int i = 0; i < H; ++i)
+        for (int j = 0; j < H; ++j) {
+          bf[((size_t)g * H + i) * H + j] = Q[(size_t)j * n + 2 * i + g];   // Qe^T / Qo^T
+          bb[((size_t)g * H + i) * H + j] = Q[(size_t)i * n + 2 * j + g];   // Qe / Qo
+        }
     std::vector<__nv_bfloat16> h, l;
-    split_bf16(Q, h, l);
-    RIDC_TRY(upload(c, &c->Qh, h));
-    RIDC_TRY(upload(c, &c->Ql, l));
-    split_bf16(Qt, h, l);
-    RIDC_TRY(upload(c, &c->Qth, h));
-    RIDC_TRY(upload(c, &c->Qtl, l));
-    std::vector<float> lf(lam.begin(), lam.end());
+    split_bf16(bf, h, l);
+    RIDC_TRY(upload(c, &c->Bfh, h));
+    RIDC_TRY(upload(c, &c->Bfl, l));
+    split_bf16(bb, h, l);
+    RIDC_TRY(upload(c, &c->Bbh, h));
+    RIDC_TRY(upload(c, &c->Bbl, l));
+    std::vector<float> lf(n);   // eigenvalues in split order: even modes, then odd modes
+    for (int k = 0; k < n; ++k) lf[k] = (float)lam[k < H ? 2 * k : 2 * (k - H) + 1];
     RIDC_TRY(upload(c, &c->lam_f, lf));
   }
   return RIDC_OK;
@@ -289,7 +299,7 @@ static void free_all(Ctx* c) {
   auto f = [](void* p) { if (p) cudaFree(p); };
   for (int j = 0; j < kMaxOrder; ++j) { f(c->eta[j]); f(c->fN[j]); f(c->Fq[j]); }
   f(c->r); f(c->delta); f(c->delta2); f(c->dinc); f(c->t1); f(c->t2); f(c->xh); f(c->xl); f(c->yh); f(c->yl);
-  f(c->Q); f(c->Qt); f(c->inv_den); f(c->lam_f); f(c->Qh); f(c->Ql); f(c->Qth); f(c->Qtl);
+  f(c->Q); f(c->Qt); f(c->inv_den); f(c->lam_f); f(c->Bfh); f(c->Bfl); f(c->Bbh); f(c->Bbl);
   f(c->tri); f(c->sched_dev); f(c->p_dev); f(c->err_dev);
   if (c->pinned) cudaFreeHost(c->pinned);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -346,15 +356,20 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
     }
     RIDC_TRY(build_tables_2d(c));
     if (c->prec == RIDC_MIXED_BF16X3) {
-      const long rows = (long)order * c->S * n;
-      RIDC_TRY(make_tensor_map(&c->tm_xh, c->xh, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_xl, c->xl, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_yh, c->yh, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_yl, c->yl, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Qh, c->Qh, n, n, 256));
-      RIDC_TRY(make_tensor_map(&c->tm_Ql, c->Ql, n, n, 256));
-      RIDC_TRY(make_tensor_map(&c->tm_Qth, c->Qth, n, n, 256));
-      RIDC_TRY(make_tensor_map(&c->tm_Qtl, c->Qtl, n, n, 256));
+      const long rows = (long)order * c->S * n, H = n / 2;
+      c->grows = rows;
+      RIDC_TRY(make_tensor_map(&c->tm_Xh, c->xh, 2 * rows, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Xl, c->xl, 2 * rows, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Yh, c->yh, 2 * rows, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Yl, c->yl, 2 * rows, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Wh, c->xh, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Wl, c->xl, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Zh, c->yh, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Zl, c->yl, rows, n, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Bfh, c->Bfh, n, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Bfl, c->Bfl, n, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Bbh, c->Bbh, n, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Bbl, c->Bbl, n, H, 128));
     }
   }
   RIDC_CUDA(cudaDeviceSynchronize());
@@ -473,7 +488,8 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
 // ------------------------------------------------------------------------------------------
 // Fast diagonalisation: delta = Q ((Q^T R Q) ./ den) Q^T, den = 1 - dt nu_s (lam_ky + lam_kx).
 // Each GEMM contracts the contiguous axis of every plane and stores its result transposed,
-// so four identical "rows x Q" products realise the two-sided transform.
+// so four "rows x Q" products realise the two-sided transform (the mixed form splits each
+// into even and odd eigenvector halves, see gemm_sym.cu).
 // The mixed form: pass 0 solves from the split right-hand side; every refinement pass forms
 // the FP64 residual of the running total (ping-pong buffers, so neighbours read a consistent
 // total) and solves for the next FP32 increment. The result stays split as total + increment.
@@ -495,14 +511,18 @@ static int solve_planes_dev(Ctx* c, int nplanes, bool rhs_split_done, DeltaParts
       RIDC_TRY(launch_residual(c, nplanes, total, c->dinc, dst));
       total = dst;
     }
-    RIDC_TRY(launch_gemm_tc(c, &c->tm_xh, &c->tm_xl, &c->tm_Qth, &c->tm_Qtl, nplanes, EPI_STORE,
-                            c->yh, c->yl, nullptr));
-    RIDC_TRY(launch_gemm_tc(c, &c->tm_yh, &c->tm_yl, &c->tm_Qth, &c->tm_Qtl, nplanes,
-                            EPI_SCALE_DEN, c->xh, c->xl, nullptr));
-    RIDC_TRY(launch_gemm_tc(c, &c->tm_xh, &c->tm_xl, &c->tm_Qh, &c->tm_Ql, nplanes, EPI_STORE,
-                            c->yh, c->yl, nullptr));
-    RIDC_TRY(launch_gemm_tc(c, &c->tm_yh, &c->tm_yl, &c->tm_Qh, &c->tm_Ql, nplanes, EPI_DELTA,
-                            nullptr, nullptr, c->dinc));
+    // x forward (parity-split operand X from the right-hand side or residual kernel) -> FP32 T
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Xh, &c->tm_Xl, &c->tm_Bfh, &c->tm_Bfl, nplanes,
+                             SYM_FWD_F32, nullptr, nullptr, c->dinc));
+    // y parity split of T -> Y;  y forward, divided by the denominators -> W
+    RIDC_TRY(launch_ybfly(c, nplanes, c->dinc));
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Yh, &c->tm_Yl, &c->tm_Bfh, &c->tm_Bfl, nplanes,
+                             SYM_FWD_DEN, c->xh, c->xl, nullptr));
+    // x inverse -> Z;  y inverse -> FP32 increment
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Wh, &c->tm_Wl, &c->tm_Bbh, &c->tm_Bbl, nplanes,
+                             SYM_BWD_SPLIT, c->yh, c->yl, nullptr));
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Zh, &c->tm_Zl, &c->tm_Bbh, &c->tm_Bbl, nplanes,
+                             SYM_BWD_F32, nullptr, nullptr, c->dinc));
   }
   *out = {total, c->dinc};
   return RIDC_OK;
@@ -590,6 +610,8 @@ static int step_2d(Ctx* c, unsigned mask) {
   ra.r = c->r;
   ra.r_hi = (c->prec == RIDC_MIXED_BF16X3) ? c->xh : nullptr;
   ra.r_lo = (c->prec == RIDC_MIXED_BF16X3) ? c->xl : nullptr;
+  ra.n = c->n;
+  ra.grows = c->grows;
   fa.nlev = na;
   RIDC_TRY(launch_rhs(c, ra));
   DeltaParts parts;

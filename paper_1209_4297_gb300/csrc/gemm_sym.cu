@@ -1,0 +1,431 @@
+// Split-precision fast-diagonalisation GEMMs on the 5th-generation tensor cores (sm_103a),
+// with the parity of the eigenvectors folded in.
+//
+// The cosine (Neumann) and sine (Dirichlet) eigenvectors of the cell-centred Laplacian obey
+// Q[N-1-x][k] = (-1)^k Q[x][k]. With H = N/2, Qe[x'][k'] = Q[x'][2k'], Qo[x'][k'] = Q[x'][2k'+1]:
+//   forward   V[2k']   = sum_{x'<H} (v[x'] + v[N-1-x']) Qe[x'][k']
+//             V[2k'+1] = sum_{x'<H} (v[x'] - v[N-1-x']) Qo[x'][k']
+//   inverse   u[x'] = E[x'] + O[x'],  u[N-1-x'] = E[x'] - O[x'],
+//             E = sum_{k'} V[2k'] Qe[x'][k'],  O = sum_{k'} V[2k'+1] Qo[x'][k']
+// so each transform is two (rows x H) x (H x H) products instead of one (rows x N) x (N x N):
+// half the tensor-core work. Spectral indices are kept in split order (even k, then odd k).
+//
+// Operands are BF16 hi/lo splits, C ~= Ah Bh + Ah Bl + Al Bh with FP32 accumulation in TMEM.
+// Every product contracts the contiguous axis of its A rows and stores transposed per plane.
+//   SYM_FWD_F32   forward, FP32 store                       (first transform, x)
+//   SYM_FWD_DEN   forward, times 1/den, BF16 hi/lo store     (second transform, y)
+//   SYM_BWD_SPLIT inverse with the E +- O butterfly, BF16    (third transform, x)
+//   SYM_BWD_F32   inverse with the E +- O butterfly, FP32    (fourth transform, y: the increment)
+//
+// Persistent: one CTA per SM over a static tile list; a TMA producer thread and an MMA thread
+// run ahead over a 3-stage ring of 64 KB stages (Ah, Al, Bh, Bl tiles of 128 x 64, 128B
+// swizzle); two TMEM buffers of 256 columns (E and O accumulators of 128 columns each) let four
+// epilogue warps drain one tile while the next is computed. Every mbarrier wait is bounded
+// (2 s of %globaltimer); on expiry the kernel flags the error, drains and frees TMEM.
+#include <cudaTypedefs.h>
+
+#include "ridc_internal.h"
+
+namespace ridc {
+
+namespace {
+
+constexpr int SY_BM = 128, SY_BN = 128, SY_BK = 64, SY_STAGES = 3;
+constexpr int SY_TILE = SY_BM * SY_BK * 2;   // 16 KB: 128 rows x 64 BF16
+constexpr int SY_STAGE = 4 * SY_TILE;        // Ah, Al, Bh, Bl
+constexpr int SY_MAXN = 4096;
+constexpr int SY_SMEM = SY_STAGES * SY_STAGE + 1024 + 1024 + SY_MAXN * 4;
+constexpr int SY_THREADS = 192;
+constexpr uint32_t SY_ACC_COLS = 256;        // per TMEM buffer: E (128) + O (128)
+constexpr unsigned long long SY_WAIT_NS = 2000000000ull;
+// kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = 128
+constexpr uint32_t SY_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SY_BN >> 3) << 17) |
+                              ((uint32_t)(SY_BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long s_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool s_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool s_wait(uint32_t bar, uint32_t parity, int* err) {
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (s_try(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      const unsigned long long t = s_gtimer();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > SY_WAIT_NS) {
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void s_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void s_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void s_tma(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int c0,
+                                      int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// K-major operand tile of 128 rows x 64 BF16 (128 B rows), 128B swizzle, 8-row groups 1 KB apart
+__device__ __forceinline__ uint64_t s_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void s_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(SY_IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void s_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void s_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void s_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void s_split(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, size_t idx) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[idx] = h;
+  lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+struct SymArgs {
+  int n, H, rows, mode, S;
+  long grows;         // row stride between the two parity groups of a forward operand
+  float* o32;
+  __nv_bfloat16* oh;
+  __nv_bfloat16* ol;
+  const float* lam;   // eigenvalues in split order
+  float dtnu[kMaxSpecies];
+  int* err;
+};
+
+// tile -> (A row base, B row base, output plane-row base, column base, group)
+struct SymTile {
+  int arow, brow, m0, c0, g;
+};
+
+__device__ __forceinline__ SymTile sym_tile(const SymArgs& a, int t, bool fwd) {
+  const int rt = a.rows / SY_BM, ct = a.H / SY_BN;
+  SymTile T;
+  if (fwd) {
+    T.g = t / (rt * ct);
+    const int r = t - T.g * rt * ct;
+    T.m0 = (r / ct) * SY_BM;
+    T.c0 = (r % ct) * SY_BN;
+    T.arow = (int)(T.g * a.grows) + T.m0;
+    T.brow = T.g * a.H + T.c0;
+  } else {
+    T.g = 0;
+    T.m0 = (t / ct) * SY_BM;
+    T.c0 = (t % ct) * SY_BN;
+    T.arow = T.m0;
+    T.brow = T.c0;
+  }
+  return T;
+}
+
+__global__ void __launch_bounds__(SY_THREADS, 1)
+    gemm_sym_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                    const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+                    const __grid_constant__ SymArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SY_STAGES * SY_STAGE);
+  // full[S], empty[S], acc_full[2], acc_empty[2], mma_done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SY_STAGES + 5);
+  float* lam_s = reinterpret_cast<float*>(smem + SY_STAGES * SY_STAGE + 1024);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool fwd = a.mode == SYM_FWD_F32 || a.mode == SYM_FWD_DEN;
+  const int nseg = fwd ? 1 : 2;
+  const int KB = a.H / SY_BK;
+  const int ntiles = (fwd ? 2 : 1) * (a.rows / SY_BM) * (a.H / SY_BN);
+  volatile int* errv = a.err;
+  auto full = [&](int s) { return s_u32(bars + s); };
+  auto empty = [&](int s) { return s_u32(bars + SY_STAGES + s); };
+  auto accf = [&](int b) { return s_u32(bars + 2 * SY_STAGES + b); };
+  auto acce = [&](int b) { return s_u32(bars + 2 * SY_STAGES + 2 + b); };
+  const uint32_t mma_done = s_u32(bars + 2 * SY_STAGES + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SY_STAGES; ++s) {
+      s_init(full(s), 1);
+      s_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      s_init(accf(b), 1);
+      s_init(acce(b), 4);
+    }
+    s_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tAh)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tAl)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tBh)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tBl)) : "memory");
+  }
+  if (a.mode == SYM_FWD_DEN)
+    for (int i = threadIdx.x; i < a.n; i += SY_THREADS) lam_s[i] = a.lam[i];
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     s_u32(tmem_slot)),
+                 "r"(2 * SY_ACC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    long issued = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok && !*errv; t += gridDim.x) {
+      const SymTile T = sym_tile(a, t, fwd);
+      for (int seg = 0; seg < nseg && ok; ++seg) {
+        const int koff = seg * a.H, brow = T.brow + seg * a.H;
+        for (int kb = 0; kb < KB; ++kb, ++issued) {
+          const int s = (int)(issued % SY_STAGES);
+          const long it = issued / SY_STAGES;
+          if (issued >= SY_STAGES && !s_wait(empty(s), (uint32_t)((it - 1) & 1), a.err)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * SY_STAGE;
+          s_expect(full(s), SY_STAGE);
+          s_tma(s_u32(st), &tAh, full(s), (fwd ? 0 : koff) + kb * SY_BK, T.arow);
+          s_tma(s_u32(st + SY_TILE), &tAl, full(s), (fwd ? 0 : koff) + kb * SY_BK, T.arow);
+          s_tma(s_u32(st + 2 * SY_TILE), &tBh, full(s), kb * SY_BK, brow);
+          s_tma(s_u32(st + 3 * SY_TILE), &tBl, full(s), kb * SY_BK, brow);
+        }
+      }
+    }
+    for (long q = issued - 1; q >= 0 && q >= issued - SY_STAGES; --q)
+      s_wait(full((int)(q % SY_STAGES)), (uint32_t)((q / SY_STAGES) & 1), a.err);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    long consumed = 0;
+    int local = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok && !*errv; t += gridDim.x, ++local) {
+      const int b = local & 1;
+      const int use = local >> 1;
+      if (use > 0 && !s_wait(acce(b), (uint32_t)((use - 1) & 1), a.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int seg = 0; seg < nseg && ok; ++seg) {
+        const uint32_t acc = tmem + (uint32_t)(b * SY_ACC_COLS + seg * SY_BN);
+        for (int kb = 0; kb < KB; ++kb, ++consumed) {
+          const int s = (int)(consumed % SY_STAGES);
+          if (!s_wait(full(s), (uint32_t)((consumed / SY_STAGES) & 1), a.err)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = s_u32(smem + s * SY_STAGE);
+          const uint64_t ah = s_desc(st), al = s_desc(st + SY_TILE);
+          const uint64_t bh = s_desc(st + 2 * SY_TILE), bl = s_desc(st + 3 * SY_TILE);
+#pragma unroll
+          for (int kk = 0; kk < SY_BK / 16; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+            s_mma(acc, ah + adv, bh + adv, (kb | kk) != 0);
+            s_mma(acc, ah + adv, bl + adv, 1);
+            s_mma(acc, al + adv, bh + adv, 1);
+          }
+          s_commit(empty(s));
+        }
+      }
+      if (!ok) break;
+      s_commit(accf(b));
+    }
+    s_commit(mma_done);
+    s_wait(mma_done, 0, a.err);
+  } else if (warp >= 2) {
+    // ---- epilogue ----
+    const int q = warp & 3;
+    const int n = a.n;
+    int local = 0;
+    for (int t = blockIdx.x; t < ntiles && !*errv; t += gridDim.x, ++local) {
+      const int b = local & 1;
+      if (!s_wait(accf(b), (uint32_t)((local >> 1) & 1), a.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const SymTile T = sym_tile(a, t, fwd);
+      const int row = T.m0 + q * 32 + lane;
+      const int plane = row / n, rl = row - plane * n;
+      const size_t pbase = (size_t)plane * n;
+      const uint32_t acc = tmem + (uint32_t)(b * SY_ACC_COLS) + ((uint32_t)(q * 32) << 16);
+      if (fwd) {
+        const int cbase = T.g * a.H + T.c0;   // output column position (split order)
+        const float dtnu = a.dtnu[plane % a.S];
+        const float den_r = (a.mode == SYM_FWD_DEN) ? 1.0f - dtnu * lam_s[rl] : 0.f;
+        for (int c = 0; c < SY_BN; c += 16) {
+          uint32_t v[16];
+          s_ld16(acc + (uint32_t)c, v);
+          s_ld_wait();
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int m = cbase + c + jj;
+            const size_t idx = (pbase + m) * n + rl;
+            float val = __uint_as_float(v[jj]);
+            if (a.mode == SYM_FWD_F32) {
+              a.o32[idx] = val;
+            } else {
+              val *= __frcp_rn(fmaf(-dtnu, lam_s[m], den_r));
+              s_split(val, a.oh, a.ol, idx);
+            }
+          }
+        }
+      } else {
+        for (int c = 0; c < SY_BN; c += 16) {
+          uint32_t e[16], o[16];
+          s_ld16(acc + (uint32_t)c, e);
+          s_ld16(acc + (uint32_t)(SY_BN + c), o);
+          s_ld_wait();
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int x = T.c0 + c + jj;
+            const float ev = __uint_as_float(e[jj]), ov = __uint_as_float(o[jj]);
+            const size_t i0 = (pbase + x) * n + rl, i1 = (pbase + (n - 1 - x)) * n + rl;
+            if (a.mode == SYM_BWD_F32) {
+              a.o32[i0] = ev + ov;
+              a.o32[i1] = ev - ov;
+            } else {
+              s_split(ev + ov, a.oh, a.ol, i0);
+              s_split(ev - ov, a.oh, a.ol, i1);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(b)) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * SY_ACC_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return RIDC_ERR_CUDA;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)SY_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? RIDC_OK : RIDC_ERR_CUDA;
+}
+
+int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
+                    const CUtensorMap* bl, int nplanes, int mode, __nv_bfloat16* oh,
+                    __nv_bfloat16* ol, float* o32) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SY_SMEM);
+    if (e != cudaSuccess) return cuda_status(e);
+    attr_done = true;
+  }
+  const int n = c->n;
+  if (n % 256 != 0 || n > SY_MAXN) return RIDC_ERR_UNSUPPORTED;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  SymArgs a{};
+  a.n = n;
+  a.H = n / 2;
+  a.rows = nplanes * n;
+  a.grows = (long)c->P * c->S * n;
+  a.mode = mode;
+  a.S = c->S;
+  a.o32 = o32;
+  a.oh = oh;
+  a.ol = ol;
+  a.lam = c->lam_f;
+  for (int s = 0; s < c->S; ++s) a.dtnu[s] = (float)(c->dt * c->nu[s]);
+  a.err = c->err_dev;
+  const bool fwd = mode == SYM_FWD_F32 || mode == SYM_FWD_DEN;
+  const int ntiles = (fwd ? 2 : 1) * (a.rows / SY_BM) * (a.H / SY_BN);
+  dim3 grid(ntiles < sms ? ntiles : sms);
+  cudaEvent_t e0;
+  prof_begin(c, RIDC_KERNEL_GEMM_TC, &e0);
+  gemm_sym_kernel<<<grid, SY_THREADS, SY_SMEM, c->stream>>>(*ah, *al, *bh, *bl, a);
+  prof_end(c, RIDC_KERNEL_GEMM_TC, e0);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace ridc

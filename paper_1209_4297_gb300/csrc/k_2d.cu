@@ -3,8 +3,9 @@
 //                    eq. (corr)), with the Lagrange quadrature of Section III-C; elementwise.
 //   finalize_kernel  eta_{n+1} = base + delta, then f^N(eta) and f = f^N + D eta of the new
 //                    state (5-point stencil from a shared-memory tile with ghost cells).
-//   residual_kernel  refinement residual r - (I - dt nu L) delta of the mixed solve, split
-//                    into BF16 hi/lo for the next tensor-core pass.
+//   residual_kernel  refinement residual r - (I - dt nu L) delta of the mixed solve, parity-
+//                    split along x and split into BF16 hi/lo for the next tensor-core pass.
+//   ybfly_kernel     parity split along y between the first and second tensor-core products.
 //   gemm_f64_kernel  FP64 fast-diagonalisation GEMM (DFMA; GB300's DMMA is slower than DFMA).
 #include "ridc_internal.h"
 
@@ -43,13 +44,6 @@ __device__ __forceinline__ double flip_sign(double v, bool neg) {
   return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
 }
 
-// BF16 hi/lo split of an FP64 value: x ~= hi + lo with |x - hi - lo| <= 2^-17 |x| (about).
-__device__ __forceinline__ void split2(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  const float f = f64_to_f32(x);
-  hi = __float2bfloat16_rn(f);
-  lo = __float2bfloat16_rn(f - __bfloat162float(hi));
-}
-
 // ---------------------------------------------------------------------------------------------
 // right-hand side: one level per blockIdx.y, S*N*N values, two per thread per iteration.
 // The quadrature has exactly NODES terms per level (a switch picks the instantiation): on
@@ -57,8 +51,42 @@ __device__ __forceinline__ void split2(double x, __nv_bfloat16& hi, __nv_bfloat1
 // be issued for absent nodes.
 // ---------------------------------------------------------------------------------------------
 template <int NODES>
+__device__ __forceinline__ double2 rhs_at(const RhsArgs& a, const RhsLevel& L,
+                                          const double2* const (&Fn)[NODES],
+                                          const double (&w)[NODES], long i) {
+  double2 acc;
+  if (L.eta_j) {
+    const double2 e = ((const double2*)L.eta_j)[i], ep = ((const double2*)L.eta_pn)[i];
+    const double2 f = ((const double2*)L.fN_j)[i], fp = ((const double2*)L.fN_p)[i];
+    acc.x = fma(a.dt, f.x - fp.x, e.x - ep.x);
+    acc.y = fma(a.dt, f.y - fp.y, e.y - ep.y);
+#pragma unroll
+    for (int k = 0; k < NODES; ++k) {
+      const double2 F = __ldg(Fn[k] + i);
+      acc.x = fma(w[k], F.x, acc.x);
+      acc.y = fma(w[k], F.y, acc.y);
+    }
+  } else {
+    const double2 F = __ldg(Fn[0] + i);
+    acc.x = w[0] * F.x;
+    acc.y = w[0] * F.y;
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void store_split2(__nv_bfloat16* hi, __nv_bfloat16* lo, long idx,
+                                             float v0, float v1) {
+  __nv_bfloat162 hv, lv;
+  hv.x = __float2bfloat16_rn(v0);
+  hv.y = __float2bfloat16_rn(v1);
+  lv.x = __float2bfloat16_rn(v0 - __bfloat162float(hv.x));
+  lv.y = __float2bfloat16_rn(v1 - __bfloat162float(hv.y));
+  *reinterpret_cast<__nv_bfloat162*>(hi + idx) = hv;
+  *reinterpret_cast<__nv_bfloat162*>(lo + idx) = lv;
+}
+
+template <int NODES>
 __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, long out_off) {
-  const long half = a.plane >> 1;
   const double2* Fn[NODES];
   double w[NODES];
 #pragma unroll
@@ -66,37 +94,36 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
     Fn[k] = (const double2*)L.Fn[k];
     w[k] = L.w[k];
   }
-  const bool corr = L.eta_j != nullptr;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < half;
-       i += (long)gridDim.x * blockDim.x) {
-    double2 acc;
-    if (corr) {
-      const double2 e = ((const double2*)L.eta_j)[i], ep = ((const double2*)L.eta_pn)[i];
-      const double2 f = ((const double2*)L.fN_j)[i], fp = ((const double2*)L.fN_p)[i];
-      acc.x = fma(a.dt, f.x - fp.x, e.x - ep.x);
-      acc.y = fma(a.dt, f.y - fp.y, e.y - ep.y);
-#pragma unroll
-      for (int k = 0; k < NODES; ++k) {
-        const double2 F = __ldg(Fn[k] + i);
-        acc.x = fma(w[k], F.x, acc.x);
-        acc.y = fma(w[k], F.y, acc.y);
-      }
-    } else {
-      const double2 F = __ldg(Fn[0] + i);
-      acc.x = w[0] * F.x;
-      acc.y = w[0] * F.y;
-    }
-    ((double2*)(a.r + out_off))[i] = acc;
-    if (a.r_hi) {
-      __nv_bfloat16 h0, l0, h1, l1;
-      split2(acc.x, h0, l0);
-      split2(acc.y, h1, l1);
-      __nv_bfloat162 hv, lv;
-      hv.x = h0; hv.y = h1;
-      lv.x = l0; lv.y = l1;
-      ((__nv_bfloat162*)(a.r_hi + out_off))[i] = hv;
-      ((__nv_bfloat162*)(a.r_lo + out_off))[i] = lv;
-    }
+  double2* r2 = (double2*)(a.r + out_off);
+  if (!a.r_hi) {
+    const long half = a.plane >> 1;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < half;
+         i += (long)gridDim.x * blockDim.x)
+      r2[i] = rhs_at<NODES>(a, L, Fn, w, i);
+    return;
+  }
+  // mixed form: each thread takes cells (2q, 2q+1) of a row and their mirrors (n-2-2q, n-1-2q)
+  // and also writes the parity split along x, v+- = v[x'] +- v[n-1-x'], of the FP32 values as
+  // BF16 hi/lo (layout [group][plane*n + y][x'], x' < n/2)
+  const int n = a.n, q4 = n / 4, H = n / 2;
+  const long nn = (long)n * n, cells = a.plane / 4;
+  const long plane0 = out_off / nn;   // first plane of this level in the stacked operand
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < cells;
+       e += (long)gridDim.x * blockDim.x) {
+    const long sp = e / ((long)n * q4), rem = e - sp * (long)n * q4;
+    const int y = (int)(rem / q4), q = (int)(rem - (long)y * q4);
+    const long rowoff = sp * nn + (long)y * n;
+    const long iL = (rowoff + 2 * q) >> 1, iR = (rowoff + n - 2 - 2 * q) >> 1;
+    const double2 vL = rhs_at<NODES>(a, L, Fn, w, iL);
+    const double2 vR = rhs_at<NODES>(a, L, Fn, w, iR);
+    r2[iL] = vL;
+    r2[iR] = vR;
+    const float l0 = f64_to_f32(vL.x), l1 = f64_to_f32(vL.y);
+    const float m1 = f64_to_f32(vR.x), m0 = f64_to_f32(vR.y);   // mirrors of 2q+1 and 2q
+    const long orow = (plane0 + sp) * n + y;
+    const long ip = orow * H + 2 * q, im = (a.grows + orow) * H + 2 * q;
+    store_split2(a.r_hi, a.r_lo, ip, l0 + m0, l1 + m1);
+    store_split2(a.r_hi, a.r_lo, im, l0 - m0, l1 - m1);
   }
 }
 
@@ -120,7 +147,7 @@ __global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArg
 }
 
 int launch_rhs(Ctx* c, const RhsArgs& a) {
-  const long half = a.plane / 2;
+  const long half = a.r_hi ? a.plane / 4 : a.plane / 2;
   long bx = (half + 255) / 256;
   const long cap = 148L * 16 / (a.nlev > 0 ? a.nlev : 1) + 1;
   if (bx > cap * 8) bx = cap * 8;
@@ -235,48 +262,70 @@ struct ResArgs {
   const double* dprev;
   const float* inc;
   double* dout;
-  __nv_bfloat16* hi;
+  __nv_bfloat16* hi;        // parity-split operand [group][plane*n + y][x'], x' < n/2
   __nv_bfloat16* lo;
   int n, S;
+  long grows;
   double c[kMaxSpecies];    // c_s
   double c1[kMaxSpecies];   // -(1 + 4 c_s)
 };
 
+// One block covers a 32 x 32 tile at x0 < n/2 and its mirror tile at n-32-x0: it forms r' on
+// both, then the parity split r'[x'] +- r'[n-1-x'] (FP32) as BF16 hi/lo.
 template <bool ODD>
 __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant__ ResArgs a) {
   __shared__ double tile[TY + 2][TX + 2];
+  __shared__ float rv[2][TY][TX + 1];
   const int n = a.n;
   const long nn = (long)n * n;
   const int p = blockIdx.z;
   const long off = (long)p * nn;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int gx = x0 + threadIdx.x;
+  const int y0 = blockIdx.y * TY;
   const bool has_d = a.dprev || a.inc;
-  if (has_d) {
-    load_tile<ODD>(tile, nullptr, a.dprev ? a.dprev + off : nullptr, a.inc ? a.inc + off : nullptr,
-                   n, x0, y0);
-    __syncthreads();
-  }
-  if (gx >= n) return;
   const int sp = p % a.S;
   const double cs = a.c[sp], c1 = a.c1[sp];
+  for (int side = 0; side < 2; ++side) {
+    const int x0 = side == 0 ? blockIdx.x * TX : n - TX - blockIdx.x * TX;
+    if (has_d) {
+      __syncthreads();
+      load_tile<ODD>(tile, nullptr, a.dprev ? a.dprev + off : nullptr,
+                     a.inc ? a.inc + off : nullptr, n, x0, y0);
+      __syncthreads();
+    }
+    const int gx = x0 + threadIdx.x;
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int ty = threadIdx.y + rr * BY + 1, gy = y0 + ty - 1;
+      if (gy >= n) break;
+      const long o = off + (long)gy * n + gx;
+      double v = a.r[o];
+      if (has_d) {
+        const int tx = threadIdx.x + 1;
+        const double d = tile[ty][tx];
+        const double sum = (tile[ty - 1][tx] + tile[ty + 1][tx]) + (tile[ty][tx - 1] + tile[ty][tx + 1]);
+        v = fma(cs, sum, fma(c1, d, v));
+        a.dout[o] = d;
+      }
+      rv[side][ty - 1][threadIdx.x] = f64_to_f32(v);
+    }
+  }
+  __syncthreads();
+  const int H = n / 2;
+  const int xp = blockIdx.x * TX + threadIdx.x;   // x' < n/2; its mirror is column 31 - tx of side 1
 #pragma unroll
   for (int rr = 0; rr < RPT; ++rr) {
-    const int ty = threadIdx.y + rr * BY + 1, gy = y0 + ty - 1;
+    const int ly = threadIdx.y + rr * BY, gy = y0 + ly;
     if (gy >= n) break;
-    const long o = off + (long)gy * n + gx;
-    double v = a.r[o];
-    if (has_d) {
-      const int tx = threadIdx.x + 1;
-      const double d = tile[ty][tx];
-      const double sum = (tile[ty - 1][tx] + tile[ty + 1][tx]) + (tile[ty][tx - 1] + tile[ty][tx + 1]);
-      v = fma(cs, sum, fma(c1, d, v));
-      a.dout[o] = d;
-    }
-    __nv_bfloat16 h, l;
-    split2(v, h, l);
-    a.hi[o] = h;
-    a.lo[o] = l;
+    const float u = rv[0][ly][threadIdx.x], m = rv[1][ly][TX - 1 - threadIdx.x];
+    const long orow = (long)p * n + gy;
+    const long ip = orow * H + xp, im = (a.grows + orow) * H + xp;
+    const float vp = u + m, vm = u - m;
+    __nv_bfloat16 h = __float2bfloat16_rn(vp);
+    a.hi[ip] = h;
+    a.lo[ip] = __float2bfloat16_rn(vp - __bfloat162float(h));
+    h = __float2bfloat16_rn(vm);
+    a.hi[im] = h;
+    a.lo[im] = __float2bfloat16_rn(vm - __bfloat162float(h));
   }
 }
 
@@ -290,17 +339,50 @@ int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, 
   a.lo = c->xl;
   a.n = c->n;
   a.S = c->S;
+  a.grows = c->grows;
   for (int s = 0; s < c->S; ++s) {
     a.c[s] = c->dt * c->nu[s] / (c->h * c->h);
     a.c1[s] = -(1.0 + 4.0 * a.c[s]);
   }
-  dim3 grid((c->n + TX - 1) / TX, (c->n + TY - 1) / TY, nplanes);
+  if (c->n % (2 * TX) != 0) return RIDC_ERR_UNSUPPORTED;
+  dim3 grid(c->n / (2 * TX), (c->n + TY - 1) / TY, nplanes);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_RESIDUAL, &e0);
   if (c->kind == RIDC_ADV_DIFF_2D_DIRICHLET)
     residual_kernel<true><<<grid, dim3(TX, BY), 0, c->stream>>>(a);
   else
     residual_kernel<false><<<grid, dim3(TX, BY), 0, c->stream>>>(a);
+  prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
+  return cuda_status(cudaGetLastError());
+}
+
+// Parity split along y of the first transform's output T[plane][k][y] (FP32):
+// Y[group][plane*n + k][y'] = T[..][y'] +- T[..][n-1-y'], y' < n/2, as BF16 hi/lo.
+__global__ void __launch_bounds__(256) ybfly_kernel(const float* __restrict__ in,
+                                                    __nv_bfloat16* __restrict__ hi,
+                                                    __nv_bfloat16* __restrict__ lo, int n,
+                                                    long rows, long grows) {
+  const int q4 = n / 4, H = n / 2;
+  const long total = rows * q4;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long row = e / q4;
+    const int q = (int)(e - row * q4);
+    const float2 L = *reinterpret_cast<const float2*>(in + row * n + 2 * q);
+    const float2 R = *reinterpret_cast<const float2*>(in + row * n + n - 2 - 2 * q);
+    const long ip = row * H + 2 * q, im = (grows + row) * H + 2 * q;
+    store_split2(hi, lo, ip, L.x + R.y, L.y + R.x);
+    store_split2(hi, lo, im, L.x - R.y, L.y - R.x);
+  }
+}
+
+int launch_ybfly(Ctx* c, int nplanes, const float* in) {
+  const long rows = (long)nplanes * c->n;
+  long blocks = (rows * (c->n / 4) + 255) / 256;
+  if (blocks > 152L * 16) blocks = 152L * 16;
+  cudaEvent_t e0;
+  prof_begin(c, RIDC_KERNEL_RESIDUAL, &e0);
+  ybfly_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(in, c->yh, c->yl, c->n, rows, c->grows);
   prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
   return cuda_status(cudaGetLastError());
 }

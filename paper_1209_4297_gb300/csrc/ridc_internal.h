@@ -37,8 +37,10 @@ struct RhsArgs {
   long plane;             // S * N * N values per level
   double dt;
   double* r;              // [nlev*S][N][N]
-  __nv_bfloat16* r_hi;    // split of r for the tensor-core solve (nullptr for FP64)
-  __nv_bfloat16* r_lo;
+  __nv_bfloat16* r_hi;    // x-butterflied split of r for the tensor-core solve (nullptr: FP64)
+  __nv_bfloat16* r_lo;    //   layout [parity group][P*S*N rows][N/2]
+  int n;
+  long grows;             // P*S*N: row stride between the parity groups
 };
 
 // New state of one advancing level: eta = base + d64 + d32, then f^N(eta) and
@@ -111,9 +113,14 @@ struct Ctx {
   double* Q = nullptr;       // [N][N]
   double* Qt = nullptr;      // [N][N], transpose of Q
   double* inv_den = nullptr; // [S][N][N]  1 / (1 - dt nu_s (lam_ky + lam_kx)), FP64 path
-  float* lam_f = nullptr;    // [N] eigenvalues (FP32, mixed path epilogue)
-  __nv_bfloat16 *Qh = nullptr, *Ql = nullptr, *Qth = nullptr, *Qtl = nullptr;
-  CUtensorMap tm_xh, tm_xl, tm_yh, tm_yl, tm_Qh, tm_Ql, tm_Qth, tm_Qtl;
+  float* lam_f = nullptr;    // [N] eigenvalues in split order (even modes, then odd), FP32
+  // parity-split eigenvector tables, BF16 hi/lo, each [N][N/2]:
+  //   Bf = [Qe^T; Qo^T] (forward products), Bb = [Qe; Qo] (inverse products)
+  __nv_bfloat16 *Bfh = nullptr, *Bfl = nullptr, *Bbh = nullptr, *Bbl = nullptr;
+  long grows = 0;            // P*S*N rows per parity group of a forward operand
+  // A operands: X, Y = [2*grows][N/2] (forward), W, Z = [grows][N] (inverse); X/W share xh/xl,
+  // Y/Z share yh/yl
+  CUtensorMap tm_Xh, tm_Xl, tm_Yh, tm_Yl, tm_Wh, tm_Wl, tm_Zh, tm_Zl, tm_Bfh, tm_Bfl, tm_Bbh, tm_Bbl;
 
   // 1D: constant factors of the cyclic tridiagonal solve
   double* tri = nullptr;     // [4][N]: c', 1/pivot, z (Sherman-Morrison), misc
@@ -155,14 +162,18 @@ int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, 
 // out = d64 + d32 elementwise over count values (either part may be nullptr)
 int launch_combine(Ctx* c, const double* d64, const float* d32, double* out, long count);
 int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi);
-int launch_gemm_tc(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
-                   const CUtensorMap* bl, int nplanes, int epi, __nv_bfloat16* oh,
-                   __nv_bfloat16* ol, float* o32);
+int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
+                    const CUtensorMap* bl, int nplanes, int mode, __nv_bfloat16* oh,
+                    __nv_bfloat16* ol, float* o32);
+// y-butterfly of the first transform's FP32 output into the second's split operand
+int launch_ybfly(Ctx* c, int nplanes, const float* in);
 int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
 int launch_1d(Ctx* c, long nsteps_pipe, int init_only);
 int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
 
-// epilogue kinds of the fast-diagonalisation GEMMs
+// epilogue kinds of the FP64 fast-diagonalisation GEMM
 enum { EPI_STORE = 0, EPI_SCALE_DEN = 1, EPI_DELTA = 2 };
+// modes of the parity-split tensor-core GEMM
+enum { SYM_FWD_F32 = 0, SYM_FWD_DEN = 1, SYM_BWD_SPLIT = 2, SYM_BWD_F32 = 3 };
 
 }  // namespace ridc
