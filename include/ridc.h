@@ -76,7 +76,8 @@ typedef struct {
 
 typedef struct {
     int dim;              /* 1 or 2; must match the kind                                     */
-    int n;                /* grid points per side: 1D n >= 8; 2D FP64 4 <= n <= 16384;
+    int n;                /* grid points per side: 1D a multiple of 32 (32 per warp lane
+                             chunk) with (2 order + 1) n <= 25600; 2D FP64 4 <= n <= 16384;
                              2D mixed: n a multiple of 256, at most 4096                      */
 } ridc_grid;
 

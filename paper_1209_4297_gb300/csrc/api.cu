@@ -253,42 +253,19 @@ static int build_tables_2d(Ctx* c) {
 }
 
 // Cyclic tridiagonal (I - dt nu L) with L the periodic second difference: diagonal 1 + 2 mu,
-// off-diagonals -mu, mu = nu dt / h^2. Sherman-Morrison splits it into a tridiagonal B plus
-// the rank-one corner term u v^T; B's Thomas factors and z = B^{-1} u are constant.
-// Layout tri[0..N): c'_i, [N..2N): 1/pivot_i, [2N..3N): z_i, [3N]: mu, [3N+1]: v_{N-1},
-// [3N+2]: 1 / (1 + v.z).
+// off-diagonals -mu, mu = nu dt / h^2. It factors as (mu/rho)(1 - rho E)(1 - rho E^-1) with the
+// cyclic shift E and rho the root in (0, 1) of mu rho^2 - (1 + 2 mu) rho + mu = 0, written
+// without cancellation as rho = 2 mu / (1 + 2 mu + sqrt(1 + 4 mu)).
+// Layout tri[0..n]: rho^k, [n+1]: 1 / (1 - rho^n), [n+2]: rho / mu, then the weights.
 static int build_tables_1d(Ctx* c) {
   const int n = c->n;
   const double mu = c->nu[0] * c->dt / (c->h * c->h);
-  const double bdiag = 1.0 + 2.0 * mu, off = -mu;
-  const double gamma = -bdiag;
-  std::vector<double> bp(n, bdiag);
-  bp[0] = bdiag - gamma;
-  bp[n - 1] = bdiag - off * off / gamma;
-  // the quadrature weight table [P][P][P] follows the solver factors
-  std::vector<double> tri((size_t)3 * n + 3 + (size_t)c->P * c->P * c->P, 0.0);
-  fill_weights(c->P, tri.data() + 3 * n + 3);
-  double* cp = tri.data();
-  double* inv = tri.data() + n;
-  double* z = tri.data() + 2 * n;
-  inv[0] = 1.0 / bp[0];
-  cp[0] = off * inv[0];
-  for (int i = 1; i < n; ++i) {
-    inv[i] = 1.0 / (bp[i] - off * cp[i - 1]);
-    cp[i] = (i < n - 1) ? off * inv[i] : 0.0;
-  }
-  // z = B^{-1} u, u = (gamma, 0, ..., 0, off)
-  std::vector<double> dp(n);
-  for (int i = 0; i < n; ++i) {
-    const double ui = (i == 0) ? gamma : (i == n - 1 ? off : 0.0);
-    dp[i] = (i == 0) ? ui * inv[0] : (ui - off * dp[i - 1]) * inv[i];
-  }
-  z[n - 1] = dp[n - 1];
-  for (int i = n - 2; i >= 0; --i) z[i] = dp[i] - cp[i] * z[i + 1];
-  const double vlast = off / gamma;   // v = (1, 0, ..., 0, off/gamma)
-  tri[3 * n] = mu;
-  tri[3 * n + 1] = vlast;
-  tri[3 * n + 2] = 1.0 / (1.0 + z[0] + vlast * z[n - 1]);
+  const double rho = 2.0 * mu / (1.0 + 2.0 * mu + std::sqrt(1.0 + 4.0 * mu));
+  std::vector<double> tri((size_t)n + 3 + (size_t)c->P * c->P * c->P, 0.0);
+  for (int k = 0; k <= n; ++k) tri[k] = std::pow(rho, (double)k);
+  tri[n + 1] = 1.0 / (1.0 - tri[n]);
+  tri[n + 2] = rho / mu;
+  fill_weights(c->P, tri.data() + n + 3);
   return upload(c, &c->tri, tri);
 }
 
@@ -389,9 +366,10 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
   for (int s = 0; s < S; ++s)
     if (!(nu[s] > 0.0) || !std::isfinite(nu[s])) return RIDC_ERR_ARG;
   if (pr->kind == RIDC_ADV_DIFF_1D_PERIODIC) {
-    if (g->dim != 1 || g->n < 8) return RIDC_ERR_ARG;
+    if (g->dim != 1 || g->n < 32) return RIDC_ERR_ARG;
     if (pr->precision != RIDC_FP64) return RIDC_ERR_UNSUPPORTED;
-    if ((2L * order + 3) * g->n > 25600) return RIDC_ERR_UNSUPPORTED;   // shared-memory bound
+    if ((2L * order + 1) * g->n > 25600) return RIDC_ERR_UNSUPPORTED;   // shared-memory bound
+    if (g->n % 32 != 0) return RIDC_ERR_UNSUPPORTED;   // one chunk per lane of a warp
   } else {
     if (g->dim != 2 || g->n < 4) return RIDC_ERR_ARG;
     if (pr->precision == RIDC_MIXED_BF16X3 && ((g->n % 256) != 0 || g->n > 4096))
@@ -490,6 +468,34 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
 // Each GEMM contracts the contiguous axis of every plane and stores its result transposed,
 // so four "rows x Q" products realise the two-sided transform (the mixed form splits each
 // into even and odd eigenvector halves, see gemm_sym.cu).
+// Mixed solve of planes [p0, p0 + np) on the handle's stream.
+static int solve_group_mixed(Ctx* c, int p0, int np, bool rhs_split_done, const double** total) {
+  const double* tot = nullptr;
+  for (int pass = 0; pass <= c->n_refine; ++pass) {
+    if (pass == 0) {
+      if (!rhs_split_done) RIDC_TRY(launch_residual(c, p0, np, nullptr, nullptr, nullptr));
+    } else {
+      double* dst = (tot == c->delta) ? c->delta2 : c->delta;
+      RIDC_TRY(launch_residual(c, p0, np, tot, c->dinc, dst));
+      tot = dst;
+    }
+    // x forward (parity-split operand X from the right-hand side or residual kernel) -> FP32 T
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Xh, &c->tm_Xl, &c->tm_Bfh, &c->tm_Bfl, p0, np,
+                             SYM_FWD_F32, nullptr, nullptr, c->dinc));
+    // y parity split of T -> Y;  y forward, divided by the denominators -> W
+    RIDC_TRY(launch_ybfly(c, p0, np, c->dinc));
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Yh, &c->tm_Yl, &c->tm_Bfh, &c->tm_Bfl, p0, np,
+                             SYM_FWD_DEN, c->xh, c->xl, nullptr));
+    // x inverse -> Z;  y inverse -> FP32 increment
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Wh, &c->tm_Wl, &c->tm_Bbh, &c->tm_Bbl, p0, np,
+                             SYM_BWD_SPLIT, c->yh, c->yl, nullptr));
+    RIDC_TRY(launch_gemm_sym(c, &c->tm_Zh, &c->tm_Zl, &c->tm_Bbh, &c->tm_Bbl, p0, np,
+                             SYM_BWD_F32, nullptr, nullptr, c->dinc));
+  }
+  *total = tot;
+  return RIDC_OK;
+}
+
 // The mixed form: pass 0 solves from the split right-hand side; every refinement pass forms
 // the FP64 residual of the running total (ping-pong buffers, so neighbours read a consistent
 // total) and solves for the next FP32 increment. The result stays split as total + increment.
@@ -503,27 +509,7 @@ static int solve_planes_dev(Ctx* c, int nplanes, bool rhs_split_done, DeltaParts
     return RIDC_OK;
   }
   const double* total = nullptr;
-  for (int pass = 0; pass <= c->n_refine; ++pass) {
-    if (pass == 0) {
-      if (!rhs_split_done) RIDC_TRY(launch_residual(c, nplanes, nullptr, nullptr, nullptr));
-    } else {
-      double* dst = (total == c->delta) ? c->delta2 : c->delta;
-      RIDC_TRY(launch_residual(c, nplanes, total, c->dinc, dst));
-      total = dst;
-    }
-    // x forward (parity-split operand X from the right-hand side or residual kernel) -> FP32 T
-    RIDC_TRY(launch_gemm_sym(c, &c->tm_Xh, &c->tm_Xl, &c->tm_Bfh, &c->tm_Bfl, nplanes,
-                             SYM_FWD_F32, nullptr, nullptr, c->dinc));
-    // y parity split of T -> Y;  y forward, divided by the denominators -> W
-    RIDC_TRY(launch_ybfly(c, nplanes, c->dinc));
-    RIDC_TRY(launch_gemm_sym(c, &c->tm_Yh, &c->tm_Yl, &c->tm_Bfh, &c->tm_Bfl, nplanes,
-                             SYM_FWD_DEN, c->xh, c->xl, nullptr));
-    // x inverse -> Z;  y inverse -> FP32 increment
-    RIDC_TRY(launch_gemm_sym(c, &c->tm_Wh, &c->tm_Wl, &c->tm_Bbh, &c->tm_Bbl, nplanes,
-                             SYM_BWD_SPLIT, c->yh, c->yl, nullptr));
-    RIDC_TRY(launch_gemm_sym(c, &c->tm_Zh, &c->tm_Zl, &c->tm_Bbh, &c->tm_Bbl, nplanes,
-                             SYM_BWD_F32, nullptr, nullptr, c->dinc));
-  }
+  RIDC_TRY(solve_group_mixed(c, 0, nplanes, rhs_split_done, &total));
   *out = {total, c->dinc};
   return RIDC_OK;
 }
@@ -611,7 +597,6 @@ static int step_2d(Ctx* c, unsigned mask) {
   ra.r_hi = (c->prec == RIDC_MIXED_BF16X3) ? c->xh : nullptr;
   ra.r_lo = (c->prec == RIDC_MIXED_BF16X3) ? c->xl : nullptr;
   ra.n = c->n;
-  ra.grows = c->grows;
   fa.nlev = na;
   RIDC_TRY(launch_rhs(c, ra));
   DeltaParts parts;

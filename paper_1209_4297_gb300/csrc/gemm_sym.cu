@@ -34,7 +34,10 @@ constexpr int SY_BM = 128, SY_BN = 128, SY_BK = 64, SY_STAGES = 3;
 constexpr int SY_TILE = SY_BM * SY_BK * 2;   // 16 KB: 128 rows x 64 BF16
 constexpr int SY_STAGE = 4 * SY_TILE;        // Ah, Al, Bh, Bl
 constexpr int SY_MAXN = 4096;
-constexpr int SY_SMEM = SY_STAGES * SY_STAGE + 1024 + 1024 + SY_MAXN * 4;
+// dynamic shared memory: stages + barriers + alignment slack, plus the eigenvalues in the
+// denominator mode only
+constexpr int SY_SMEM_BASE = SY_STAGES * SY_STAGE + 1024 + 1024;
+constexpr int SY_SMEM_MAX = SY_SMEM_BASE + SY_MAXN * 4;
 constexpr int SY_THREADS = 192;
 constexpr uint32_t SY_ACC_COLS = 256;        // per TMEM buffer: E (128) + O (128)
 constexpr unsigned long long SY_WAIT_NS = 2000000000ull;
@@ -140,8 +143,7 @@ __device__ __forceinline__ void s_split(float v, __nv_bfloat16* hi, __nv_bfloat1
 }
 
 struct SymArgs {
-  int n, H, rows, mode, S;
-  long grows;         // row stride between the two parity groups of a forward operand
+  int n, H, rows, mode, S, plane0;
   float* o32;
   __nv_bfloat16* oh;
   __nv_bfloat16* ol;
@@ -163,13 +165,15 @@ __device__ __forceinline__ SymTile sym_tile(const SymArgs& a, int t, bool fwd) {
     const int r = t - T.g * rt * ct;
     T.m0 = (r / ct) * SY_BM;
     T.c0 = (r % ct) * SY_BN;
-    T.arow = (int)(T.g * a.grows) + T.m0;
+    // forward operands are laid out [plane][parity group][row][H]
+    const int pl = a.plane0 + T.m0 / a.n;
+    T.arow = (pl * 2 + T.g) * a.n + (T.m0 - (T.m0 / a.n) * a.n);
     T.brow = T.g * a.H + T.c0;
   } else {
     T.g = 0;
     T.m0 = (t / ct) * SY_BM;
     T.c0 = (t % ct) * SY_BN;
-    T.arow = T.m0;
+    T.arow = a.plane0 * a.n + T.m0;
     T.brow = T.c0;
   }
   return T;
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const SymTile T = sym_tile(a, t, fwd);
       const int row = T.m0 + q * 32 + lane;
-      const int plane = row / n, rl = row - plane * n;
+      const int plane = a.plane0 + row / n, rl = row - (row / n) * n;
       const size_t pbase = (size_t)plane * n;
       const uint32_t acc = tmem + (uint32_t)(b * SY_ACC_COLS) + ((uint32_t)(q * 32) << 16);
       if (fwd) {
@@ -321,7 +325,8 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
             if (a.mode == SYM_FWD_F32) {
               a.o32[idx] = val;
             } else {
-              val *= __frcp_rn(fmaf(-dtnu, lam_s[m], den_r));
+              // the split keeps ~16 bits: a 2-ulp fast division is ample
+              val = __fdividef(val, fmaf(-dtnu, lam_s[m], den_r));
               s_split(val, a.oh, a.ol, idx);
             }
           }
@@ -387,12 +392,12 @@ int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int
 }
 
 int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
-                    const CUtensorMap* bl, int nplanes, int mode, __nv_bfloat16* oh,
+                    const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
                     __nv_bfloat16* ol, float* o32) {
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(gemm_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SY_SMEM);
+                                         SY_SMEM_MAX);
     if (e != cudaSuccess) return cuda_status(e);
     attr_done = true;
   }
@@ -409,7 +414,7 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
   a.n = n;
   a.H = n / 2;
   a.rows = nplanes * n;
-  a.grows = (long)c->P * c->S * n;
+  a.plane0 = plane0;
   a.mode = mode;
   a.S = c->S;
   a.o32 = o32;
@@ -421,9 +426,10 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
   const bool fwd = mode == SYM_FWD_F32 || mode == SYM_FWD_DEN;
   const int ntiles = (fwd ? 2 : 1) * (a.rows / SY_BM) * (a.H / SY_BN);
   dim3 grid(ntiles < sms ? ntiles : sms);
+  const int smem = SY_SMEM_BASE + (mode == SYM_FWD_DEN ? n * 4 : 0);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_TC, &e0);
-  gemm_sym_kernel<<<grid, SY_THREADS, SY_SMEM, c->stream>>>(*ah, *al, *bh, *bl, a);
+  gemm_sym_kernel<<<grid, SY_THREADS, smem, c->stream>>>(*ah, *al, *bh, *bl, a);
   prof_end(c, RIDC_KERNEL_GEMM_TC, e0);
   return cuda_status(cudaGetLastError());
 }

@@ -5,7 +5,7 @@
 //   r   = dt F^0_n                                                    (j = 0, eq. (pred))
 //   r   = (eta^j_n - eta^{j-1}_{n+1}) + dt (f^N(eta^j_n) - f^N(eta^{j-1}_n))
 //         + dt sum_i w[j][m][i] F^{j-1}_{b+i}                          (j >= 1, eq. (corr))
-//   solve (I - dt nu L) delta = r   (cyclic tridiagonal: Thomas + Sherman-Morrison)
+//   solve (I - dt nu L) delta = r   (cyclic tridiagonal: two warp-parallel recurrences)
 //   eta^j_{n+1} = base + delta, base = eta^0_n (j = 0) or eta^{j-1}_{n+1}
 //   f^N = -a (eta_{i+1} - eta_{i-1}) / 2h,  F = f^N + nu (eta_{i+1} - 2 eta_i + eta_{i-1}) / h^2
 // The step masks come from the host's plan of the same lock-step rule.
@@ -19,7 +19,7 @@ struct OneDArgs {
   double* F[kMaxOrder];
   int cap[kMaxOrder];
   const double* wq;        // [P][P][P]
-  const double* tri;       // c'[n], 1/pivot[n], z[n], mu, v_last, 1/(1+v.z)
+  const double* tri;       // rho^k (k = 0..n), 1/(1 - rho^n), rho/mu, then the weights
   const unsigned* sched;   // step masks
   long nsteps_pipe;
   long* p_dev;             // steps taken per level (read at start, written at the end)
@@ -37,14 +37,72 @@ __device__ __forceinline__ void eval_state(const double* e, double* fN, double* 
   }
 }
 
+// Cyclic solve of (I - dt nu L) x = r for one level by one warp. The periodic tridiagonal
+// matrix (diagonal 1 + 2mu, off-diagonals -mu) factors as (mu/rho)(1 - rho E)(1 - rho E^-1)
+// with the cyclic shift (E x)_j = x_{j+1} and rho = 2mu / (1 + 2mu + sqrt(1 + 4mu)) < 1, so
+//   z = (1 - rho E)^-1 r      : z_j = r_j + rho z_{j+1}          (backward, cyclic)
+//   x = (rho/mu)(1 - rho E^-1)^-1 z : x_j = (rho/mu) z_j + rho x_{j-1}   (forward, cyclic)
+// Each first-order recurrence is a scan: every lane runs its chunk of N/32 values, a 5-step
+// shuffle scan combines the chunk carries with weights rho^(chunk * 2^k), and the cyclic wrap
+// is exact: z_cyc_j = z_j + rho^(N-j) z_0 / (1 - rho^N), x_cyc_j = x_j + rho^(j+1) x_{N-1} / (1 - rho^N).
+// The dependent FP64 chain is about 30 operations instead of the 2N of a Thomas sweep.
+__device__ void cyclic_solve_warp(double* r, int n, const double* rp, double inv_wrap, double s) {
+  const int lane = threadIdx.x & 31;
+  const int m = n >> 5;
+  const int j0 = lane * m;
+  const double rho = rp[1];
+  // backward recurrence, local part: t_j = r_j + rho t_{j+1}, t_{j0+m} = 0
+  double t = 0.0;
+  for (int i = m - 1; i >= 0; --i) {
+    t = fma(rho, t, r[j0 + i]);
+    r[j0 + i] = t;
+  }
+  // carry C_l = z_{l m} = t_{l m} + rho^m C_{l+1}: reverse inclusive scan over the lanes
+  double C = t;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double up = __shfl_down_sync(0xffffffffu, C, d);
+    if (lane + d < 32) C = fma(rp[m * d], up, C);
+  }
+  const double z0 = __shfl_sync(0xffffffffu, C, 0) * inv_wrap;   // cyclic z_0
+  double Cnext = __shfl_down_sync(0xffffffffu, C, 1);
+  if (lane == 31) Cnext = 0.0;
+  __syncwarp();
+  for (int i = 0; i < m; ++i) {
+    const int j = j0 + i;
+    r[j] = fma(rp[n - j], z0, fma(rp[m - i], Cnext, r[j]));
+  }
+  __syncwarp();
+  // forward recurrence, local part: t_j = s z_j + rho t_{j-1}, t_{j0-1} = 0
+  t = 0.0;
+  for (int i = 0; i < m; ++i) {
+    t = fma(rho, t, s * r[j0 + i]);
+    r[j0 + i] = t;
+  }
+  // carry D_l = x_{(l+1)m-1} = t_{(l+1)m-1} + rho^m D_{l-1}: inclusive scan over the lanes
+  double D = t;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double dn = __shfl_up_sync(0xffffffffu, D, d);
+    if (lane >= d) D = fma(rp[m * d], dn, D);
+  }
+  const double xl = __shfl_sync(0xffffffffu, D, 31) * inv_wrap;  // cyclic x_{N-1}
+  double Dprev = __shfl_up_sync(0xffffffffu, D, 1);
+  if (lane == 0) Dprev = 0.0;
+  __syncwarp();
+  for (int i = 0; i < m; ++i) {
+    const int j = j0 + i;
+    r[j] = fma(rp[j + 1], xl, fma(rp[i + 1], Dprev, r[j]));
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(256) ridc1d_kernel(const __grid_constant__ OneDArgs a) {
   extern __shared__ double sm[];
   const int n = a.n, P = a.P;
   double* R = sm;                    // [P][n] right-hand sides, then solutions
   double* E = sm + (size_t)P * n;    // [P][n] new states
-  double* cp = E + (size_t)P * n;    // [n]
-  double* inv = cp + n;              // [n]
-  double* z = inv + n;               // [n]
+  double* rp = E + (size_t)P * n;    // [n+1] powers rho^k
   __shared__ long p[kMaxOrder];
   __shared__ int lev[kMaxOrder];
   __shared__ int na;
@@ -53,11 +111,11 @@ __global__ void __launch_bounds__(256) ridc1d_kernel(const __grid_constant__ One
     eval_state(a.eta[0], a.fN[0], a.F[0], n, a.a2h, a.c_lap);
     return;
   }
-  for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) cp[i] = a.tri[i];
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) rp[i] = a.tri[i];
   if (threadIdx.x < kMaxOrder) p[threadIdx.x] = a.p_dev[threadIdx.x];
-  const double mu = a.tri[3 * n], vlast = a.tri[3 * n + 1], smfac = a.tri[3 * n + 2];
+  const double inv_wrap = a.tri[n + 1], sfac = a.tri[n + 2];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
 
   for (long s = 0; s < a.nsteps_pipe; ++s) {
     const unsigned mask = a.sched[s];
@@ -93,27 +151,9 @@ __global__ void __launch_bounds__(256) ridc1d_kernel(const __grid_constant__ One
       }
     }
     __syncthreads();
-    // cyclic tridiagonal solves, one warp per level: Thomas on B, then Sherman-Morrison
-    for (int q = warp; q < na; q += (int)(blockDim.x >> 5)) {
-      double* r = R + (size_t)q * n;
-      if (lane == 0) {
-        double d = r[0] * inv[0];
-        r[0] = d;
-        for (int i = 1; i < n; ++i) {
-          d = fma(mu, d, r[i]) * inv[i];
-          r[i] = d;
-        }
-        double x = d;
-        for (int i = n - 2; i >= 0; --i) {
-          x = fma(-cp[i], x, r[i]);
-          r[i] = x;
-        }
-      }
-      __syncwarp();
-      const double sfac = fma(vlast, r[n - 1], r[0]) * smfac;
-      __syncwarp();
-      for (int i = lane; i < n; i += 32) r[i] = fma(-sfac, z[i], r[i]);
-    }
+    // cyclic solves, one warp per level
+    for (int q = warp; q < na; q += (int)(blockDim.x >> 5))
+      cyclic_solve_warp(R + (size_t)q * n, n, rp, inv_wrap, sfac);
     __syncthreads();
     // new states
     for (int q = 0; q < na; ++q) {
@@ -158,10 +198,9 @@ int launch_1d(Ctx* c, long nsteps_pipe, int init_only) {
   a.dt = c->dt;
   a.a2h = c->a / (2.0 * c->h);
   a.c_lap = c->nu[0] / (c->h * c->h);
-  // weights live next to the tridiagonal factors: uploaded once per handle
-  static_assert(sizeof(double) == 8, "");
-  a.wq = c->tri + 3 * c->n + 3;
-  const size_t smem = ((size_t)2 * c->P * c->n + 3 * (size_t)c->n) * sizeof(double);
+  // the quadrature weights follow the solver constants: uploaded once per handle
+  a.wq = c->tri + c->n + 3;
+  const size_t smem = ((size_t)2 * c->P * c->n + (size_t)c->n + 1) * sizeof(double);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(ridc1d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

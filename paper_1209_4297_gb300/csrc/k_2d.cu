@@ -104,7 +104,7 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
   }
   // mixed form: each thread takes cells (2q, 2q+1) of a row and their mirrors (n-2-2q, n-1-2q)
   // and also writes the parity split along x, v+- = v[x'] +- v[n-1-x'], of the FP32 values as
-  // BF16 hi/lo (layout [group][plane*n + y][x'], x' < n/2)
+  // BF16 hi/lo (layout [plane][group][y][x'], x' < n/2)
   const int n = a.n, q4 = n / 4, H = n / 2;
   const long nn = (long)n * n, cells = a.plane / 4;
   const long plane0 = out_off / nn;   // first plane of this level in the stacked operand
@@ -120,8 +120,8 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
     r2[iR] = vR;
     const float l0 = f64_to_f32(vL.x), l1 = f64_to_f32(vL.y);
     const float m1 = f64_to_f32(vR.x), m0 = f64_to_f32(vR.y);   // mirrors of 2q+1 and 2q
-    const long orow = (plane0 + sp) * n + y;
-    const long ip = orow * H + 2 * q, im = (a.grows + orow) * H + 2 * q;
+    const long prow = (plane0 + sp) * 2 * n + y;   // group 0 row; group 1 is n rows further
+    const long ip = prow * H + 2 * q, im = (prow + n) * H + 2 * q;
     store_split2(a.r_hi, a.r_lo, ip, l0 + m0, l1 + m1);
     store_split2(a.r_hi, a.r_lo, im, l0 - m0, l1 - m1);
   }
@@ -262,10 +262,9 @@ struct ResArgs {
   const double* dprev;
   const float* inc;
   double* dout;
-  __nv_bfloat16* hi;        // parity-split operand [group][plane*n + y][x'], x' < n/2
+  __nv_bfloat16* hi;        // parity-split operand [plane][group][y][x'], x' < n/2
   __nv_bfloat16* lo;
-  int n, S;
-  long grows;
+  int n, S, plane0;
   double c[kMaxSpecies];    // c_s
   double c1[kMaxSpecies];   // -(1 + 4 c_s)
 };
@@ -278,7 +277,7 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
   __shared__ float rv[2][TY][TX + 1];
   const int n = a.n;
   const long nn = (long)n * n;
-  const int p = blockIdx.z;
+  const int p = a.plane0 + blockIdx.z;
   const long off = (long)p * nn;
   const int y0 = blockIdx.y * TY;
   const bool has_d = a.dprev || a.inc;
@@ -317,8 +316,8 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
     const int ly = threadIdx.y + rr * BY, gy = y0 + ly;
     if (gy >= n) break;
     const float u = rv[0][ly][threadIdx.x], m = rv[1][ly][TX - 1 - threadIdx.x];
-    const long orow = (long)p * n + gy;
-    const long ip = orow * H + xp, im = (a.grows + orow) * H + xp;
+    const long prow = (long)p * 2 * n + gy;
+    const long ip = prow * H + xp, im = (prow + n) * H + xp;
     const float vp = u + m, vm = u - m;
     __nv_bfloat16 h = __float2bfloat16_rn(vp);
     a.hi[ip] = h;
@@ -329,8 +328,10 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
   }
 }
 
-int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, double* dout) {
+int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const float* inc,
+                    double* dout) {
   ResArgs a{};
+  a.plane0 = plane0;
   a.r = c->r;
   a.dprev = dprev;
   a.inc = inc;
@@ -339,7 +340,6 @@ int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, 
   a.lo = c->xl;
   a.n = c->n;
   a.S = c->S;
-  a.grows = c->grows;
   for (int s = 0; s < c->S; ++s) {
     a.c[s] = c->dt * c->nu[s] / (c->h * c->h);
     a.c1[s] = -(1.0 + 4.0 * a.c[s]);
@@ -357,11 +357,11 @@ int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, 
 }
 
 // Parity split along y of the first transform's output T[plane][k][y] (FP32):
-// Y[group][plane*n + k][y'] = T[..][y'] +- T[..][n-1-y'], y' < n/2, as BF16 hi/lo.
+// Y[plane][group][k][y'] = T[..][y'] +- T[..][n-1-y'], y' < n/2, as BF16 hi/lo.
 __global__ void __launch_bounds__(256) ybfly_kernel(const float* __restrict__ in,
                                                     __nv_bfloat16* __restrict__ hi,
                                                     __nv_bfloat16* __restrict__ lo, int n,
-                                                    long rows, long grows) {
+                                                    long rows) {
   const int q4 = n / 4, H = n / 2;
   const long total = rows * q4;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
@@ -370,19 +370,24 @@ __global__ void __launch_bounds__(256) ybfly_kernel(const float* __restrict__ in
     const int q = (int)(e - row * q4);
     const float2 L = *reinterpret_cast<const float2*>(in + row * n + 2 * q);
     const float2 R = *reinterpret_cast<const float2*>(in + row * n + n - 2 - 2 * q);
-    const long ip = row * H + 2 * q, im = (grows + row) * H + 2 * q;
+    const long pl = row / n, k = row - pl * n;
+    const long prow = pl * 2 * n + k;
+    const long ip = prow * H + 2 * q, im = (prow + n) * H + 2 * q;
     store_split2(hi, lo, ip, L.x + R.y, L.y + R.x);
     store_split2(hi, lo, im, L.x - R.y, L.y - R.x);
   }
 }
 
-int launch_ybfly(Ctx* c, int nplanes, const float* in) {
+int launch_ybfly(Ctx* c, int plane0, int nplanes, const float* in) {
   const long rows = (long)nplanes * c->n;
   long blocks = (rows * (c->n / 4) + 255) / 256;
   if (blocks > 152L * 16) blocks = 152L * 16;
+  const long r0 = (long)plane0 * c->n;
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_RESIDUAL, &e0);
-  ybfly_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(in, c->yh, c->yl, c->n, rows, c->grows);
+  // plane p's split operand starts at element p * n * n, like its unsplit form
+  ybfly_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(in + r0 * c->n, c->yh + r0 * c->n,
+                                                     c->yl + r0 * c->n, c->n, rows);
   prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
   return cuda_status(cudaGetLastError());
 }

@@ -38,9 +38,8 @@ struct RhsArgs {
   double dt;
   double* r;              // [nlev*S][N][N]
   __nv_bfloat16* r_hi;    // x-butterflied split of r for the tensor-core solve (nullptr: FP64)
-  __nv_bfloat16* r_lo;    //   layout [parity group][P*S*N rows][N/2]
+  __nv_bfloat16* r_lo;    //   layout [plane][parity group][N rows][N/2]
   int n;
-  long grows;             // P*S*N: row stride between the parity groups
 };
 
 // New state of one advancing level: eta = base + d64 + d32, then f^N(eta) and
@@ -117,9 +116,9 @@ struct Ctx {
   // parity-split eigenvector tables, BF16 hi/lo, each [N][N/2]:
   //   Bf = [Qe^T; Qo^T] (forward products), Bb = [Qe; Qo] (inverse products)
   __nv_bfloat16 *Bfh = nullptr, *Bfl = nullptr, *Bbh = nullptr, *Bbl = nullptr;
-  long grows = 0;            // P*S*N rows per parity group of a forward operand
-  // A operands: X, Y = [2*grows][N/2] (forward), W, Z = [grows][N] (inverse); X/W share xh/xl,
-  // Y/Z share yh/yl
+  long grows = 0;            // P*S*N: rows of an inverse operand (half those of a forward one)
+  // A operands: X, Y = [plane][parity group][N][N/2] (forward), W, Z = [plane][N][N] (inverse);
+  // X/W share xh/xl and Y/Z share yh/yl, each plane at the same addresses in both layouts
   CUtensorMap tm_Xh, tm_Xl, tm_Yh, tm_Yl, tm_Wh, tm_Wl, tm_Zh, tm_Zl, tm_Bfh, tm_Bfl, tm_Bbh, tm_Bbl;
 
   // 1D: constant factors of the cyclic tridiagonal solve
@@ -158,15 +157,16 @@ int launch_finalize(Ctx* c, const FinArgs& a);
 // r' = r - (I - dt nu_s L)(dprev + inc), split to BF16 hi/lo into xh/xl; the new total
 // dprev + inc is written to dout. dprev, inc may be nullptr (absent); with both absent the
 // kernel only splits r.
-int launch_residual(Ctx* c, int nplanes, const double* dprev, const float* inc, double* dout);
+int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const float* inc,
+                    double* dout);
 // out = d64 + d32 elementwise over count values (either part may be nullptr)
 int launch_combine(Ctx* c, const double* d64, const float* d32, double* out, long count);
 int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi);
 int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
-                    const CUtensorMap* bl, int nplanes, int mode, __nv_bfloat16* oh,
+                    const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
                     __nv_bfloat16* ol, float* o32);
 // y-butterfly of the first transform's FP32 output into the second's split operand
-int launch_ybfly(Ctx* c, int nplanes, const float* in);
+int launch_ybfly(Ctx* c, int plane0, int nplanes, const float* in);
 int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
 int launch_1d(Ctx* c, long nsteps_pipe, int init_only);
 int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
