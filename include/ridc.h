@@ -165,7 +165,7 @@ int ridc_solve_planes_fixed(int kind, int n, const double* nu, double dt, const 
 
 /* Many independent instances of RIDC_ADV_DIFF_2D_DIRICHLET (uneven grid sides 16..512, each a
  * multiple of 16; orders 1..4; own a, b, nu and dt) advanced together by one persistent kernel
- * launch: each CTA integrates whole instances, largest first. Solves run in FP32
+ * launch: a cluster of CTAs integrates each instance, largest instances first. Solves run in FP32
  * (problem.precision must be RIDC_FP32_SOLVE); everything else is FP64, as in ridc_create.
  * The paper integrates one instance at a time; batching many is this library's addition.
  *   count      : number of instances; problems, grids, nu, dt, order are arrays of `count`.
@@ -190,10 +190,13 @@ int ridc_batch_get_solution(ridc_batch b, int i, double* out, size_t count, int 
 /* Sum over instances of n_i^2: the cell-updates one top-level step performs.               */
 long ridc_batch_cells(ridc_batch b);
 
-/* Autotuner: times each launch configuration (GEMM register tile 4x4 or 8x4, one or two CTAs
- * per SM) on `nsteps` pipeline steps of this batch and keeps the fastest for later advances.
- * Requires an initial state and leaves the state undefined: call ridc_batch_set_initial
- * afterwards. *choice = tile variant + 2 * (CTAs per SM - 1); *best_ms = its time.          */
+/* Autotuner: picks, per grid side, the GEMM tile (64 x 64 or 128 x 128) that integrates that
+ * side's instances fastest, then the cluster size (1, 2 or 4 CTAs cooperating on each
+ * instance) and the CTAs per SM (1 or 2) that run the whole batch fastest; each trial
+ * advances `nsteps` steps of the real batch. The choice is kept for later advances. Requires
+ * an initial state and leaves the state undefined: call ridc_batch_set_initial afterwards.
+ * *choice = CTAs per SM * 256 + cluster size * 16 + bit c set when side class c (ascending
+ * sides) uses 128 x 128 tiles; *best_ms = the fastest whole-batch trial.                    */
 int ridc_batch_autotune(ridc_batch b, long nsteps, int* choice, float* best_ms);
 
 /* Release everything the batch holds (synchronises its stream). NULL is ok.                */

@@ -1,18 +1,24 @@
 // Batched ensemble: many independent RIDC instances (2D Dirichlet advection-diffusion of
 // uneven grid sizes, orders and coefficients) advanced by one persistent launch.
 //
-// Each CTA takes instances from a shared counter, largest work first (a longest-processing-
-// time order fixed at creation), and integrates its instance through every pipeline step of
-// the advance call before taking the next, so CTAs never wait on one another. Per pipeline
-// step of an instance, for every advancing level (Section III, eq. (pred) / eq. (corr)):
+// A cluster of CL CTAs (CL = 1, 2 or 4, chosen by the autotuner) takes instances from a shared
+// counter, largest work first (a longest-processing-time order fixed at creation), and
+// integrates its instance through every pipeline step of the advance call before taking the
+// next. Inside a cluster every phase is split across its CTAs (GEMM tiles, cells) and the
+// phases are separated by cluster barriers (release/acquire, so global writes of one CTA are
+// visible to the others); different clusters never wait on one another. Per pipeline step of
+// an instance, for every advancing level (Section III, eq. (pred) / eq. (corr)):
 //   1. right-hand side in delta form, FP64 (defect + Lagrange quadrature, Section III-C);
 //   2. (I - dt nu L) delta = r by fast diagonalisation in FP32: four FP32 SIMT GEMMs with the
-//      sine eigenvectors of the cell-centred Dirichlet Laplacian (one per side class);
+//      sine eigenvectors of the cell-centred Dirichlet Laplacian (one table per grid side), in
+//      64 x 64 or 128 x 128 tiles (the autotuner picks one per side);
 //   3. optional refinement: FP64 residual r - (I - dt nu L) delta, FP32 solve, FP64 update;
 //   4. eta = base + delta in FP64, then f^N = -a u_x - b u_y and f = f^N + nu L eta (FP64).
-// FP64 work uses the integer-based conversions and sign flips of the single-instance kernels
-// (the FP64 pipe of GB300 is narrow). Workspace is per CTA, sized for the largest instance.
+// FP64 work uses integer bit operations for conversions and sign flips (GB300's FP64 pipe is
+// narrow) and never issues predicated-off FP64 instructions. Workspace is per cluster, sized
+// for the largest instance.
 #include <algorithm>
+#include <cooperative_groups.h>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -68,7 +74,7 @@ struct EnsInst {
   double* F[EMaxP];
   int cap[EMaxP];
   int s, P, cls;
-  double dt, a2h, b2h, c_lap, c_lap4, cres, cres1;   // see ens_fill_consts
+  double dt, a2h, b2h, c_lap, c_lap4, cres, cres1;
   float dtnu;
   long p[EMaxP];
 };
@@ -78,82 +84,91 @@ struct EnsClass {
   const float* Qt;   // [s][s]
   const float* lam;  // [s]
   int s;
+  int variant;       // GEMM tile: 0 = 64 x 64 (4 x 4 per thread), 1 = 128 x 128 (8 x 8)
 };
 
 struct EnsArgs {
   EnsInst* inst;
-  int ninst;
+  int ntotal;         // instances in the batch (bound of the ids in `order`)
+  int ninst;          // length of `order`
   const int* order;
   int* next;
   const EnsClass* cls;
   const unsigned* masks[EMaxP + 1];
   int nmask[EMaxP + 1];
   const double* wq;   // [kMaxOrder][kMaxOrder][kMaxOrder]
-  double* r_ws;       // per CTA: [EMaxP][s_max^2] FP64
-  double* d_ws;       // per CTA: [EMaxP][s_max^2] FP64 (refinement total)
-  float* f_ws;        // per CTA: 3 x [EMaxP][s_max^2] FP32 (operand, two intermediates)
+  double* r_ws;       // per cluster: [EMaxP][s_max^2] FP64
+  double* d_ws;       // per cluster: [EMaxP][s_max^2] FP64 (refinement total)
+  float* f_ws;        // per cluster: 3 x [EMaxP][s_max^2] FP32 (operand, two intermediates)
   long ws_plane;
   int nref;
 };
 
-// ---- block-level FP32 GEMM: C[row][m] = sum_k A[row][k] B[m][k], rows = np * s,
-// stored transposed per plane out[plane][m][row % s], optionally times
-// 1 / (1 - dtnu (lam[row % s] + lam[m])). Block tile (16 * MT) x 64, MT x 4 per thread,
-// 16-deep K slices: the next slice is fetched into registers (float4) while the current one is
-// multiplied out of shared memory (two buffers). s must be a multiple of 16.
-template <int MT>
-struct SgemmSmem {
-  float A[2][16][16 * MT + 4];
-  float B[2][16][64 + 4];
+// ---- cluster-level FP32 GEMM: C[row][m] = sum_k A[row][k] B[m][k], rows = np * s, stored
+// transposed per plane out[plane][m][row % s], optionally times 1/(1 - dtnu (lam[row % s] +
+// lam[m])). Block tile (16 TM) x (16 TN), TM x TN per thread; tiles are dealt round-robin to
+// the CL CTAs of the cluster. 16-deep K slices: the next slice is fetched into registers
+// (float4) while the current one is multiplied out of shared memory (two buffers).
+template <int TM, int TN>
+struct SgSmem {
+  float A[2][16][16 * TM + 4];
+  float B[2][16][16 * TN + 4];
 };
 
-template <int MT>
+union EnsSmem {
+  SgSmem<4, 4> s44;
+  SgSmem<8, 8> s88;
+};
+
+template <int TM, int TN>
 __device__ void block_sgemm(const float* __restrict__ A, const float* __restrict__ B,
                             float* __restrict__ out, int s, int rows, const float* lam,
-                            float dtnu, bool scale, SgemmSmem<MT>& sm) {
-  constexpr int BM = 16 * MT, BN = 64;
-  constexpr int AV = BM * 4 / ENS_THREADS;   // float4 loads of A per thread and slice
+                            float dtnu, bool scale, SgSmem<TM, TN>& sm, int rank, int CL) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
+  constexpr int AV = BM * 4 / ENS_THREADS, BV = BN * 4 / ENS_THREADS;
   const int t = threadIdx.x;
   const int tr = t & 15, tc = t >> 4;
-  const int nrt = (rows + BM - 1) / BM, nct = s / BN + ((s % BN) ? 1 : 0);
+  const int nrt = (rows + BM - 1) / BM, nct = (s + BN - 1) / BN;
   const int KT = s / 16;
-  for (int tile = 0; tile < nrt * nct; ++tile) {
+  for (int tile = rank; tile < nrt * nct; tile += CL) {
     const int row0 = (tile / nct) * BM, col0 = (tile % nct) * BN;
-    float acc[MT][4];
+    float acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < MT; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    float4 ra[AV], rb;
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    float4 ra[AV], rb[BV];
     auto fetch = [&](int kt) {
 #pragma unroll
       for (int v = 0; v < AV; ++v) {
-        const int e = t + v * ENS_THREADS;
-        const int lr = e >> 2, q = e & 3;
-        const int gr = row0 + lr;
+        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3, gr = row0 + lr;
         ra[v] = (gr < rows) ? *reinterpret_cast<const float4*>(A + (long)gr * s + kt * 16 + q * 4)
                             : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      const int lr = t >> 2, q = t & 3;
-      const int gc = col0 + lr;
-      rb = (gc < s) ? *reinterpret_cast<const float4*>(B + (long)gc * s + kt * 16 + q * 4)
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int v = 0; v < BV; ++v) {
+        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3, gc = col0 + lr;
+        rb[v] = (gc < s) ? *reinterpret_cast<const float4*>(B + (long)gc * s + kt * 16 + q * 4)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     };
     auto stash = [&](int buf) {
 #pragma unroll
       for (int v = 0; v < AV; ++v) {
-        const int e = t + v * ENS_THREADS;
-        const int lr = e >> 2, q = e & 3;
+        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
         sm.A[buf][q * 4 + 0][lr] = ra[v].x;
         sm.A[buf][q * 4 + 1][lr] = ra[v].y;
         sm.A[buf][q * 4 + 2][lr] = ra[v].z;
         sm.A[buf][q * 4 + 3][lr] = ra[v].w;
       }
-      const int lr = t >> 2, q = t & 3;
-      sm.B[buf][q * 4 + 0][lr] = rb.x;
-      sm.B[buf][q * 4 + 1][lr] = rb.y;
-      sm.B[buf][q * 4 + 2][lr] = rb.z;
-      sm.B[buf][q * 4 + 3][lr] = rb.w;
+#pragma unroll
+      for (int v = 0; v < BV; ++v) {
+        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
+        sm.B[buf][q * 4 + 0][lr] = rb[v].x;
+        sm.B[buf][q * 4 + 1][lr] = rb[v].y;
+        sm.B[buf][q * 4 + 2][lr] = rb[v].z;
+        sm.B[buf][q * 4 + 3][lr] = rb[v].w;
+      }
     };
     __syncthreads();
     fetch(0);
@@ -164,65 +179,90 @@ __device__ void block_sgemm(const float* __restrict__ A, const float* __restrict
       if (kt + 1 < KT) fetch(kt + 1);
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
-        float av[MT], bv[4];
+        float av[TM], bv[TN];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) av[i] = sm.A[buf][kk][tr * MT + i];
+        for (int i = 0; i < TM; ++i) av[i] = sm.A[buf][kk][tr * TM + i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = sm.B[buf][kk][tc * 4 + j];
+        for (int j = 0; j < TN; ++j) bv[j] = sm.B[buf][kk][tc * TN + j];
 #pragma unroll
-        for (int i = 0; i < MT; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
       if (kt + 1 < KT) stash(buf ^ 1);
       __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < MT; ++i) {
-      const int gr = row0 + tr * MT + i;
+    for (int i = 0; i < TM; ++i) {
+      const int gr = row0 + tr * TM + i;
       if (gr >= rows) continue;
       const int plane = gr / s, rl = gr - plane * s;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int m = col0 + tc * 4 + j;
+      for (int j = 0; j < TN; ++j) {
+        const int m = col0 + tc * TN + j;
         if (m >= s) continue;
         float v = acc[i][j];
-        if (scale) v *= __frcp_rn(1.0f - dtnu * (lam[rl] + lam[m]));
+        if (scale) v = __fdividef(v, 1.0f - dtnu * (lam[rl] + lam[m]));
         out[((long)plane * s + m) * s + rl] = v;
       }
     }
   }
-  __syncthreads();
+}
+
+template <int CL>
+__device__ __forceinline__ void csync() {
+  if (CL > 1) cooperative_groups::this_cluster().sync();
+  else __syncthreads();
 }
 
 // FP32 fast-diagonalisation solve of np planes: df = Q ((Q^T rf Q) ./ den) Q^T
-template <int MT>
-__device__ void block_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf,
-                            float* t1, float* t2, float* df, SgemmSmem<MT>& sm) {
+template <int CL, int TM, int TN>
+__device__ void cl_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf, float* t1,
+                         float* t2, float* df, SgSmem<TM, TN>& sm, int rank) {
   const int s = C.s, rows = np * s;
-  block_sgemm<MT>(rf, C.Qt, t1, s, rows, C.lam, I.dtnu, false, sm);
-  block_sgemm<MT>(t1, C.Qt, t2, s, rows, C.lam, I.dtnu, true, sm);
-  block_sgemm<MT>(t2, C.Q, t1, s, rows, C.lam, I.dtnu, false, sm);
-  block_sgemm<MT>(t1, C.Q, df, s, rows, C.lam, I.dtnu, false, sm);
+  block_sgemm<TM, TN>(rf, C.Qt, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
+  csync<CL>();
+  block_sgemm<TM, TN>(t1, C.Qt, t2, s, rows, C.lam, I.dtnu, true, sm, rank, CL);
+  csync<CL>();
+  block_sgemm<TM, TN>(t2, C.Q, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
+  csync<CL>();
+  block_sgemm<TM, TN>(t1, C.Q, df, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
+  csync<CL>();
 }
 
-template <int MT>
-__global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_constant__ EnsArgs a) {
-  __shared__ SgemmSmem<MT> sm;
+template <int CL>
+__device__ __forceinline__ void solve_any(const EnsClass& C, const EnsInst& I, int np,
+                                          const float* rf, float* t1, float* t2, float* df,
+                                          EnsSmem& sm, int rank) {
+  if (C.variant == 1) cl_solve<CL, 8, 8>(C, I, np, rf, t1, t2, df, sm.s88, rank);
+  else cl_solve<CL, 4, 4>(C, I, np, rf, t1, t2, df, sm.s44, rank);
+}
+
+template <int CL>
+__global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_constant__ EnsArgs a) {
+  __shared__ EnsSmem sm;
   __shared__ int item;
+  const int rank = (CL > 1) ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+  const long cid = blockIdx.x / CL;
   const long wp = a.ws_plane;
-  double* r = a.r_ws + (long)blockIdx.x * EMaxP * wp;
-  double* dt_tot = a.d_ws + (long)blockIdx.x * EMaxP * wp;
-  float* rf = a.f_ws + (long)blockIdx.x * 3 * EMaxP * wp;
+  double* r = a.r_ws + cid * EMaxP * wp;
+  double* dt_tot = a.d_ws + cid * EMaxP * wp;
+  float* rf = a.f_ws + cid * 3 * EMaxP * wp;
   float* t1 = rf + EMaxP * wp;
   float* t2 = t1 + EMaxP * wp;
+  const long g0 = (long)rank * ENS_THREADS + threadIdx.x, gs = (long)CL * ENS_THREADS;
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) item = atomicAdd(a.next, 1);
-    __syncthreads();
-    const int w = item;
+    if (rank == 0 && threadIdx.x == 0) item = atomicAdd(a.next, 1);
+    csync<CL>();
+    int w;
+    if (CL > 1) w = *cooperative_groups::this_cluster().map_shared_rank(&item, 0);
+    else w = item;
+    // every CTA must have read rank 0's `item` before any CTA of the cluster may exit (its
+    // shared memory goes away) or take the next instance
+    csync<CL>();
     if (w >= a.ninst) break;
     const int id = a.order[w];
+    if (id < 0 || id >= a.ntotal) continue;   // cannot happen: host-built list; never index past it
     EnsInst& Ig = a.inst[id];
     const EnsInst I = Ig;
     const EnsClass C = a.cls[I.cls];
@@ -247,7 +287,7 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
         float* fq = rf + q * ss;
         if (j == 0) {
           const double* F0 = I.F[0] + (n % I.cap[0]) * ss;
-          for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
+          for (long i = g0; i < ss; i += gs) {
             const double v = I.dt * F0[i];
             rq[i] = v;
             fq[i] = e_f64_to_f32(v);
@@ -269,7 +309,7 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
           }
           // exactly j+1 quadrature terms: no predicated-off FP64 work (it still costs pipe time)
 #define ENS_RHS_LOOP(EXTRA)                                          \
-  for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {             \
+  for (long i = g0; i < ss; i += gs) {                               \
     double acc = fma(I.dt, fj[i] - fp[i], ej[i] - ep[i]);            \
     acc = fma(wd[0], Fb[0][i], acc);                                 \
     acc = fma(wd[1], Fb[1][i], acc);                                 \
@@ -287,16 +327,16 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
 #undef ENS_RHS_LOOP
         }
       }
-      __syncthreads();
+      csync<CL>();
       // 2./3. FP32 solve (the increment overwrites rf, free after the first GEMM), then
       // refinement passes against the FP64 residual
       const float* df = rf;
-      block_solve<MT>(C, I, na, rf, t1, t2, rf, sm);
+      solve_any<CL>(C, I, na, rf, t1, t2, rf, sm, rank);
       for (int pass = 1; pass <= a.nref; ++pass) {
-        for (long e = threadIdx.x; e < na * ss; e += ENS_THREADS)
+        for (long e = g0; e < na * ss; e += gs)
           dt_tot[e] = (pass == 1) ? e_f32_to_f64(df[e]) : dt_tot[e] + e_f32_to_f64(df[e]);
-        __syncthreads();
-        for (long e = threadIdx.x; e < na * ss; e += ENS_THREADS) {
+        csync<CL>();
+        for (long e = g0; e < na * ss; e += gs) {
           const long q = e / ss, i = e - q * ss;
           const int gy = (int)(i / s), gx = (int)(i - (long)gy * s);
           const double* d = dt_tot + q * ss;
@@ -305,8 +345,8 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
           const double v = fma(I.cres, sum, fma(I.cres1, d[i], r[e]));
           rf[e] = e_f64_to_f32(v);   // safe: df was folded into dt_tot above
         }
-        __syncthreads();
-        block_solve<MT>(C, I, na, rf, t1, t2, rf, sm);
+        csync<CL>();
+        solve_any<CL>(C, I, na, rf, t1, t2, rf, sm, rank);
       }
       // 4a. new states eta = base + delta (FP64)
       for (int q = 0; q < na; ++q) {
@@ -317,13 +357,13 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
         double* out = I.eta[j] + ((n + 1) % I.cap[j]) * ss;
         const float* dq = df + q * ss;
         const double* tq = dt_tot + q * ss;
-        for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
-          double d = e_f32_to_f64(dq[i]);
-          if (a.nref > 0) d += tq[i];
-          out[i] = base[i] + d;
+        if (a.nref > 0) {
+          for (long i = g0; i < ss; i += gs) out[i] = base[i] + (e_f32_to_f64(dq[i]) + tq[i]);
+        } else {
+          for (long i = g0; i < ss; i += gs) out[i] = base[i] + e_f32_to_f64(dq[i]);
         }
       }
-      __syncthreads();
+      csync<CL>();
       // 4b. f^N and f of the new states
       for (int q = 0; q < na; ++q) {
         const int j = lev[q];
@@ -331,7 +371,7 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
         const double* e = I.eta[j] + slot;
         double* fN = I.fN[j] + slot;
         double* F = I.F[j] ? I.F[j] + slot : nullptr;
-        for (long i = threadIdx.x; i < ss; i += ENS_THREADS) {
+        for (long i = g0; i < ss; i += gs) {
           const int gy = (int)(i / s), gx = (int)(i - (long)gy * s);
           const double xe = odd_at(e, s, gy, gx + 1), xw = odd_at(e, s, gy, gx - 1);
           const double yn = odd_at(e, s, gy + 1, gx), ys = odd_at(e, s, gy - 1, gx);
@@ -340,10 +380,10 @@ __global__ void __launch_bounds__(ENS_THREADS) ensemble_kernel(const __grid_cons
           if (F) F[i] = fma(I.c_lap, (xe + xw) + (yn + ys), fma(I.c_lap4, e[i], fn));
         }
       }
-      __syncthreads();
+      csync<CL>();
       for (int q = 0; q < na; ++q) p[lev[q]]++;
     }
-    if (threadIdx.x == 0)
+    if (rank == 0 && threadIdx.x == 0)
       for (int j = 0; j < EMaxP; ++j) Ig.p[j] = p[j];
   }
 }
@@ -356,12 +396,12 @@ struct BatchCtx {
   cudaStream_t stream = nullptr;
   int nref = 0;
   std::vector<EnsInst> inst;           // host mirror (progress kept in sync on the host)
-  std::vector<int> cls_of_side;        // side -> class index
   std::vector<EnsClass> cls;
   std::vector<void*> allocs;
   EnsInst* inst_dev = nullptr;
   EnsClass* cls_dev = nullptr;
   int* order_dev = nullptr;
+  int* sub_dev = nullptr;              // scratch instance list of the autotuner
   int* next_dev = nullptr;
   double* wq_dev = nullptr;
   unsigned* masks_dev[EMaxP + 1] = {nullptr};
@@ -369,7 +409,8 @@ struct BatchCtx {
   double *r_ws = nullptr, *d_ws = nullptr;
   float* f_ws = nullptr;
   long ws_plane = 0;
-  int grid = 0, variant = 0;   // autotuned launch configuration
+  int cl = 1;                          // autotuned cluster size (CTAs per instance)
+  int per_sm = 1;                      // autotuned CTAs per SM
   int sms = 0;
   bool initialised = false;
   long cells_per_step = 0;
@@ -387,20 +428,36 @@ static void b_free(BatchCtx* b) {
   b->allocs.clear();
 }
 
-static int launch_variant(BatchCtx* b, const EnsArgs& a, int variant, int grid) {
-  if (variant == 0)
-    ensemble_kernel<4><<<grid, ENS_THREADS, 0, b->stream>>>(a);
-  else
-    ensemble_kernel<8><<<grid, ENS_THREADS, 0, b->stream>>>(a);
-  return cuda_status(cudaGetLastError());
+template <int CL>
+static int launch_cl(BatchCtx* b, const EnsArgs& a, int grid) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(ENS_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cuda_status(cudaLaunchKernelEx(&cfg, ensemble_kernel<CL>, a));
 }
 
-// plan the lock-step schedule of every order class for `nsteps` more top-level steps
-static int batch_run(BatchCtx* b, long nsteps, int variant, int grid) {
+// grid for cluster size cl and `per_sm` CTAs per SM (workspace holds 2 * sms clusters)
+static int grid_for(const BatchCtx* b, int cl, int per_sm, int count) {
+  const int clusters = std::max(1, std::min(count, per_sm * b->sms / cl));
+  return clusters * cl;
+}
+
+// Advance the instances listed in `order` (count of them) by nsteps top-level steps.
+static int batch_run(BatchCtx* b, long nsteps, int cl, int per_sm, const int* order, int count) {
   EnsArgs a{};
   a.inst = b->inst_dev;
-  a.ninst = b->n;
-  a.order = b->order_dev;
+  a.ntotal = b->n;
+  a.ninst = count;
+  a.order = order;
   a.next = b->next_dev;
   a.cls = b->cls_dev;
   a.wq = b->wq_dev;
@@ -444,7 +501,11 @@ static int batch_run(BatchCtx* b, long nsteps, int variant, int grid) {
   }
   cudaError_t e = cudaMemsetAsync(b->next_dev, 0, sizeof(int), b->stream);
   if (e != cudaSuccess) return cuda_status(e);
-  const int rc = launch_variant(b, a, variant, grid);
+  const int grid = grid_for(b, cl, per_sm, count);
+  int rc;
+  if (cl == 4) rc = launch_cl<4>(b, a, grid);
+  else if (cl == 2) rc = launch_cl<2>(b, a, grid);
+  else rc = launch_cl<1>(b, a, grid);
   if (rc != RIDC_OK) return rc;
   for (EnsInst& I : b->inst)
     for (int j = 0; j < I.P; ++j) I.p[j] = newp[I.P][j];
@@ -515,6 +576,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     }
     EnsClass C{};
     C.s = s;
+    C.variant = s >= 128 ? 1 : 0;   // until the autotuner decides
     void* p;
     if ((rc = b_alloc(b, &p, Q.size() * 4)) != RIDC_OK) return fail(rc);
     cudaMemcpy(p, Q.data(), Q.size() * 4, cudaMemcpyHostToDevice);
@@ -571,7 +633,9 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   void* p;
   if ((rc = b_alloc(b, &p, count * sizeof(int))) != RIDC_OK) return fail(rc);
   b->order_dev = (int*)p;
-  cudaMemcpy(p, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->order_dev, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+  if ((rc = b_alloc(b, &p, count * sizeof(int))) != RIDC_OK) return fail(rc);
+  b->sub_dev = (int*)p;
   if ((rc = b_alloc(b, &p, sizeof(int))) != RIDC_OK) return fail(rc);
   b->next_dev = (int*)p;
   if ((rc = b_alloc(b, &p, b->cls.size() * sizeof(EnsClass))) != RIDC_OK) return fail(rc);
@@ -591,7 +655,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   if ((rc = b_alloc(b, &p, wq.size() * sizeof(double))) != RIDC_OK) return fail(rc);
   b->wq_dev = (double*)p;
   cudaMemcpy(p, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice);
-  // per-CTA workspace for at most 2 CTAs per SM
+  // per-cluster workspace, enough for one-CTA clusters, two per SM
   b->ws_plane = (long)smax * smax;
   const long ctas = 2L * b->sms;
   if ((rc = b_alloc(b, &p, (size_t)ctas * EMaxP * b->ws_plane * sizeof(double))) != RIDC_OK) return fail(rc);
@@ -600,8 +664,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   b->d_ws = (double*)p;
   if ((rc = b_alloc(b, &p, (size_t)ctas * 3 * EMaxP * b->ws_plane * sizeof(float))) != RIDC_OK) return fail(rc);
   b->f_ws = (float*)p;
-  b->grid = std::min(count, b->sms);
-  b->variant = 0;
+  b->cl = 4;
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_status(e));
   *out = reinterpret_cast<ridc_batch>(b);
@@ -672,7 +735,7 @@ extern "C" int ridc_batch_advance(ridc_batch h, long nsteps) {
   BatchCtx* b = bctx(h);
   if (!b || nsteps < 0 || !b->initialised) return RIDC_ERR_ARG;
   if (nsteps == 0) return RIDC_OK;
-  return batch_run(b, nsteps, b->variant, b->grid);
+  return batch_run(b, nsteps, b->cl, b->per_sm, b->order_dev, b->n);
 }
 
 extern "C" int ridc_batch_get_solution(ridc_batch h, int i, double* out, size_t count,
@@ -700,9 +763,13 @@ extern "C" long ridc_batch_cells(ridc_batch h) {
   return b ? b->cells_per_step : -1;
 }
 
-// Times every launch configuration (GEMM register tile 4x4 or 8x4; one or two CTAs per SM)
-// on `nsteps` pipeline steps of the real batch, keeps the fastest and reports it in *choice
-// (variant + 2 * (CTAs per SM - 1)). The state is scrambled: call ridc_batch_set_initial after.
+// Autotuner. First, per grid side, the GEMM tile (64 x 64 or 128 x 128) that integrates the
+// instances of that side fastest on their own (one-CTA clusters); then the cluster size (1, 2
+// or 4 CTAs per instance) and the CTAs per SM (1 or 2) that run the whole batch fastest with
+// those tiles. Each trial advances `nsteps` top-level steps from the current state. The
+// choice is kept for later advances; *choice = CTAs per SM * 256 + cluster size * 16 + (bit
+// c set: side class c uses 128 x 128 tiles).
+// The state is scrambled: call ridc_batch_set_initial afterwards.
 extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float* best_ms) {
   BatchCtx* b = bctx(h);
   if (!b || nsteps < 1) return RIDC_ERR_ARG;
@@ -710,38 +777,66 @@ extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int bv = 0, bg = b->grid;
   const std::vector<EnsInst> saved = b->inst;
-  for (int per_sm = 1; per_sm <= 2; ++per_sm) {
-    for (int v = 0; v < 2; ++v) {
-      const int grid = std::min(b->n, per_sm * b->sms);
-      b->inst = saved;
-      int rc = batch_run(b, nsteps, v, grid);   // warm-up
-      if (rc != RIDC_OK) return rc;
-      b->inst = saved;
-      cudaMemcpyAsync(b->inst_dev, b->inst.data(), b->n * sizeof(EnsInst), cudaMemcpyHostToDevice,
-                      b->stream);
-      cudaEventRecord(e0, b->stream);
-      rc = batch_run(b, nsteps, v, grid);
-      if (rc != RIDC_OK) return rc;
-      cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
+  auto restore = [&]() {
+    b->inst = saved;
+    return cudaMemcpyAsync(b->inst_dev, b->inst.data(), b->n * sizeof(EnsInst),
+                           cudaMemcpyHostToDevice, b->stream);
+  };
+  auto timed = [&](int cl, int per_sm, const int* ord, int cnt, float* ms) -> int {
+    restore();
+    int rc = batch_run(b, nsteps, cl, per_sm, ord, cnt);   // warm-up
+    if (rc != RIDC_OK) return rc;
+    restore();
+    cudaEventRecord(e0, b->stream);
+    rc = batch_run(b, nsteps, cl, per_sm, ord, cnt);
+    if (rc != RIDC_OK) return rc;
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    return RIDC_OK;
+  };
+  int rc = RIDC_OK;
+  int mask = 0;
+  for (size_t c = 0; c < b->cls.size() && rc == RIDC_OK; ++c) {
+    std::vector<int> sub;
+    for (int i = 0; i < b->n; ++i)
+      if (b->inst[i].cls == (int)c) sub.push_back(i);
+    if (sub.empty()) continue;
+    cudaMemcpyAsync(b->sub_dev, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice,
+                    b->stream);
+    float best = 1e30f;
+    int bv = b->cls[c].variant;
+    for (int v = 0; v < 2 && rc == RIDC_OK; ++v) {
+      b->cls[c].variant = v;
+      cudaMemcpyAsync(b->cls_dev, b->cls.data(), b->cls.size() * sizeof(EnsClass),
+                      cudaMemcpyHostToDevice, b->stream);
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; bv = v; bg = grid; }
-      b->inst = saved;
-      cudaMemcpyAsync(b->inst_dev, b->inst.data(), b->n * sizeof(EnsInst), cudaMemcpyHostToDevice,
-                      b->stream);
+      rc = timed(1, 1, b->sub_dev, (int)sub.size(), &ms);
+      if (ms < best) { best = ms; bv = v; }
     }
+    b->cls[c].variant = bv;
+    if (bv) mask |= 1 << c;
   }
+  cudaMemcpyAsync(b->cls_dev, b->cls.data(), b->cls.size() * sizeof(EnsClass),
+                  cudaMemcpyHostToDevice, b->stream);
+  float best = 1e30f;
+  int bcl = b->cl, bps = b->per_sm;
+  for (int per_sm = 1; per_sm <= 2 && rc == RIDC_OK; ++per_sm)
+    for (int cl = 1; cl <= 4 && rc == RIDC_OK; cl *= 2) {
+      float ms = 0.f;
+      rc = timed(cl, per_sm, b->order_dev, b->n, &ms);
+      if (ms < best) { best = ms; bcl = cl; bps = per_sm; }
+    }
+  restore();
   cudaStreamSynchronize(b->stream);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->variant = bv;
-  b->grid = bg;
+  if (rc != RIDC_OK) return rc;
+  b->cl = bcl;
+  b->per_sm = bps;
   b->initialised = false;
-  if (choice) *choice = bv + 2 * (bg > b->sms ? 1 : 0);
+  if (choice) *choice = bps * 256 + bcl * 16 + mask;
   if (best_ms) *best_ms = best;
   return RIDC_OK;
 }
