@@ -55,6 +55,21 @@ def _dist():
     return ws, rank, local
 
 
+def whole_job_rate(local_ms: float, units_per_rank: float, device=None) -> tuple[float, float]:
+    """(units/s over all ranks, slowest rank's ms): every rank processed `units_per_rank`
+    units in `local_ms`; the job's rate is the units of all ranks over the slowest rank's
+    time (replicas, weak scaling). Works with any torch.distributed backend (gloo on CPU
+    tensors, NCCL on CUDA tensors), or without a process group."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slow = float(t.item())
+    return ws * units_per_rank / (slow * 1e-3), slow
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples every 200 ms while active."""
 
@@ -306,12 +321,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     stats = {k: it.kernel_stats(k) for k in ("rhs", "gemm_tc", "residual", "finalize")}
     it.set_profiling(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     cells = float(N * N * args.nt)
-    value = ws * cells * args.steps / (ms_max * 1e-3)
+    value, ms_max = whole_job_rate(ms, cells * args.steps, device="cuda")
 
     # ---- end to end through the C ABI with host buffers ----------------------------------
     e2e_runs = max(1, min(args.steps, 2))
@@ -324,10 +335,7 @@ def main():
         it.advance(args.nt)
         it.solution(out_host.numpy())
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = ws * cells * e2e_runs / float(te.item())
+    e2e_val, _ = whole_job_rate(1e3 * e2e_s, cells * e2e_runs, device="cuda")
     mixed_final = out_host.numpy().copy()
 
     # ---- FP64 GPU form on a truncated run; accuracy of the mixed path against it ---------
