@@ -343,8 +343,8 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
       RIDC_TRY(make_tensor_map(&c->tm_Wl, c->xl, rows, n, 128));
       RIDC_TRY(make_tensor_map(&c->tm_Zh, c->yh, rows, n, 128));
       RIDC_TRY(make_tensor_map(&c->tm_Zl, c->yl, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Bfh, c->Bfh, n, H, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Bfl, c->Bfl, n, H, 128));
+      RIDC_TRY(make_tensor_map(&c->tm_Bfh, c->Bfh, n, H, gemm_sym_fwd_bn(n)));
+      RIDC_TRY(make_tensor_map(&c->tm_Bfl, c->Bfl, n, H, gemm_sym_fwd_bn(n)));
       RIDC_TRY(make_tensor_map(&c->tm_Bbh, c->Bbh, n, H, 128));
       RIDC_TRY(make_tensor_map(&c->tm_Bbl, c->Bbl, n, H, 128));
     }

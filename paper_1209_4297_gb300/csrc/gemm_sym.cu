@@ -18,9 +18,10 @@
 //   SYM_BWD_F32   inverse with the E +- O butterfly, FP32    (fourth transform, y: the increment)
 //
 // Persistent: one CTA per SM over a static tile list; a TMA producer thread and an MMA thread
-// run ahead over a 3-stage ring of 64 KB stages (Ah, Al, Bh, Bl tiles of 128 x 64, 128B
-// swizzle); two TMEM buffers of 256 columns (E and O accumulators of 128 columns each) let four
-// epilogue warps drain one tile while the next is computed. Every mbarrier wait is bounded
+// run ahead over a ring of stages (Ah, Al, Bh, Bl tiles, K = 64, 128B swizzle): forward
+// products use 128 x 256 tiles in two 96 KB stages, inverse products 128 x 128 tiles with E
+// and O accumulators in three 64 KB stages; two TMEM buffers of 256 columns let four epilogue
+// warps drain one tile while the next is computed. Every mbarrier wait is bounded
 // (2 s of %globaltimer); on expiry the kernel flags the error, drains and frees TMEM.
 #include <cudaTypedefs.h>
 
@@ -30,20 +31,31 @@ namespace ridc {
 
 namespace {
 
-constexpr int SY_BM = 128, SY_BN = 128, SY_BK = 64, SY_STAGES = 3;
-constexpr int SY_TILE = SY_BM * SY_BK * 2;   // 16 KB: 128 rows x 64 BF16
-constexpr int SY_STAGE = 4 * SY_TILE;        // Ah, Al, Bh, Bl
+constexpr int SY_BM = 128, SY_BK = 64;
+constexpr int SY_TILE = SY_BM * SY_BK * 2;   // 16 KB: 128 rows x 64 BF16 (A tiles)
 constexpr int SY_MAXN = 4096;
+
+// Tile shapes. Forward products (one accumulator) use 128 x 256 tiles when N/2 allows: the
+// tensor cores read both operands from shared memory, and 256 columns per instruction keep
+// that traffic under the per-SM bandwidth (128 columns need about 95% of it). Inverse
+// products keep two 128-column accumulators (E and O) per tile.
+template <bool FWD, int BN>
+struct SyCfg {
+  static constexpr int BTILE = BN * SY_BK * 2;
+  static constexpr int STAGE = 2 * SY_TILE + 2 * BTILE;
+  static constexpr int STAGES = (BN == 256) ? 2 : 3;
+  static constexpr int NSEG = FWD ? 1 : 2;
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(SY_BM >> 4) << 24);
+};
 // dynamic shared memory: stages + barriers + alignment slack, plus the eigenvalues in the
 // denominator mode only
-constexpr int SY_SMEM_BASE = SY_STAGES * SY_STAGE + 1024 + 1024;
-constexpr int SY_SMEM_MAX = SY_SMEM_BASE + SY_MAXN * 4;
+template <bool FWD, int BN>
+constexpr int sy_smem_base() { return SyCfg<FWD, BN>::STAGES * SyCfg<FWD, BN>::STAGE + 1024 + 1024; }
+constexpr int SY_SMEM_MAX = 2 * (2 * SY_TILE + 2 * 256 * SY_BK * 2) + 2048 + SY_MAXN * 4;
 constexpr int SY_THREADS = 192;
 constexpr uint32_t SY_ACC_COLS = 256;        // per TMEM buffer: E (128) + O (128)
 constexpr unsigned long long SY_WAIT_NS = 2000000000ull;
-// kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = 128
-constexpr uint32_t SY_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SY_BN >> 3) << 17) |
-                              ((uint32_t)(SY_BM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -110,11 +122,13 @@ __device__ __forceinline__ uint64_t s_desc(uint32_t addr) {
   return d;
 }
 
-__device__ __forceinline__ void s_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+// kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N from the instruction descriptor
+__device__ __forceinline__ void s_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                      uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(SY_IDESC), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void s_commit(uint32_t bar) {
@@ -157,14 +171,14 @@ struct SymTile {
   int arow, brow, m0, c0, g;
 };
 
-__device__ __forceinline__ SymTile sym_tile(const SymArgs& a, int t, bool fwd) {
-  const int rt = a.rows / SY_BM, ct = a.H / SY_BN;
+__device__ __forceinline__ SymTile sym_tile(const SymArgs& a, int t, bool fwd, int BN) {
+  const int rt = a.rows / SY_BM, ct = a.H / BN;
   SymTile T;
   if (fwd) {
     T.g = t / (rt * ct);
     const int r = t - T.g * rt * ct;
     T.m0 = (r / ct) * SY_BM;
-    T.c0 = (r % ct) * SY_BN;
+    T.c0 = (r % ct) * BN;
     // forward operands are laid out [plane][parity group][row][H]
     const int pl = a.plane0 + T.m0 / a.n;
     T.arow = (pl * 2 + T.g) * a.n + (T.m0 - (T.m0 / a.n) * a.n);
@@ -172,13 +186,14 @@ __device__ __forceinline__ SymTile sym_tile(const SymArgs& a, int t, bool fwd) {
   } else {
     T.g = 0;
     T.m0 = (t / ct) * SY_BM;
-    T.c0 = (t % ct) * SY_BN;
+    T.c0 = (t % ct) * BN;
     T.arow = a.plane0 * a.n + T.m0;
     T.brow = T.c0;
   }
   return T;
 }
 
+template <bool FWD, int BN>
 __global__ void __launch_bounds__(SY_THREADS, 1)
     gemm_sym_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                     const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
@@ -186,15 +201,17 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
+  using Cfg = SyCfg<FWD, BN>;
+  constexpr int SY_STAGES = Cfg::STAGES, SY_STAGE = Cfg::STAGE, BTILE = Cfg::BTILE;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SY_STAGES * SY_STAGE);
   // full[S], empty[S], acc_full[2], acc_empty[2], mma_done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SY_STAGES + 5);
   float* lam_s = reinterpret_cast<float*>(smem + SY_STAGES * SY_STAGE + 1024);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool fwd = a.mode == SYM_FWD_F32 || a.mode == SYM_FWD_DEN;
-  const int nseg = fwd ? 1 : 2;
+  constexpr bool fwd = FWD;
+  constexpr int nseg = Cfg::NSEG;
   const int KB = a.H / SY_BK;
-  const int ntiles = (fwd ? 2 : 1) * (a.rows / SY_BM) * (a.H / SY_BN);
+  const int ntiles = (fwd ? 2 : 1) * (a.rows / SY_BM) * (a.H / BN);
   volatile int* errv = a.err;
   auto full = [&](int s) { return s_u32(bars + s); };
   auto empty = [&](int s) { return s_u32(bars + SY_STAGES + s); };
@@ -237,7 +254,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
     long issued = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok && !*errv; t += gridDim.x) {
-      const SymTile T = sym_tile(a, t, fwd);
+      const SymTile T = sym_tile(a, t, fwd, BN);
       for (int seg = 0; seg < nseg && ok; ++seg) {
         const int koff = seg * a.H, brow = T.brow + seg * a.H;
         for (int kb = 0; kb < KB; ++kb, ++issued) {
@@ -252,7 +269,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
           s_tma(s_u32(st), &tAh, full(s), (fwd ? 0 : koff) + kb * SY_BK, T.arow);
           s_tma(s_u32(st + SY_TILE), &tAl, full(s), (fwd ? 0 : koff) + kb * SY_BK, T.arow);
           s_tma(s_u32(st + 2 * SY_TILE), &tBh, full(s), kb * SY_BK, brow);
-          s_tma(s_u32(st + 3 * SY_TILE), &tBl, full(s), kb * SY_BK, brow);
+          s_tma(s_u32(st + 2 * SY_TILE + BTILE), &tBl, full(s), kb * SY_BK, brow);
         }
       }
     }
@@ -269,7 +286,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
       if (use > 0 && !s_wait(acce(b), (uint32_t)((use - 1) & 1), a.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int seg = 0; seg < nseg && ok; ++seg) {
-        const uint32_t acc = tmem + (uint32_t)(b * SY_ACC_COLS + seg * SY_BN);
+        const uint32_t acc = tmem + (uint32_t)(b * SY_ACC_COLS + seg * BN);
         for (int kb = 0; kb < KB; ++kb, ++consumed) {
           const int s = (int)(consumed % SY_STAGES);
           if (!s_wait(full(s), (uint32_t)((consumed / SY_STAGES) & 1), a.err)) {
@@ -279,13 +296,13 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t st = s_u32(smem + s * SY_STAGE);
           const uint64_t ah = s_desc(st), al = s_desc(st + SY_TILE);
-          const uint64_t bh = s_desc(st + 2 * SY_TILE), bl = s_desc(st + 3 * SY_TILE);
+          const uint64_t bh = s_desc(st + 2 * SY_TILE), bl = s_desc(st + 2 * SY_TILE + BTILE);
 #pragma unroll
           for (int kk = 0; kk < SY_BK / 16; ++kk) {
             const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            s_mma(acc, ah + adv, bh + adv, (kb | kk) != 0);
-            s_mma(acc, ah + adv, bl + adv, 1);
-            s_mma(acc, al + adv, bh + adv, 1);
+            s_mma(acc, ah + adv, bh + adv, Cfg::IDESC, (kb | kk) != 0);
+            s_mma(acc, ah + adv, bl + adv, Cfg::IDESC, 1);
+            s_mma(acc, al + adv, bh + adv, Cfg::IDESC, 1);
           }
           s_commit(empty(s));
         }
@@ -304,7 +321,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
       const int b = local & 1;
       if (!s_wait(accf(b), (uint32_t)((local >> 1) & 1), a.err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const SymTile T = sym_tile(a, t, fwd);
+      const SymTile T = sym_tile(a, t, fwd, BN);
       const int row = T.m0 + q * 32 + lane;
       const int plane = a.plane0 + row / n, rl = row - (row / n) * n;
       const size_t pbase = (size_t)plane * n;
@@ -313,7 +330,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
         const int cbase = T.g * a.H + T.c0;   // output column position (split order)
         const float dtnu = a.dtnu[plane % a.S];
         const float den_r = (a.mode == SYM_FWD_DEN) ? 1.0f - dtnu * lam_s[rl] : 0.f;
-        for (int c = 0; c < SY_BN; c += 16) {
+        for (int c = 0; c < BN; c += 16) {
           uint32_t v[16];
           s_ld16(acc + (uint32_t)c, v);
           s_ld_wait();
@@ -332,10 +349,10 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
           }
         }
       } else {
-        for (int c = 0; c < SY_BN; c += 16) {
+        for (int c = 0; c < BN; c += 16) {
           uint32_t e[16], o[16];
           s_ld16(acc + (uint32_t)c, e);
-          s_ld16(acc + (uint32_t)(SY_BN + c), o);
+          s_ld16(acc + (uint32_t)(BN + c), o);
           s_ld_wait();
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
@@ -391,16 +408,28 @@ int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int
   return r == CUDA_SUCCESS ? RIDC_OK : RIDC_ERR_CUDA;
 }
 
-int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
-                    const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
-                    __nv_bfloat16* ol, float* o32) {
+int gemm_sym_fwd_bn(int n) { return (n / 2) % 256 == 0 ? 256 : 128; }
+
+template <bool FWD, int BN>
+static int launch_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
+                      const CUtensorMap* bl, const SymArgs& a, int sms) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SY_SMEM_MAX);
+    cudaError_t e = cudaFuncSetAttribute(gemm_sym_kernel<FWD, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM_MAX);
     if (e != cudaSuccess) return cuda_status(e);
     attr_done = true;
   }
+  const int ntiles = (FWD ? 2 : 1) * (a.rows / SY_BM) * (a.H / BN);
+  dim3 grid(ntiles < sms ? ntiles : sms);
+  const int smem = sy_smem_base<FWD, BN>() + (a.mode == SYM_FWD_DEN ? a.n * 4 : 0);
+  gemm_sym_kernel<FWD, BN><<<grid, SY_THREADS, smem, c->stream>>>(*ah, *al, *bh, *bl, a);
+  return cuda_status(cudaGetLastError());
+}
+
+int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
+                    const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
+                    __nv_bfloat16* ol, float* o32) {
   const int n = c->n;
   if (n % 256 != 0 || n > SY_MAXN) return RIDC_ERR_UNSUPPORTED;
   static int sms = 0;
@@ -424,14 +453,14 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
   for (int s = 0; s < c->S; ++s) a.dtnu[s] = (float)(c->dt * c->nu[s]);
   a.err = c->err_dev;
   const bool fwd = mode == SYM_FWD_F32 || mode == SYM_FWD_DEN;
-  const int ntiles = (fwd ? 2 : 1) * (a.rows / SY_BM) * (a.H / SY_BN);
-  dim3 grid(ntiles < sms ? ntiles : sms);
-  const int smem = SY_SMEM_BASE + (mode == SYM_FWD_DEN ? n * 4 : 0);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_TC, &e0);
-  gemm_sym_kernel<<<grid, SY_THREADS, smem, c->stream>>>(*ah, *al, *bh, *bl, a);
+  int rc;
+  if (!fwd) rc = launch_sym<false, 128>(c, ah, al, bh, bl, a, sms);
+  else if (gemm_sym_fwd_bn(n) == 256) rc = launch_sym<true, 256>(c, ah, al, bh, bl, a, sms);
+  else rc = launch_sym<true, 128>(c, ah, al, bh, bl, a, sms);
   prof_end(c, RIDC_KERNEL_GEMM_TC, e0);
-  return cuda_status(cudaGetLastError());
+  return rc;
 }
 
 }  // namespace ridc

@@ -168,6 +168,8 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
 // y-butterfly of the first transform's FP32 output into the second's split operand
 int launch_ybfly(Ctx* c, int plane0, int nplanes, const float* in);
 int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
+// column-tile width of the forward parity-split products for side n (the B box height)
+int gemm_sym_fwd_bn(int n);
 int launch_1d(Ctx* c, long nsteps_pipe, int init_only);
 int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
 
