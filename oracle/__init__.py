@@ -19,7 +19,7 @@ a matrix-exponential solution of the 2D Dirichlet problem.
 """
 from .quadrature import lagrange_weights, weight_table, stencil
 from .problems import AdvDiff1DPeriodic, GrayScott2DNeumann, AdvDiff2DDirichlet, from_workload
-from .ridc import ridc_sequential, fbe
+from .ridc import ridc_sequential, ridc_restarted, fbe
 
 __all__ = ["lagrange_weights", "weight_table", "stencil", "AdvDiff1DPeriodic", "GrayScott2DNeumann",
-           "AdvDiff2DDirichlet", "from_workload", "ridc_sequential", "fbe"]
+           "AdvDiff2DDirichlet", "from_workload", "ridc_sequential", "ridc_restarted", "fbe"]

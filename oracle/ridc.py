@@ -59,3 +59,20 @@ def ridc_sequential(problem, y0: np.ndarray, dt: float, nsteps: int, order: int,
         finals.append(eta[nsteps])
         prev = eta
     return finals if all_levels else finals[-1]
+
+
+def ridc_restarted(problem, y0: np.ndarray, dt: float, nsteps: int, order: int,
+                   restart_every: int):
+    """RIDC with restarts (Section III-E): the interval is cut into pieces of `restart_every`
+    steps (the last piece may be shorter), and each piece is a fresh RIDC computation whose
+    initial value is the most corrected solution at the end of the previous piece.
+    restart_every <= 0 means no restarts. Returns the most corrected solution at nsteps."""
+    if restart_every <= 0:
+        return ridc_sequential(problem, y0, dt, nsteps, order)
+    y = np.array(y0, dtype=np.float64, copy=True)
+    done = 0
+    while done < nsteps:
+        k = min(restart_every, nsteps - done)
+        y = ridc_sequential(problem, y, dt, k, order)
+        done += k
+    return y

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import inputs
-from oracle import AdvDiff1DPeriodic, fbe, from_workload, ridc_sequential
+from oracle import AdvDiff1DPeriodic, fbe, from_workload, ridc_restarted, ridc_sequential
 
 
 def _modes(n):
@@ -88,3 +88,55 @@ def test_zero_steps_is_identity():
     w = inputs.adv_diff_1d()
     p = from_workload(w)
     np.testing.assert_array_equal(ridc_sequential(p, w.u0, w.dt, 0, 4), w.u0)
+
+
+# ---------------------------------------------------------------- restarts (Section III-E)
+@pytest.mark.parametrize("every", [1, 3, 7, 20])
+def test_restarted_fbe_is_fbe(every):
+    """With one level the most corrected solution is the FBE state itself, so restarting
+    from it at any interval must reproduce the plain FBE run bit for bit (this fails if a
+    restart loses or repeats a step, or hands over the wrong state)."""
+    w = inputs.adv_diff_1d(n=64, nsteps=20, dt=1.0 / 256)
+    p = from_workload(w)
+    plain = fbe(p, w.u0, w.dt, 20)[-1]
+    np.testing.assert_array_equal(ridc_restarted(p, w.u0, w.dt, 20, 1, every), plain)
+
+
+def test_restarted_without_restart_is_plain():
+    w = inputs.adv_diff_1d(n=64, nsteps=12, dt=1.0 / 256)
+    p = from_workload(w)
+    plain = ridc_sequential(p, w.u0, w.dt, 12, 4)
+    np.testing.assert_array_equal(ridc_restarted(p, w.u0, w.dt, 12, 4, 0), plain)
+    np.testing.assert_array_equal(ridc_restarted(p, w.u0, w.dt, 12, 4, 12), plain)
+
+
+def test_error_falls_as_restarts_increase():
+    """Section IV-A (figure of RIDC4 error against restarts): on advection-diffusion to
+    T = 40 with a fixed 4000 steps, the final error of RIDC4 falls as restarts are added.
+    Here: u0 = 2 + sin(2 pi x), a = 0.1, nu = 1e-3, central differences on 128 points, error
+    against the semi-discrete exact solution (time error only); 0, 1, 3 and 9 restarts."""
+    n, a, nu, T, nt = 128, 0.1, 1e-3, 40.0, 4000
+    p = AdvDiff1DPeriodic(n, a, nu)
+    x = np.arange(n) / n
+    sig, om = _modes(n)
+    u0 = 2.0 + np.sin(2 * np.pi * x)
+    exact = 2.0 + np.exp(-nu * sig[1] * T) * np.sin(2 * np.pi * x - a * om[1] * T)
+    errs = []
+    for restarts in (0, 1, 3, 9):
+        u = ridc_restarted(p, u0, T / nt, nt, 4, nt // (restarts + 1))
+        errs.append(np.linalg.norm(u - exact) / np.linalg.norm(exact))
+    assert all(e1 < 0.5 * e0 for e0, e1 in zip(errs, errs[1:])), errs
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_restarts_fall_at_fixed_times(order):
+    """Restarts happen at fixed multiples of the interval, so running to a restart time and
+    continuing from there gives the same numbers as one run (this fails if a piece is
+    longer or shorter than the interval)."""
+    w = inputs.adv_diff_1d(n=64, nsteps=23, dt=1.0 / 256)
+    p = from_workload(w)
+    every = 5
+    one = ridc_restarted(p, w.u0, w.dt, 2 * every + 3, order, every)
+    mid = ridc_restarted(p, w.u0, w.dt, every, order, every)
+    two = ridc_restarted(p, mid, w.dt, every + 3, order, every)
+    np.testing.assert_array_equal(one, two)
