@@ -126,6 +126,86 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "reasons": reasons}
 
 
+# DRAM traffic of one full (8-plane) gemm_sym launch from one ncu capture
+# (profiles/gemm_sym_gray_scott_2048_mixed.md: dram__bytes_read.sum + dram__bytes_write.sum,
+# mean over the four modes), valid only for the kernel source it was taken on.
+GEMM_TRAFFIC = {"bytes": 2.326e8,
+                "source_sha256": "a2609d96631d2e43fc5601e3f793b649b5167d482c658e7384c080bd5e97a425"}
+
+
+def gemm_traffic():
+    """Per-launch DRAM bytes of gemm_sym, or None once its source differs from the one the
+    counters were taken on."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1209_4297_gb300", "csrc", "gemm_sym.cu")
+    try:
+        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return GEMM_TRAFFIC["bytes"] if digest == GEMM_TRAFFIC["source_sha256"] else None
+
+
+# FP64 pipe of GB300: 2 FP64 operations (DADD, DMUL or DFMA) per clock per SM, i.e. the
+# nominal 1.25 TFLOP/s (FMA = 2 flop) at 152 SMs x 2070 MHz.
+FP64_OPS_PER_CLK_SM = 2
+
+
+def step_work(masks, species=2, order=ORDER, nref=NREF, n=N):
+    """Algorithmic FP64 operations and bytes of the non-GEMM kernels of the mixed
+    Gray-Scott path, summed over the pipeline steps in `masks` (bit j: level j advances).
+    Per plane-cell (one species of one advancing level):
+      rhs       predictor 1 op (dt F), corrector j: 2 differences, dt fma, j+1 quadrature
+                fmas = j+4 ops; reads 1 (predictor) or j+5 FP64 fields, writes r (8 B) and
+                the split operand (4 B)
+      residual  first pass 5 ops (stencil: 3 adds, 2 fmas), later passes 6 (+1 add for
+                delta = previous + increment); reads r (8 B), increment (4 B) and from the
+                second pass the previous delta (8 B), writes delta (8 B) and the split (4 B)
+      ybfly     no FP64 work; reads 4 B, writes 4 B
+      finalize  eta = base + d64 + d32 (2 adds), f = f^N + D eta on levels that keep f
+                (3 adds, 2 fmas), plus the reaction per cell (u v^2: 2 muls; 1 add, 2 fmas);
+                reads base, d64, d32 (20 B), writes eta, f^N and f where kept (8 B each)."""
+    cells = float(n * n)
+    ops = {"rhs": 0.0, "residual": 0.0, "ybfly": 0.0, "finalize": 0.0}
+    byt = dict(ops)
+    for m in masks:
+        act = [j for j in range(order) if (int(m) >> j) & 1]
+        for j in act:
+            keeps_f = j < order - 1 or j == 0
+            ops["rhs"] += (1 if j == 0 else j + 4) * species * cells
+            byt["rhs"] += ((8 if j == 0 else 8 * (j + 5)) + 12) * species * cells
+            ops["residual"] += (5 + 6 * (nref - 1)) * species * cells
+            byt["residual"] += (24 + 32 * (nref - 1)) * species * cells
+            byt["ybfly"] += 8 * (nref + 1) * species * cells
+            ops["finalize"] += (2 * species + 5 + (5 * species if keeps_f else 0)) * cells
+            byt["finalize"] += (20 + 16 + (8 if keeps_f else 0)) * species * cells
+    return ops, byt
+
+
+def fp64_kernel_rooflines(masks, stats, runs, peaks):
+    """Achieved FP64-pipe and HBM rates of the non-GEMM kernels over the timed region."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = FP64_OPS_PER_CLK_SM * sms * mhz * 1e6
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ops, byt = step_work(masks)
+    out = {"bound": "alu", "unit": "FP64 op/s (DADD, DMUL, DFMA each 1)", "peak": peak_ops,
+           "peak_source": f"{FP64_OPS_PER_CLK_SM} FP64 ops/clk/SM x {sms} SMs x {mhz:.0f} MHz "
+                          "(nominal 1.25 TFLOP/s)", "kernels": {}}
+    for k in ops:
+        launches, ms = stats[k]
+        if ms <= 0:
+            continue
+        s = ms * 1e-3
+        ent = {"launches": launches, "ms": ms,
+               "hbm_gbs": runs * byt[k] / s / 1e9, "hbm_frac": runs * byt[k] / s / 1e9 / hbm}
+        if ops[k] > 0:
+            ent["fp64_ops_per_s"] = runs * ops[k] / s
+            ent["fp64_frac"] = runs * ops[k] / s / peak_ops
+        out["kernels"][k] = ent
+    return out
+
+
 def cpu_baseline(steps: int = 6):
     """The FP64 oracle (sequential classic-IDC order, numpy/scipy) on 2048^2 Gray-Scott."""
     import inputs
@@ -253,6 +333,55 @@ def run_single(args):
     print(json.dumps(line), flush=True)
 
 
+def run_accuracy(args):
+    """Accuracy of the headline workload over its whole length: the mixed path against the
+    FP64 GPU path at every `--check-every` top-level steps of the 1000-step 2048^2
+    Gray-Scott run, and the sensitivity envelope of the problem itself: the mixed path
+    started from the initial field with every value moved by one ulp (seeded directions).
+    Not a timing line; the FP64 run takes several minutes."""
+    import torch
+
+    import inputs
+    from paper_1209_4297_gb300 import Integrator
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    w = inputs.gray_scott_2d(n=N, nsteps=args.nt)
+    rng = np.random.default_rng(12345)
+    toward = np.where(rng.random(w.u0.shape) < 0.5, -np.inf, np.inf)
+    u0p = np.nextafter(w.u0, toward)
+    runs = {"mixed": (w.u0, "mixed_bf16x3"), "fp64": (w.u0, "fp64"),
+            "mixed_ulp": (u0p, "mixed_bf16x3")}
+    its = {}
+    for k, (u0, prec) in runs.items():
+        its[k] = Integrator.from_workload(w, precision=prec, n_refine=NREF,
+                                          stream=stream.cuda_stream)
+        its[k].set_initial(torch.from_numpy(u0).cuda())
+    rows, done, t0 = [], 0, time.perf_counter()
+    while done < args.nt:
+        k = min(args.check_every, args.nt - done)
+        for it in its.values():
+            it.advance(k)
+        done += k
+        sol = {name: it.solution() for name, it in its.items()}
+        ref = np.linalg.norm(sol["fp64"])
+        rows.append({"step": done,
+                     "mixed_vs_fp64": float(np.linalg.norm(sol["mixed"] - sol["fp64"]) / ref),
+                     "ulp_envelope": float(np.linalg.norm(sol["mixed_ulp"] - sol["mixed"])
+                                           / np.linalg.norm(sol["mixed"]))})
+        print(f"# step {done}: {rows[-1]} ({time.perf_counter() - t0:.0f} s)", file=sys.stderr,
+              flush=True)
+    for it in its.values():
+        it.close()
+    line = {"metric": "relative L2, mixed BF16x3 (2 refinements) vs FP64 GPU, 2048^2 Gray-Scott "
+                      "RIDC-4", "value": rows[-1]["mixed_vs_fp64"], "unit": "relative L2",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "gray_scott_2048_ridc4", "grid": N, "order": ORDER,
+                       "top_level_steps": args.nt, "dt": 0.5, "n_refine": NREF},
+            "checkpoints": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,7 +394,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="gray_scott_2048",
                     choices=["gray_scott_2048", "ensemble", "adv_diff_1d", "gray_scott_1024_fp64",
-                             "adv_diff_4096"])
+                             "adv_diff_4096", "accuracy_2048"])
+    ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--ens-refine", type=int, default=1)
     ap.add_argument("--nt-truncate", type=int, default=60)
     args = ap.parse_args()
@@ -273,6 +403,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "accuracy_2048":
+        return run_accuracy(args)
     if args.workload != "gray_scott_2048":
         return run_single(args)
 
@@ -319,7 +451,7 @@ def main():
         dist.barrier()
     launches = it.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    stats = {k: it.kernel_stats(k) for k in ("rhs", "gemm_tc", "residual", "finalize")}
+    stats = {k: it.kernel_stats(k) for k in ("rhs", "gemm_tc", "residual", "ybfly", "finalize")}
     it.set_profiling(False)
     cells = float(N * N * args.nt)
     value, ms_max = whole_job_rate(ms, cells * args.steps, device="cuda")
@@ -392,8 +524,10 @@ def main():
             "useful_tflops": achieved_tf / 3 if achieved_tf else None,
             "dense_equivalent_tflops": 2 * achieved_tf / 3 if achieved_tf else None,
             "avg_launch_ms": ms_tc / n_tc if n_tc else None,
-            "traffic": None}
+            "traffic": gemm_traffic(),
+            "traffic_note": "DRAM bytes of one 8-plane launch (ncu); algorithmic 2.77e8"}
     share = {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items()}
+    fp64_roof = fp64_kernel_rooflines(masks, stats, args.steps, peaks)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -408,6 +542,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": roof,
         "kernel_ms": share,
+        "fp64_kernels": fp64_roof,
         "fp64_gpu": fp64,
         "clocks": clk.summary(),
     }

@@ -71,7 +71,10 @@ typedef struct {
     double F, k;          /* Gray-Scott feed and kill rates (unused otherwise)               */
     int    precision;     /* ridc_precision; 1D problems accept RIDC_FP64 only               */
     int    n_refine;      /* refinement passes of the mixed solve (0..4); ignored for FP64  */
-    int    restart_every; /* reserved for restarts (Section III-E); must be 0                */
+    int    restart_every; /* restarts (Section III-E): every restart_every steps of the most
+                             corrected level, all levels restart from its solution and re-enter
+                             start-up; 0 = no restarts. Single integrators only (a batch
+                             requires 0).                                                    */
 } ridc_problem;
 
 typedef struct {
@@ -118,11 +121,36 @@ int ridc_get_solution(ridc_handle h, double* out, size_t count, int out_on_devic
 int ridc_get_level(ridc_handle h, int level, double* out, size_t count, int out_on_device,
                    long* step);
 
-/* Time t_p = p * dt of the most corrected level (t_0 = 0).                                 */
+/* Time t_p = p * dt of the most corrected level (t_0 = 0; p counts every step since
+ * ridc_set_initial, across restarts).                                                      */
 int ridc_get_time(ridc_handle h, double* t);
 
-/* Steps taken so far by each level: steps[j] = p_j for j < nlevels (nlevels <= order).     */
+/* Steps taken so far by each level: steps[j] = p_j for j < nlevels (nlevels <= order),
+ * counted from ridc_set_initial across restarts (after a restart every level stands at the
+ * restart time).                                                                           */
 int ridc_get_progress(ridc_handle h, long* steps, int nlevels);
+
+/* ---- checkpoint / resume ---------------------------------------------------------------- */
+
+/* Write the integrator's whole state into host memory `buf`: the steps taken by each level,
+ * every slot of every level's ring (eta, f^N and, where the level keeps it, f = f^N + D eta;
+ * Section III-E's memory footprint) and the problem parameters that state depends on.
+ * The format is this library's own: a version-tagged header in native byte order followed
+ * by FP64 values.
+ *   buf == NULL : only *len is set, to the number of bytes needed.
+ *   *len too small : RIDC_ERR_ARG, and *len is set to the number of bytes needed.
+ * Synchronises the stream; RIDC_ERR_TIMEOUT if an earlier device-side wait gave up (the
+ * state would be incomplete). A state written before ridc_set_initial is refused
+ * (RIDC_ERR_ARG). On success *len is the number of bytes written.                            */
+int ridc_save_state(ridc_handle h, void* buf, size_t* len);
+
+/* Restore a state written by ridc_save_state. The handle must have been created for the
+ * same problem: kind, grid, order, dt, nu, a, b, F, k and restart_every equal bit for bit
+ * (precision and n_refine may differ: the state is FP64 in every precision). Continuing
+ * from a loaded state gives the same numbers as continuing the saved integrator.
+ * RIDC_ERR_ARG if len is short or the buffer is not a state of this problem; nothing is
+ * changed then. Synchronises the stream, so `buf` may be reused on return.                 */
+int ridc_load_state(ridc_handle h, const void* buf, size_t len);
 
 /* Release all device and host memory of the handle (synchronises its stream). NULL is ok. */
 void ridc_destroy(ridc_handle h);
@@ -225,7 +253,8 @@ int ridc_quadrature_weights(int order, double* out, size_t cap);
 #define RIDC_KERNEL_RESIDUAL  3   /* FP64 refinement residual + split                      */
 #define RIDC_KERNEL_FINALIZE  4   /* solution accumulation + f^N, f of the new state       */
 #define RIDC_KERNEL_1D        5   /* persistent 1D pipeline kernel                         */
-#define RIDC_KERNEL_COUNT     6
+#define RIDC_KERNEL_YBFLY     6   /* parity split between the first two tensor-core GEMMs  */
+#define RIDC_KERNEL_COUNT     7
 
 /* Enable (1) or disable (0) CUDA-event timing of every kernel launch on the handle's
  * stream. Enabling clears the counters.                                                     */

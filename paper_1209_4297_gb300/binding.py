@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libridc.so")
 
 KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dirichlet": 2}
 PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1, "fp32_solve": 2}
-KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5}
+KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5,
+           "ybfly": 6}
 
 
 class RidcError(RuntimeError):
@@ -62,6 +63,8 @@ def lib() -> ctypes.CDLL:
         "ridc_destroy": (None, [vp]),
         "ridc_error_string": (ctypes.c_char_p, [i]),
         "ridc_solve_planes": (i, [vp, vp, vp, i, i]),
+        "ridc_save_state": (i, [vp, vp, POINTER(sz)]),
+        "ridc_load_state": (i, [vp, vp, sz]),
         "ridc_schedule_plan": (i, [i, lg, POINTER(c_uint), sz, POINTER(sz)]),
         "ridc_quadrature_weights": (i, [i, POINTER(c_double), sz]),
         "ridc_set_profiling": (i, [vp, i]),
@@ -136,11 +139,11 @@ class Integrator:
 
     def __init__(self, kind: str, n: int, nu, dt: float, order: int, *, a: float = 0.0,
                  b: float = 0.0, F: float = 0.0, k: float = 0.0, precision: str = "fp64",
-                 n_refine: int = 2, stream=None):
+                 n_refine: int = 2, restart_every: int = 0, stream=None):
         L = lib()
         self._h = c_void_p(None)
         nu = np.atleast_1d(np.asarray(nu, dtype=np.float64))
-        pr = Problem(KINDS[kind], a, b, F, k, PRECISIONS[precision], n_refine, 0)
+        pr = Problem(KINDS[kind], a, b, F, k, PRECISIONS[precision], n_refine, restart_every)
         gr = Grid(1 if kind == "adv_diff_1d_periodic" else 2, n)
         if stream is None:
             stream = _current_stream()
@@ -153,9 +156,10 @@ class Integrator:
 
     @classmethod
     def from_workload(cls, w, precision: str = "fp64", n_refine: int = 2, stream=None,
-                      order: int | None = None):
+                      order: int | None = None, restart_every: int = 0):
         return cls(w.kind, w.n, w.nu, w.dt, order or w.order, a=w.a, b=w.b, F=w.F, k=w.k,
-                   precision=precision, n_refine=n_refine, stream=stream)
+                   precision=precision, n_refine=n_refine, restart_every=restart_every,
+                   stream=stream)
 
     def close(self) -> None:
         if self._h:
@@ -206,6 +210,21 @@ class Integrator:
         t = c_double(0)
         _check(lib().ridc_get_time(self._h, byref(t)), "ridc_get_time")
         return t.value
+
+    def save_state(self) -> np.ndarray:
+        """The whole integrator state (ridc_save_state) as a host byte array."""
+        need = c_size_t(0)
+        _check(lib().ridc_save_state(self._h, None, byref(need)), "ridc_save_state")
+        buf = np.empty(need.value, dtype=np.uint8)
+        _check(lib().ridc_save_state(self._h, c_void_p(buf.ctypes.data), byref(need)),
+               "ridc_save_state")
+        return buf
+
+    def load_state(self, buf: np.ndarray) -> None:
+        """Restore a state returned by save_state() of an integrator of the same problem."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().ridc_load_state(self._h, c_void_p(buf.ctypes.data), buf.size),
+               "ridc_load_state")
 
     def solve_planes(self, r, out=None):
         """(I - dt nu_s L)^{-1} r for r of shape [planes][n][n] (plane p -> species p % S)."""

@@ -288,6 +288,7 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
   c->a = pr->a; c->b = pr->b; c->gsF = pr->F; c->gsk = pr->k;
   c->prec = pr->precision;
   c->n_refine = pr->n_refine;
+  c->restart_every = pr->restart_every;
   c->dim = g->dim;
   c->n = g->n;
   c->P = order;
@@ -358,7 +359,7 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
   if (!pr || !g || !nu || !out) return RIDC_ERR_ARG;
   if (order < 1 || order > kMaxOrder) return RIDC_ERR_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return RIDC_ERR_ARG;
-  if (pr->restart_every != 0) return RIDC_ERR_UNSUPPORTED;
+  if (pr->restart_every < 0) return RIDC_ERR_ARG;
   if (pr->kind < 0 || pr->kind > 2) return RIDC_ERR_ARG;
   if (pr->precision != RIDC_FP64 && pr->precision != RIDC_MIXED_BF16X3) return RIDC_ERR_ARG;
   if (pr->n_refine < 0 || pr->n_refine > 4) return RIDC_ERR_ARG;
@@ -424,15 +425,14 @@ static void fill_fin_consts(Ctx* c, FinArgs* fa) {
 // ------------------------------------------------------------------------------------------
 // initial state
 // ------------------------------------------------------------------------------------------
-extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, int on_device) {
-  Ctx* c = ctx_of(h);
-  if (!c || !u0 || count != (size_t)c->plane) return RIDC_ERR_ARG;
-  const size_t bytes = count * sizeof(double);
+// Every level's slot 0 := u0 (host or device), with f^N and F of that state; p := 0.
+static int start_from(Ctx* c, const double* u0, int on_device) {
+  const size_t bytes = (size_t)c->plane * sizeof(double);
   if (on_device) {
     RIDC_CUDA(cudaMemcpyAsync(c->eta[0], u0, bytes, cudaMemcpyDeviceToDevice, c->stream));
   } else {
     RIDC_CUDA(cudaStreamSynchronize(c->stream));   // staging buffer may still be in use
-    RIDC_TRY(ensure_pinned(c, count));
+    RIDC_TRY(ensure_pinned(c, (size_t)c->plane));
     memcpy(c->pinned, u0, bytes);
     RIDC_CUDA(cudaMemcpyAsync(c->eta[0], c->pinned, bytes, cudaMemcpyHostToDevice, c->stream));
   }
@@ -449,7 +449,7 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
     RIDC_CUDA(cudaMemsetAsync(c->p_dev, 0, kMaxOrder * sizeof(long), c->stream));
     RIDC_TRY(launch_1d(c, 0, 1));   // evaluates f^N and F of slot 0 only
   }
-  // every level starts from the same data at t_0
+  // every level starts from the same data
   for (int j = 1; j < c->P; ++j) {
     RIDC_CUDA(cudaMemcpyAsync(c->eta[j], c->eta[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
     RIDC_CUDA(cudaMemcpyAsync(c->fN[j], c->fN[0], bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -459,6 +459,13 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
   for (int j = 0; j < kMaxOrder; ++j) c->p[j] = 0;
   c->initialised = true;
   return RIDC_OK;
+}
+
+extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, int on_device) {
+  Ctx* c = ctx_of(h);
+  if (!c || !u0 || count != (size_t)c->plane) return RIDC_ERR_ARG;
+  c->seg_base = 0;
+  return start_from(c, u0, on_device);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -611,11 +618,8 @@ static int step_2d(Ctx* c, unsigned mask) {
   return RIDC_OK;
 }
 
-extern "C" int ridc_advance(ridc_handle h, long nsteps) {
-  Ctx* c = ctx_of(h);
-  if (!c || nsteps < 0) return RIDC_ERR_ARG;
-  if (!c->initialised) return RIDC_ERR_ARG;
-  if (nsteps == 0) return RIDC_OK;
+// Advance the top level by nsteps within the current start (no restart boundary inside).
+static int advance_run(Ctx* c, long nsteps) {
   const long target = c->p[c->P - 1] + nsteps;
   if (c->dim == 1) {
     // plan on the host (the same rule the device replays), then one persistent launch
@@ -652,6 +656,40 @@ extern "C" int ridc_advance(ridc_handle h, long nsteps) {
     RIDC_TRY(step_2d(c, m));
   }
   return c->p[c->P - 1] == target ? RIDC_OK : RIDC_ERR_CUDA;
+}
+
+extern "C" int ridc_advance(ridc_handle h, long nsteps) {
+  Ctx* c = ctx_of(h);
+  if (!c || nsteps < 0) return RIDC_ERR_ARG;
+  if (!c->initialised) return RIDC_ERR_ARG;
+  const long R = c->restart_every;
+  while (nsteps > 0) {
+    // with restarts, a run never crosses the next restart time (Section III-E): all levels
+    // drain to it, and the most corrected solution there starts a fresh computation
+    const long k = (R > 0) ? std::min(nsteps, R - c->p[c->P - 1]) : nsteps;
+    RIDC_TRY(advance_run(c, k));
+    nsteps -= k;
+    if (R > 0 && c->p[c->P - 1] == R && c->P > 1) {
+      const int top = c->P - 1;
+      RIDC_TRY(start_from(c, slot_ptr(c, c->eta[top], top, R), 1));
+      c->seg_base += R;
+    } else if (R > 0 && c->p[c->P - 1] == R) {
+      // one level: restarting from its own newest state changes nothing but the index of
+      // the current start; move that state (and its f^N, F) to slot 0
+      const long t = c->p[0];
+      if (t % c->cap[0] != 0) {
+        const size_t bytes = (size_t)c->plane * sizeof(double);
+        double* rings[3] = {c->eta[0], c->fN[0], c->Fq[0]};
+        for (double* ring : rings)
+          if (ring)
+            RIDC_CUDA(cudaMemcpyAsync(ring, slot_ptr(c, ring, 0, t), bytes,
+                                      cudaMemcpyDeviceToDevice, c->stream));
+      }
+      c->p[0] = 0;
+      c->seg_base += R;
+    }
+  }
+  return RIDC_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -693,7 +731,7 @@ extern "C" int ridc_get_level(ridc_handle h, int level, double* out, size_t coun
   if (!c || !out || level < 0 || level >= c->P || count != (size_t)c->plane) return RIDC_ERR_ARG;
   if (!c->initialised) return RIDC_ERR_ARG;
   RIDC_TRY(check_device_error(c));
-  if (step) *step = c->p[level];
+  if (step) *step = c->seg_base + c->p[level];
   return copy_out(c, slot_ptr(c, c->eta[level], level, c->p[level]), out, count, out_on_device);
 }
 
@@ -706,14 +744,131 @@ extern "C" int ridc_get_solution(ridc_handle h, double* out, size_t count, int o
 extern "C" int ridc_get_time(ridc_handle h, double* t) {
   Ctx* c = ctx_of(h);
   if (!c || !t) return RIDC_ERR_ARG;
-  *t = (double)c->p[c->P - 1] * c->dt;
+  *t = (double)(c->seg_base + c->p[c->P - 1]) * c->dt;
   return RIDC_OK;
 }
 
 extern "C" int ridc_get_progress(ridc_handle h, long* steps, int nlevels) {
   Ctx* c = ctx_of(h);
   if (!c || !steps || nlevels < 1 || nlevels > c->P) return RIDC_ERR_ARG;
-  for (int j = 0; j < nlevels; ++j) steps[j] = c->p[j];
+  for (int j = 0; j < nlevels; ++j) steps[j] = c->seg_base + c->p[j];
+  return RIDC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// checkpoint / resume
+// ------------------------------------------------------------------------------------------
+// A state is this header followed by the rings of levels 0..P-1, each as eta, f^N and (when
+// the level keeps it) f, every slot in slot order: cap[j] * plane FP64 values per field.
+struct StateHeader {
+  char magic[8];
+  int32_t version, kind, dim, n, S, P;
+  double dt, nu[kMaxSpecies], a, b, F, k;
+  int64_t restart_every, seg_base, p[kMaxOrder];
+  int32_t cap[kMaxOrder];
+  int32_t has_F[kMaxOrder];
+  uint64_t payload;
+};
+static const char kStateMagic[8] = {'R', 'I', 'D', 'C', 'S', 'T', 'A', 'T'};
+constexpr int32_t kStateVersion = 1;
+
+static uint64_t state_payload(const Ctx* c) {
+  uint64_t vals = 0;
+  for (int j = 0; j < c->P; ++j)
+    vals += (uint64_t)c->cap[j] * (uint64_t)c->plane * (c->Fq[j] ? 3u : 2u);
+  return vals * sizeof(double);
+}
+
+static void fill_header(const Ctx* c, StateHeader* hd) {
+  memset(hd, 0, sizeof(*hd));
+  memcpy(hd->magic, kStateMagic, sizeof(kStateMagic));
+  hd->version = kStateVersion;
+  hd->kind = c->kind; hd->dim = c->dim; hd->n = c->n; hd->S = c->S; hd->P = c->P;
+  hd->dt = c->dt;
+  for (int s = 0; s < kMaxSpecies; ++s) hd->nu[s] = (s < c->S) ? c->nu[s] : 0.0;
+  hd->a = c->a; hd->b = c->b; hd->F = c->gsF; hd->k = c->gsk;
+  hd->restart_every = c->restart_every;
+  hd->seg_base = c->seg_base;
+  for (int j = 0; j < kMaxOrder; ++j) {
+    hd->p[j] = (j < c->P) ? c->p[j] : 0;
+    hd->cap[j] = (j < c->P) ? c->cap[j] : 0;
+    hd->has_F[j] = (j < c->P && c->Fq[j]) ? 1 : 0;
+  }
+  hd->payload = state_payload(c);
+}
+
+extern "C" int ridc_save_state(ridc_handle h, void* buf, size_t* len) {
+  Ctx* c = ctx_of(h);
+  if (!c || !len) return RIDC_ERR_ARG;
+  if (!c->initialised) return RIDC_ERR_ARG;
+  const size_t need = sizeof(StateHeader) + state_payload(c);
+  if (!buf) {
+    *len = need;
+    return RIDC_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return RIDC_ERR_ARG;
+  }
+  RIDC_TRY(check_device_error(c));   // synchronises: the rings hold the finished state
+  StateHeader hd;
+  fill_header(c, &hd);
+  uint8_t* out = static_cast<uint8_t*>(buf);
+  memcpy(out, &hd, sizeof(hd));
+  size_t off = sizeof(hd);
+  const size_t ring_bytes_per_slot = (size_t)c->plane * sizeof(double);
+  for (int j = 0; j < c->P; ++j) {
+    const double* rings[3] = {c->eta[j], c->fN[j], c->Fq[j]};
+    for (const double* ring : rings) {
+      if (!ring) continue;
+      const size_t bytes = (size_t)c->cap[j] * ring_bytes_per_slot;
+      RIDC_CUDA(cudaMemcpy(out + off, ring, bytes, cudaMemcpyDeviceToHost));
+      off += bytes;
+    }
+  }
+  *len = need;
+  return RIDC_OK;
+}
+
+extern "C" int ridc_load_state(ridc_handle h, const void* buf, size_t len) {
+  Ctx* c = ctx_of(h);
+  if (!c || !buf || len < sizeof(StateHeader)) return RIDC_ERR_ARG;
+  StateHeader hd, mine;
+  memcpy(&hd, buf, sizeof(hd));
+  fill_header(c, &mine);
+  if (memcmp(hd.magic, kStateMagic, sizeof(kStateMagic)) != 0 || hd.version != kStateVersion)
+    return RIDC_ERR_ARG;
+  // same problem: every parameter the stored f^N and f depend on, bit for bit
+  if (hd.kind != mine.kind || hd.dim != mine.dim || hd.n != mine.n || hd.S != mine.S ||
+      hd.P != mine.P || memcmp(&hd.dt, &mine.dt, sizeof(double)) != 0 ||
+      memcmp(hd.nu, mine.nu, sizeof(hd.nu)) != 0 || memcmp(&hd.a, &mine.a, sizeof(double)) != 0 ||
+      memcmp(&hd.b, &mine.b, sizeof(double)) != 0 || memcmp(&hd.F, &mine.F, sizeof(double)) != 0 ||
+      memcmp(&hd.k, &mine.k, sizeof(double)) != 0 || hd.restart_every != mine.restart_every ||
+      memcmp(hd.cap, mine.cap, sizeof(hd.cap)) != 0 ||
+      memcmp(hd.has_F, mine.has_F, sizeof(hd.has_F)) != 0 || hd.payload != mine.payload)
+    return RIDC_ERR_ARG;
+  if (len < sizeof(StateHeader) + hd.payload) return RIDC_ERR_ARG;
+  for (int j = 0; j < c->P; ++j)
+    if (hd.p[j] < 0 || (j > 0 && hd.p[j] > hd.p[j - 1])) return RIDC_ERR_ARG;
+  if (hd.seg_base < 0 || (hd.restart_every > 0 && hd.p[c->P - 1] >= hd.restart_every))
+    return RIDC_ERR_ARG;
+  const uint8_t* in = static_cast<const uint8_t*>(buf);
+  size_t off = sizeof(hd);
+  const size_t ring_bytes_per_slot = (size_t)c->plane * sizeof(double);
+  for (int j = 0; j < c->P; ++j) {
+    double* rings[3] = {c->eta[j], c->fN[j], c->Fq[j]};
+    for (double* ring : rings) {
+      if (!ring) continue;
+      const size_t bytes = (size_t)c->cap[j] * ring_bytes_per_slot;
+      RIDC_CUDA(cudaMemcpyAsync(ring, in + off, bytes, cudaMemcpyHostToDevice, c->stream));
+      off += bytes;
+    }
+  }
+  // a pinned source is read asynchronously: finish before the caller may reuse buf
+  RIDC_CUDA(cudaStreamSynchronize(c->stream));
+  for (int j = 0; j < kMaxOrder; ++j) c->p[j] = (j < c->P) ? (long)hd.p[j] : 0;
+  c->seg_base = (long)hd.seg_base;
+  c->initialised = true;
   return RIDC_OK;
 }
 

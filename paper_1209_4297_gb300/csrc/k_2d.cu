@@ -384,11 +384,11 @@ int launch_ybfly(Ctx* c, int plane0, int nplanes, const float* in) {
   if (blocks > 152L * 16) blocks = 152L * 16;
   const long r0 = (long)plane0 * c->n;
   cudaEvent_t e0;
-  prof_begin(c, RIDC_KERNEL_RESIDUAL, &e0);
+  prof_begin(c, RIDC_KERNEL_YBFLY, &e0);
   // plane p's split operand starts at element p * n * n, like its unsplit form
   ybfly_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(in + r0 * c->n, c->yh + r0 * c->n,
                                                      c->yl + r0 * c->n, c->n, rows);
-  prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
+  prof_end(c, RIDC_KERNEL_YBFLY, e0);
   return cuda_status(cudaGetLastError());
 }
 

@@ -82,9 +82,12 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
 
-  // schedule state: steps taken by each level, top-level target of the current run
+  // schedule state: steps taken by each level since the current start (set_initial or the
+  // latest restart), and the top-level steps completed before that start
   long p[kMaxOrder] = {0};
   bool initialised = false;
+  long restart_every = 0;    // restart interval in top-level steps (0: none), Section III-E
+  long seg_base = 0;
 
   // quadrature weights w[j][m][i] (units of dt), exact rationals rounded to FP64
   std::vector<double> wq;   // [P][P][P]
