@@ -11,6 +11,8 @@ Grids:
 
 Workloads (the readings of the unstated details are listed in the design doc):
   * adv_diff_1d      N=256, a=1, nu=0.01, RIDC order 4, dt=1/512, T=1.
+  * adv_diff_upwind_1d  the paper's advection-diffusion run (dx=1/1000, T=40, upwind).
+  * burgers_1d       the paper's viscous Burgers run (dx=1/1000, T=1, Dirichlet walls).
   * gray_scott_2d    N x N, Du=2e-5, Dv=1e-5, F=0.04, k=0.06, dt=0.5.
   * ensemble_2d      512 Dirichlet advection-diffusion instances of uneven size.
   * adv_diff_2d      4096 x 4096 Dirichlet advection-diffusion, a=b=1, nu=1e-3.
@@ -31,7 +33,9 @@ def _rng(seed: int) -> np.random.Generator:
 @dataclass
 class Workload:
     """One synthetic problem instance: operator parameters, initial data and run length."""
-    kind: str                 # "adv_diff_1d_periodic" | "gray_scott_2d_neumann" | "adv_diff_2d_dirichlet"
+    kind: str                 # "adv_diff_1d_periodic" | "adv_diff_1d_upwind_periodic" |
+                              # "burgers_1d_dirichlet" | "gray_scott_2d_neumann" |
+                              # "adv_diff_2d_dirichlet"
     n: int                    # grid points per side
     dt: float
     nsteps: int
@@ -42,6 +46,7 @@ class Workload:
     b: float = 0.0            # advection velocity along y
     F: float = 0.0            # Gray-Scott feed rate
     k: float = 0.0            # Gray-Scott kill rate
+    restart_every: int = 0    # restart interval in steps (0: none)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -50,7 +55,7 @@ class Workload:
 
     @property
     def dim(self) -> int:
-        return 1 if self.kind == "adv_diff_1d_periodic" else 2
+        return 1 if self.kind.endswith("_1d_periodic") or self.kind.endswith("_1d_dirichlet") else 2
 
 
 def adv_diff_1d(n: int = 256, seed: int = 0, nsteps: int = 512, dt: float = 1.0 / 512,
@@ -65,6 +70,29 @@ def adv_diff_1d(n: int = 256, seed: int = 0, nsteps: int = 512, dt: float = 1.0 
         u0 += amp[kk] * np.sin(TWO_PI * (kk + 1) * x + phase[kk])
     return Workload("adv_diff_1d_periodic", n, dt, nsteps, order, (nu,), np.ascontiguousarray(u0),
                     a=a, meta={"modes": list(range(1, 9)), "amp": amp, "phase": phase})
+
+
+def adv_diff_upwind_1d(n: int = 1000, nsteps: int = 4000, T: float = 40.0, order: int = 4,
+                       a: float = -0.1, nu: float = 1e-3, restarts: int = 10) -> Workload:
+    """The paper's advection-diffusion run: u_t = 0.1 u_x + 1e-3 u_xx (a = -0.1 here), periodic,
+    dx = 1/1000, T = 40, u0 = 2 + sin(2 pi x), upwind advection, restarts splitting the run
+    into `restarts` equal intervals (0: none). Deterministic: no random draw."""
+    x = np.arange(n, dtype=np.float64) / n
+    u0 = 2.0 + np.sin(TWO_PI * x)
+    every = nsteps // restarts if restarts > 0 else 0
+    return Workload("adv_diff_1d_upwind_periodic", n, T / nsteps, nsteps, order, (nu,),
+                    np.ascontiguousarray(u0), a=a, restart_every=every)
+
+
+def burgers_1d(n: int = 999, nsteps: int = 2000, T: float = 1.0, order: int = 4,
+               nu: float = 1e-3) -> Workload:
+    """The paper's viscous Burgers run: u_t + (u^2/2)_x = 1e-3 u_xx, u(0) = u(1) = 0,
+    dx = 1/1000 (999 interior nodes), T = 1, u0 = sin(2 pi x) + sin(pi x) / 2, no restarts.
+    Deterministic: no random draw."""
+    x = np.arange(1, n + 1, dtype=np.float64) / (n + 1)
+    u0 = np.sin(TWO_PI * x) + 0.5 * np.sin(np.pi * x)
+    return Workload("burgers_1d_dirichlet", n, T / nsteps, nsteps, order, (nu,),
+                    np.ascontiguousarray(u0))
 
 
 def gray_scott_2d(n: int = 1024, seed: int = 0, nsteps: int = 2000, dt: float = 0.5,
@@ -152,6 +180,10 @@ def by_name(name: str, **kw) -> Workload:
     """Named workloads at their full sizes; keyword overrides shrink them for tests."""
     if name == "adv_diff_1d":
         return adv_diff_1d(**kw)
+    if name == "adv_diff_upwind_1d":
+        return adv_diff_upwind_1d(**kw)
+    if name == "burgers_1d":
+        return burgers_1d(**kw)
     if name == "gray_scott_1024":
         return gray_scott_2d(**{"n": 1024, "nsteps": 2000, **kw})
     if name == "gray_scott_2048":

@@ -18,8 +18,10 @@ eigenpairs of the Laplacians, the Gray-Scott fixed point and uniform-field ODE, 
 a matrix-exponential solution of the 2D Dirichlet problem.
 """
 from .quadrature import lagrange_weights, weight_table, stencil
-from .problems import AdvDiff1DPeriodic, GrayScott2DNeumann, AdvDiff2DDirichlet, from_workload
+from .problems import (AdvDiff1DPeriodic, AdvDiff1DUpwindPeriodic, Burgers1DDirichlet,
+                       GrayScott2DNeumann, AdvDiff2DDirichlet, from_workload)
 from .ridc import ridc_sequential, ridc_restarted, fbe
 
-__all__ = ["lagrange_weights", "weight_table", "stencil", "AdvDiff1DPeriodic", "GrayScott2DNeumann",
+__all__ = ["lagrange_weights", "weight_table", "stencil", "AdvDiff1DPeriodic",
+           "AdvDiff1DUpwindPeriodic", "Burgers1DDirichlet", "GrayScott2DNeumann",
            "AdvDiff2DDirichlet", "from_workload", "ridc_sequential", "ridc_restarted", "fbe"]

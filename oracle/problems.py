@@ -9,6 +9,7 @@ Each problem gives, in plain FP64 numpy:
 Grids and boundary ghosts (the paper treats 1D periodic and 1D Dirichlet problems; the
 2D cell-centred conventions are readings):
   * 1D periodic: x_i = i h, h = 1/N, neighbours wrap around.
+  * 1D Dirichlet (Burgers): interior nodes x_i = i h, h = 1/(N+1), zero wall ghosts.
   * 2D Neumann:  cell centres (i + 1/2) h, even ghost u_{-1} = u_0, u_N = u_{N-1}.
   * 2D Dirichlet: cell centres, odd ghost u_{-1} = -u_0, u_N = -u_{N-1} (zero on the wall).
 Arrays are [x] in 1D and [species][y][x] in 2D.
@@ -45,6 +46,54 @@ class AdvDiff1DPeriodic:
 
     def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
         # dense LU with partial pivoting of the circulant I - dt D, factored once per dt
+        if dt not in self._lu:
+            self._lu[dt] = scipy.linalg.lu_factor(np.eye(self.n) - dt * self.matrix_D())
+        return scipy.linalg.lu_solve(self._lu[dt], r)
+
+
+class AdvDiff1DUpwindPeriodic(AdvDiff1DPeriodic):
+    """The paper's advection-diffusion example (Section IV-A) on periodic [0,1): advection by
+    first-order upwind differences, diffusion by centred differences. Written here as
+    u_t + a u_x = nu u_xx (the paper's u_t = c u_x + d u_xx is a = -c, nu = d):
+        a >= 0:  f^N_i = -a (u_i - u_{i-1}) / h,    a < 0:  f^N_i = -a (u_{i+1} - u_i) / h."""
+
+    def fN(self, u: np.ndarray) -> np.ndarray:
+        if self.a >= 0.0:
+            return -self.a * (u - np.roll(u, 1)) / self.h
+        return -self.a * (np.roll(u, -1) - u) / self.h
+
+
+class Burgers1DDirichlet:
+    """Viscous Burgers, u_t + (u^2 / 2)_x = nu u_xx on [0,1] with u(0) = u(1) = 0 (Section
+    IV-B). Unknowns at the n interior nodes x_i = i h, h = 1/(n+1), i = 1..n. The paper's
+    numerical flux f_{i+1/2} = (u_{i+1}^2 + u_i^2) / 2 gives
+        f^N_i = -(1/2) (f_{i+1/2} - f_{i-1/2}) / h,
+    and D = nu L with the centred second difference; the wall values are the zero ghosts."""
+
+    def __init__(self, n: int, nu: float):
+        self.n, self.nu = n, float(nu)
+        self.h = 1.0 / (n + 1)
+        self._lu: dict[float, tuple] = {}
+
+    def _ghosted(self, u: np.ndarray) -> np.ndarray:
+        return np.concatenate(([0.0], u, [0.0]))
+
+    def fN(self, u: np.ndarray) -> np.ndarray:
+        g = self._ghosted(u)
+        flux = 0.5 * (g[1:] ** 2 + g[:-1] ** 2)          # f_{i+1/2}, i = 0..n
+        return -0.5 * (flux[1:] - flux[:-1]) / self.h
+
+    def D(self, u: np.ndarray) -> np.ndarray:
+        g = self._ghosted(u)
+        return self.nu * (g[2:] - 2.0 * g[1:-1] + g[:-2]) / self.h ** 2
+
+    def matrix_D(self) -> np.ndarray:
+        n = self.n
+        L = -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+        return self.nu * L / self.h ** 2
+
+    def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
+        # dense LU with partial pivoting of I - dt D, factored once per dt
         if dt not in self._lu:
             self._lu[dt] = scipy.linalg.lu_factor(np.eye(self.n) - dt * self.matrix_D())
         return scipy.linalg.lu_solve(self._lu[dt], r)
@@ -141,6 +190,10 @@ def from_workload(w) -> object:
     """Build the oracle problem for an inputs.Workload."""
     if w.kind == "adv_diff_1d_periodic":
         return AdvDiff1DPeriodic(w.n, w.a, w.nu[0])
+    if w.kind == "adv_diff_1d_upwind_periodic":
+        return AdvDiff1DUpwindPeriodic(w.n, w.a, w.nu[0])
+    if w.kind == "burgers_1d_dirichlet":
+        return Burgers1DDirichlet(w.n, w.nu[0])
     if w.kind == "gray_scott_2d_neumann":
         return GrayScott2DNeumann(w.n, w.nu[0], w.nu[1], w.F, w.k)
     if w.kind == "adv_diff_2d_dirichlet":
