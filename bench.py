@@ -288,6 +288,8 @@ def run_ensemble(args):
 def run_single(args):
     """One of the other single-instance workloads, timed like the default line (whole
     integrations, CUDA events, inputs resident): the 1D periodic workload (512 steps, FP64),
+    the paper's 1D runs (upwind advection-diffusion to T = 40 with 10 restart intervals;
+    viscous Burgers to T = 1),
     1024^2 Gray-Scott in FP64 (a truncated run: its 2000 steps take minutes) or the 4096^2
     Dirichlet workload (512 steps, mixed BF16x3 with 2 refinement passes)."""
     import torch
@@ -299,37 +301,61 @@ def run_single(args):
     stream = torch.cuda.current_stream()
     if args.workload == "adv_diff_1d":
         w, prec, nt = inputs.adv_diff_1d(), "fp64", 512
+    elif args.workload == "adv_diff_upwind_1d":
+        w, prec, nt = inputs.adv_diff_upwind_1d(), "fp64", 4000
+    elif args.workload == "burgers_1d":
+        w, prec, nt = inputs.burgers_1d(), "fp64", 2000
     elif args.workload == "gray_scott_1024_fp64":
         w, prec, nt = inputs.gray_scott_2d(n=1024, nsteps=2000), "fp64", args.nt_truncate
     else:
         w, prec, nt = inputs.adv_diff_2d(n=4096, nsteps=512), "mixed_bf16x3", 512
     u0 = torch.from_numpy(w.u0).cuda()
-    it = Integrator.from_workload(w, precision=prec, n_refine=2, stream=stream.cuda_stream)
-    for _ in range(args.warmup):
-        it.set_initial(u0)
-        it.advance(nt)
-    torch.cuda.synchronize()
-    times = []
-    launches0 = it.launch_count()
-    for _ in range(args.steps):
-        it.set_initial(u0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it.advance(nt)
-        e1.record(stream)
+
+    def timed(order):
+        it = Integrator.from_workload(w, precision=prec, n_refine=2, stream=stream.cuda_stream,
+                                      order=order)
+        for _ in range(args.warmup):
+            it.set_initial(u0)
+            it.advance(nt)
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    launches = it.launch_count() - launches0
-    it.close()
-    ms = statistics.median(times)
+        times = []
+        launches0 = it.launch_count()
+        for _ in range(args.steps):
+            it.set_initial(u0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it.advance(nt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        launches = it.launch_count() - launches0
+        it.close()
+        return statistics.median(times), launches
+
+    ms, launches = timed(w.order)
+    # the paper's claim in one-GPU form: the whole RIDC-4 pipeline against plain FBE (one
+    # level) on the same workload and step count
+    fbe_ms = timed(1)[0] if w.dim == 1 else None
     cells = (w.n if w.dim == 1 else w.n * w.n) * nt
+    cpu = None
+    if w.dim == 1 and not args.no_cpu:
+        # the oracle on the whole workload (restarted where the workload restarts)
+        import oracle
+        t0 = time.perf_counter()
+        oracle.ridc_restarted(oracle.from_workload(w), w.u0, w.dt, nt, w.order, w.restart_every)
+        s = time.perf_counter() - t0
+        cpu = {"value": cells / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the whole workload ({s:.1f} s, numpy/scipy FP64, dense LU solves)"}
     line = {"metric": f"RIDC-{w.order} cell-updates/s", "value": cells / (ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "us_per_pipeline_step": 1e3 * ms / (nt + w.order * (w.order - 1) // 2),
             "higher_is_better": True, "dtype": "f64" if prec == "fp64" else "f64+bf16x3(fp32 acc)",
             "data": "synthetic", "gpu_launches": int(launches),
+            "fbe_ms": fbe_ms, "ridc_over_fbe_time": (ms / fbe_ms) if fbe_ms else None,
             "config": {"workload": args.workload, "grid": w.n, "order": w.order,
-                       "top_level_steps": nt, "full_steps": w.nsteps, "dt": w.dt}}
+                       "top_level_steps": nt, "full_steps": w.nsteps, "dt": w.dt,
+                       "restart_every": w.restart_every},
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -393,8 +419,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="gray_scott_2048",
-                    choices=["gray_scott_2048", "ensemble", "adv_diff_1d", "gray_scott_1024_fp64",
-                             "adv_diff_4096", "accuracy_2048"])
+                    choices=["gray_scott_2048", "ensemble", "adv_diff_1d", "adv_diff_upwind_1d",
+                             "burgers_1d", "gray_scott_1024_fp64", "adv_diff_4096",
+                             "accuracy_2048"])
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--ens-refine", type=int, default=1)
     ap.add_argument("--nt-truncate", type=int, default=60)

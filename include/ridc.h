@@ -49,7 +49,15 @@ typedef enum {
     RIDC_GRAY_SCOTT_2D_NEUMANN = 1,
     /* u_t + a u_x + b u_y = nu lap u on [0,1]^2, u = 0 on the walls, cell centres;
        f^N = -a u_x - b u_y by central differences.                                        */
-    RIDC_ADV_DIFF_2D_DIRICHLET = 2
+    RIDC_ADV_DIFF_2D_DIRICHLET = 2,
+    /* The paper's advection-diffusion example (Section IV-A): u_t + a u_x = nu u_xx on
+       periodic [0,1), nodes x_i = i/N, f^N by first-order upwind differences
+       (-a (u_i - u_{i-1})/h for a >= 0, -a (u_{i+1} - u_i)/h for a < 0).                */
+    RIDC_ADV_DIFF_1D_UPWIND_PERIODIC = 3,
+    /* The paper's viscous Burgers example (Section IV-B): u_t + (u^2/2)_x = nu u_xx on
+       [0,1], u(0) = u(1) = 0; N interior nodes x_i = i/(N+1), i = 1..N; f^N from the flux
+       f_{i+1/2} = (u_{i+1}^2 + u_i^2)/2: f^N_i = -(u_{i+1}^2 - u_{i-1}^2)/(4h).          */
+    RIDC_BURGERS_1D_DIRICHLET = 4
 } ridc_kind;
 
 typedef enum {
@@ -79,9 +87,11 @@ typedef struct {
 
 typedef struct {
     int dim;              /* 1 or 2; must match the kind                                     */
-    int n;                /* grid points per side: 1D a multiple of 32 (32 per warp lane
-                             chunk) with (2 order + 1) n <= 25600; 2D FP64 4 <= n <= 16384;
-                             2D mixed: n a multiple of 256, at most 4096                      */
+    int n;                /* unknowns per side: 1D n >= 8 with (2 L + 1) n256 <= 28000,
+                             L = ceil(order / min(order, 8)) levels per SM and n256 = n
+                             rounded up to a multiple of 256 (shared-memory rows; n <= 9216
+                             up to order 8); 2D FP64 4 <= n <= 16384; 2D mixed: n a
+                             multiple of 256, at most 4096                                   */
 } ridc_grid;
 
 typedef struct ridc_ctx* ridc_handle;   /* opaque; owned by the library                      */
@@ -237,6 +247,13 @@ void ridc_batch_destroy(ridc_batch b);
  * most `cap` entries and the number of pipeline steps to *count (RIDC_ERR_ARG if the
  * schedule is longer than cap; *count still set). 1 <= order <= 12.                        */
 int ridc_schedule_plan(int order, long nsteps, unsigned* active, size_t cap, size_t* count);
+
+/* The same plan continued from progress start[0..order) (steps taken by each level, as
+ * ridc_get_progress reports them within one start) until the top level reaches nsteps:
+ * what one ridc_advance call runs after earlier calls. RIDC_ERR_ARG if start is not a
+ * reachable progress (negative, a level ahead of the one below, or the top past nsteps). */
+int ridc_schedule_plan_from(int order, const long* start, long nsteps, unsigned* active,
+                            size_t cap, size_t* count);
 
 /* Quadrature weights w[j][m][i] of the corrector (Section III-C), FP64, computed exactly
  * in rational arithmetic and rounded: node i of the stencil t_b..t_{b+j}, interval

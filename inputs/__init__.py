@@ -55,7 +55,7 @@ class Workload:
 
     @property
     def dim(self) -> int:
-        return 1 if self.kind.endswith("_1d_periodic") or self.kind.endswith("_1d_dirichlet") else 2
+        return 1 if "_1d_" in self.kind else 2
 
 
 def adv_diff_1d(n: int = 256, seed: int = 0, nsteps: int = 512, dt: float = 1.0 / 512,

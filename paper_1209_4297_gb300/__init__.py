@@ -5,7 +5,7 @@ The integrator runs entirely in the CUDA kernels of libridc.so (built in-tree fo
 does not load the library; the first call does, and raises if the library is missing.
 """
 from .binding import (Batch, Integrator, RidcError, error_string, lib, quadrature_weights,
-                      schedule_plan, LIB_PATH, KERNELS)
+                      schedule_plan, schedule_plan_from, LIB_PATH, KERNELS)
 
 __all__ = ["Batch", "Integrator", "RidcError", "error_string", "lib", "quadrature_weights",
-           "schedule_plan", "LIB_PATH", "KERNELS"]
+           "schedule_plan", "schedule_plan_from", "LIB_PATH", "KERNELS"]

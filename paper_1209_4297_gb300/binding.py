@@ -16,7 +16,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libridc.so")
 
-KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dirichlet": 2}
+KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dirichlet": 2,
+         "adv_diff_1d_upwind_periodic": 3, "burgers_1d_dirichlet": 4}
+KINDS_1D = ("adv_diff_1d_periodic", "adv_diff_1d_upwind_periodic", "burgers_1d_dirichlet")
 PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1, "fp32_solve": 2}
 KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5,
            "ybfly": 6}
@@ -66,6 +68,7 @@ def lib() -> ctypes.CDLL:
         "ridc_save_state": (i, [vp, vp, POINTER(sz)]),
         "ridc_load_state": (i, [vp, vp, sz]),
         "ridc_schedule_plan": (i, [i, lg, POINTER(c_uint), sz, POINTER(sz)]),
+        "ridc_schedule_plan_from": (i, [i, POINTER(lg), lg, POINTER(c_uint), sz, POINTER(sz)]),
         "ridc_quadrature_weights": (i, [i, POINTER(c_double), sz]),
         "ridc_set_profiling": (i, [vp, i]),
         "ridc_get_kernel_stats": (i, [vp, i, POINTER(lg), POINTER(d)]),
@@ -126,6 +129,19 @@ def schedule_plan(order: int, nsteps: int) -> np.ndarray:
     return np.array(out[:cnt.value], dtype=np.uint32)
 
 
+def schedule_plan_from(order: int, start, nsteps: int) -> np.ndarray:
+    """Masks of the lock-step schedule continued from per-level progress `start` until the
+    top level has taken nsteps steps."""
+    st = (c_long * order)(*[int(v) for v in start])
+    cnt = c_size_t(0)
+    L = lib()
+    L.ridc_schedule_plan_from(order, st, nsteps, None, 0, byref(cnt))
+    out = (c_uint * max(cnt.value, 1))()
+    _check(L.ridc_schedule_plan_from(order, st, nsteps, out, cnt.value, byref(cnt)),
+           "ridc_schedule_plan_from")
+    return np.array(out[:cnt.value], dtype=np.uint32)
+
+
 def quadrature_weights(order: int) -> np.ndarray:
     """w[j][m][i] as computed by the library (exact rationals rounded to FP64)."""
     buf = (c_double * (order ** 3))()
@@ -144,7 +160,7 @@ class Integrator:
         self._h = c_void_p(None)
         nu = np.atleast_1d(np.asarray(nu, dtype=np.float64))
         pr = Problem(KINDS[kind], a, b, F, k, PRECISIONS[precision], n_refine, restart_every)
-        gr = Grid(1 if kind == "adv_diff_1d_periodic" else 2, n)
+        gr = Grid(1 if kind in KINDS_1D else 2, n)
         if stream is None:
             stream = _current_stream()
         self.kind, self.n, self.order, self.dt = kind, n, order, dt
@@ -156,10 +172,12 @@ class Integrator:
 
     @classmethod
     def from_workload(cls, w, precision: str = "fp64", n_refine: int = 2, stream=None,
-                      order: int | None = None, restart_every: int = 0):
+                      order: int | None = None, restart_every: int | None = None):
+        """Integrator for an inputs.Workload; restart_every defaults to the workload's."""
         return cls(w.kind, w.n, w.nu, w.dt, order or w.order, a=w.a, b=w.b, F=w.F, k=w.k,
-                   precision=precision, n_refine=n_refine, restart_every=restart_every,
-                   stream=stream)
+                   precision=precision, n_refine=n_refine,
+                   restart_every=(getattr(w, "restart_every", 0) if restart_every is None
+                                  else restart_every), stream=stream)
 
     def close(self) -> None:
         if self._h:

@@ -252,20 +252,37 @@ static int build_tables_2d(Ctx* c) {
   return RIDC_OK;
 }
 
-// Cyclic tridiagonal (I - dt nu L) with L the periodic second difference: diagonal 1 + 2 mu,
-// off-diagonals -mu, mu = nu dt / h^2. It factors as (mu/rho)(1 - rho E)(1 - rho E^-1) with the
-// cyclic shift E and rho the root in (0, 1) of mu rho^2 - (1 + 2 mu) rho + mu = 0, written
-// without cancellation as rho = 2 mu / (1 + 2 mu + sqrt(1 + 4 mu)).
-// Layout tri[0..n]: rho^k, [n+1]: 1 / (1 - rho^n), [n+2]: rho / mu, then the weights.
+static bool is_1d_dirichlet(int kind) { return kind == RIDC_BURGERS_1D_DIRICHLET; }
+
+// (I - dt nu L) with L the second difference: diagonal 1 + 2 mu, off-diagonals -mu,
+// mu = nu dt / h^2. With the shift (S x)_j = x_{j+1} and rho the root in (0, 1) of
+// mu rho^2 - (1 + 2 mu) rho + mu = 0 (written without cancellation as
+// rho = 2 mu / (1 + 2 mu + sqrt(1 + 4 mu))), M = (mu/rho)(1 - rho S)(1 - rho S^T) equals
+//   periodic  (cyclic S):        the matrix itself;
+//   Dirichlet (S x)_{n-1} = 0:   the matrix minus mu rho e_{n-1} e_{n-1}^T,
+// so the Dirichlet solve is M^-1 plus a Sherman-Morrison correction along g = M^-1 e_{n-1}:
+//   x = y - kappa y_{n-1} g,  y = M^-1 r,  kappa = mu rho / (1 + mu rho g_{n-1}).
 static int build_tables_1d(Ctx* c) {
-  const int n = c->n;
+  const int n = c->n, npad = c->npad;
   const double mu = c->nu[0] * c->dt / (c->h * c->h);
   const double rho = 2.0 * mu / (1.0 + 2.0 * mu + std::sqrt(1.0 + 4.0 * mu));
-  std::vector<double> tri((size_t)n + 3 + (size_t)c->P * c->P * c->P, 0.0);
-  for (int k = 0; k <= n; ++k) tri[k] = std::pow(rho, (double)k);
-  tri[n + 1] = 1.0 / (1.0 - tri[n]);
-  tri[n + 2] = rho / mu;
-  fill_weights(c->P, tri.data() + n + 3);
+  const double s = rho / mu;
+  std::vector<double> tri((size_t)npad + 3 + (size_t)n + (size_t)c->P * c->P * c->P, 0.0);
+  for (int k = 0; k <= npad; ++k) tri[k] = std::pow(rho, (double)k);
+  tri[npad + 2] = s;
+  if (is_1d_dirichlet(c->kind)) {
+    // g = M^-1 e_{n-1}: z_j = rho^(n-1-j), then g_j = s z_j + rho g_{j-1}
+    double* gv = tri.data() + npad + 3;
+    double prev = 0.0;
+    for (int j = 0; j < n; ++j) {
+      prev = s * std::pow(rho, (double)(n - 1 - j)) + rho * prev;
+      gv[j] = prev;
+    }
+    tri[npad + 1] = mu * rho / (1.0 + mu * rho * gv[n - 1]);
+  } else {
+    tri[npad + 1] = 1.0 / (1.0 - std::pow(rho, (double)n));
+  }
+  fill_weights(c->P, tri.data() + npad + 3 + n);
   return upload(c, &c->tri, tri);
 }
 
@@ -296,7 +313,8 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
   c->stream = (cudaStream_t)stream;
   c->S = (pr->kind == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
   for (int s = 0; s < c->S; ++s) c->nu[s] = nu[s];
-  c->h = 1.0 / c->n;
+  c->h = is_1d_dirichlet(c->kind) ? 1.0 / (c->n + 1) : 1.0 / c->n;
+  c->npad = oned_npad(c->n);
   RIDC_CUDA(cudaGetDevice(&c->device));
 
   const long n = c->n;
@@ -360,17 +378,19 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
   if (order < 1 || order > kMaxOrder) return RIDC_ERR_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return RIDC_ERR_ARG;
   if (pr->restart_every < 0) return RIDC_ERR_ARG;
-  if (pr->kind < 0 || pr->kind > 2) return RIDC_ERR_ARG;
+  if (pr->kind < 0 || pr->kind > 4) return RIDC_ERR_ARG;
   if (pr->precision != RIDC_FP64 && pr->precision != RIDC_MIXED_BF16X3) return RIDC_ERR_ARG;
   if (pr->n_refine < 0 || pr->n_refine > 4) return RIDC_ERR_ARG;
   const int S = (pr->kind == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
   for (int s = 0; s < S; ++s)
     if (!(nu[s] > 0.0) || !std::isfinite(nu[s])) return RIDC_ERR_ARG;
-  if (pr->kind == RIDC_ADV_DIFF_1D_PERIODIC) {
-    if (g->dim != 1 || g->n < 32) return RIDC_ERR_ARG;
+  if (pr->kind == RIDC_ADV_DIFF_1D_PERIODIC || pr->kind == RIDC_ADV_DIFF_1D_UPWIND_PERIODIC ||
+      pr->kind == RIDC_BURGERS_1D_DIRICHLET) {
+    if (g->dim != 1 || g->n < 8) return RIDC_ERR_ARG;
     if (pr->precision != RIDC_FP64) return RIDC_ERR_UNSUPPORTED;
-    if ((2L * order + 1) * g->n > 25600) return RIDC_ERR_UNSUPPORTED;   // shared-memory bound
-    if (g->n % 32 != 0) return RIDC_ERR_UNSUPPORTED;   // one chunk per lane of a warp
+    // shared-memory rows of the levels one CTA carries
+    if (oned_smem_doubles(order, g->n, oned_npad(g->n)) > kOneDMaxSmemDoubles)
+      return RIDC_ERR_UNSUPPORTED;
   } else {
     if (g->dim != 2 || g->n < 4) return RIDC_ERR_ARG;
     if (pr->precision == RIDC_MIXED_BF16X3 && ((g->n % 256) != 0 || g->n > 4096))
@@ -877,9 +897,20 @@ extern "C" int ridc_load_state(ridc_handle h, const void* buf, size_t len) {
 // ------------------------------------------------------------------------------------------
 extern "C" int ridc_schedule_plan(int order, long nsteps, unsigned* active, size_t cap,
                                   size_t* count) {
-  if (order < 1 || order > kMaxOrder || nsteps < 0 || !count || (cap && !active))
+  const long zero[kMaxOrder] = {0};
+  return ridc_schedule_plan_from(order, zero, nsteps, active, cap, count);
+}
+
+extern "C" int ridc_schedule_plan_from(int order, const long* start, long nsteps,
+                                       unsigned* active, size_t cap, size_t* count) {
+  if (order < 1 || order > kMaxOrder || nsteps < 0 || !start || !count || (cap && !active))
     return RIDC_ERR_ARG;
   long p[kMaxOrder] = {0};
+  for (int j = 0; j < order; ++j) {
+    p[j] = start[j];
+    if (p[j] < 0 || (j > 0 && p[j] > p[j - 1])) return RIDC_ERR_ARG;
+  }
+  if (p[order - 1] > nsteps) return RIDC_ERR_ARG;
   size_t s = 0;
   for (;;) {
     const unsigned m = plan_step(order, p, nsteps);

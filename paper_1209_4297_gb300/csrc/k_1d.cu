@@ -1,13 +1,18 @@
-// Persistent single-CTA kernel for 1D periodic advection-diffusion: one launch runs every
-// pipeline step of an advance call. The level rings stay in global memory (a few KB, L1/L2
-// resident); right-hand sides, the tridiagonal sweeps and the new states live in shared
-// memory. Per pipeline step, for every advancing level j (step n -> n+1):
+// Persistent kernel for the 1D problems (periodic advection-diffusion with central or
+// upwind advection, viscous Burgers with Dirichlet walls): one launch runs every pipeline
+// step of an advance call. The paper gives every correction level its own processor
+// (Section III-E); here every level gets its own SM: a thread-block cluster of
+// min(order, 8) CTAs, CTA r taking levels r, r + 8, ... The level rings stay in global
+// memory (L2 resident); right-hand sides, the tridiagonal solves and the new states live
+// in shared memory. Within a pipeline step the levels are independent (the lock-step rule
+// never writes a ring slot that any level reads in the same step), so one cluster barrier
+// per step orders the whole exchange. Per step, for every advancing level j (n -> n+1):
 //   r   = dt F^0_n                                                    (j = 0, eq. (pred))
 //   r   = (eta^j_n - eta^{j-1}_{n+1}) + dt (f^N(eta^j_n) - f^N(eta^{j-1}_n))
 //         + dt sum_i w[j][m][i] F^{j-1}_{b+i}                          (j >= 1, eq. (corr))
-//   solve (I - dt nu L) delta = r   (cyclic tridiagonal: two warp-parallel recurrences)
+//   solve (I - dt nu L) delta = r   (two warp-parallel first-order recurrences)
 //   eta^j_{n+1} = base + delta, base = eta^0_n (j = 0) or eta^{j-1}_{n+1}
-//   f^N = -a (eta_{i+1} - eta_{i-1}) / 2h,  F = f^N + nu (eta_{i+1} - 2 eta_i + eta_{i-1}) / h^2
+//   f^N(eta) (Section IV's operators) and F = f^N + nu (eta_{i+1} - 2 eta_i + eta_{i-1}) / h^2
 // The step masks come from the host's plan of the same lock-step rule.
 #include "ridc_internal.h"
 
@@ -19,121 +24,196 @@ struct OneDArgs {
   double* F[kMaxOrder];
   int cap[kMaxOrder];
   const double* wq;        // [P][P][P]
-  const double* tri;       // rho^k (k = 0..n), 1/(1 - rho^n), rho/mu, then the weights
+  const double* tri;       // rho^k (k = 0..npad), wrap or kappa, rho/mu, g, weights
   const unsigned* sched;   // step masks
   long nsteps_pipe;
   long* p_dev;             // steps taken per level (read at start, written at the end)
-  int P, n, init_only;
-  double dt, a2h, c_lap;
+  int P, n, npad, init_only, kind;
+  double dt, c_lap;
+  double cadv;             // central: a/(2h); upwind: a/h; Burgers: 1/(4h)
+  bool upwind_left;        // upwind with a >= 0: backward difference
 };
 
-__device__ __forceinline__ void eval_state(const double* e, double* fN, double* F, int n,
-                                           double a2h, double c_lap) {
+// f^N and F of one state; periodic wrap or zero Dirichlet ghosts
+__device__ __forceinline__ void eval_state(const OneDArgs& a, const double* e, double* fN,
+                                           double* F) {
+  const int n = a.n;
+  const bool dir = a.kind == RIDC_BURGERS_1D_DIRICHLET;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double em = e[i == 0 ? n - 1 : i - 1], ep = e[i == n - 1 ? 0 : i + 1], ei = e[i];
-    const double fn = -a2h * (ep - em);
+    double em, ep;
+    if (dir) {
+      em = i > 0 ? e[i - 1] : 0.0;
+      ep = i < n - 1 ? e[i + 1] : 0.0;
+    } else {
+      em = e[i == 0 ? n - 1 : i - 1];
+      ep = e[i == n - 1 ? 0 : i + 1];
+    }
+    const double ei = e[i];
+    double fn;
+    if (a.kind == RIDC_ADV_DIFF_1D_PERIODIC) fn = -a.cadv * (ep - em);
+    else if (a.kind == RIDC_ADV_DIFF_1D_UPWIND_PERIODIC)
+      fn = a.upwind_left ? -a.cadv * (ei - em) : -a.cadv * (ep - ei);
+    else fn = -a.cadv * fma(ep, ep, -(em * em));
     fN[i] = fn;
-    if (F) F[i] = fma(c_lap, (ep + em) - 2.0 * ei, fn);
+    if (F) F[i] = fma(a.c_lap, (ep + em) - 2.0 * ei, fn);
   }
 }
 
-// Cyclic solve of (I - dt nu L) x = r for one level by one warp. The periodic tridiagonal
-// matrix (diagonal 1 + 2mu, off-diagonals -mu) factors as (mu/rho)(1 - rho E)(1 - rho E^-1)
-// with the cyclic shift (E x)_j = x_{j+1} and rho = 2mu / (1 + 2mu + sqrt(1 + 4mu)) < 1, so
-//   z = (1 - rho E)^-1 r      : z_j = r_j + rho z_{j+1}          (backward, cyclic)
-//   x = (rho/mu)(1 - rho E^-1)^-1 z : x_j = (rho/mu) z_j + rho x_{j-1}   (forward, cyclic)
-// Each first-order recurrence is a scan: every lane runs its chunk of N/32 values, a 5-step
-// shuffle scan combines the chunk carries with weights rho^(chunk * 2^k), and the cyclic wrap
-// is exact: z_cyc_j = z_j + rho^(N-j) z_0 / (1 - rho^N), x_cyc_j = x_j + rho^(j+1) x_{N-1} / (1 - rho^N).
-// The dependent FP64 chain is about 30 operations instead of the 2N of a Thomas sweep.
-__device__ void cyclic_solve_warp(double* r, int n, const double* rp, double inv_wrap, double s) {
-  const int lane = threadIdx.x & 31;
-  const int m = n >> 5;
-  const int j0 = lane * m;
-  const double rho = rp[1];
-  // backward recurrence, local part: t_j = r_j + rho t_{j+1}, t_{j0+m} = 0
+// Solve of (I - dt nu L) x = r for one level by the whole block, in place on r[0, npad).
+// With the shift S and rho = 2mu / (1 + 2mu + sqrt(1 + 4mu)) < 1,
+// M = (mu/rho)(1 - rho S)(1 - rho S^T):
+//   z = (1 - rho S)^-1 r      : z_j = r_j + rho z_{j+1},  z_n = 0           (backward)
+//   y = (rho/mu)(1 - rho S^T)^-1 z : y_j = (rho/mu) z_j + rho y_{j-1},  y_{-1} = 0  (forward)
+// Each first-order recurrence is a scan over the block: every thread runs its chunk of
+// m = npad / blockDim values, a 5-step shuffle scan combines the chunk carries of a warp with
+// weights rho^(m 2^k), and the warps' totals are chained through shared memory. Entries
+// past n are zero on entry, so the backward scan ends with z_n = 0 and the forward scan only
+// leaves values past n, which nothing reads. Then
+//   periodic  (cyclic S, M is the matrix): exact wrap terms make both recurrences cyclic,
+//             z_j += rho^(n-j) z_0 / (1 - rho^n),  y_j += rho^(j+1) y_{n-1} / (1 - rho^n);
+//   Dirichlet (the matrix is M + mu rho e_{n-1} e_{n-1}^T): Sherman-Morrison,
+//             x_j = y_j - kappa y_{n-1} g_j with the tabulated g = M^-1 e_{n-1}.
+// Spreading the chunks over all warps uses the FP64 pipes of all four SM partitions.
+__device__ void tri_solve_block(double* r, int n, int npad, const double* rp, double corr,
+                                double s, const double* gvec, bool cyclic, double* scratch) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NW = blockDim.x >> 5;
+  const int m = npad / blockDim.x;
+  const int j0 = tid * m;
+  const double rho = rp[1], rho_w = rp[32 * m];   // rho^m per lane, rho^(32 m) per warp
+  for (int i = 0; i < m; ++i)
+    if (j0 + i >= n) r[j0 + i] = 0.0;
+  // ---- backward recurrence, local part: t_j = r_j + rho t_{j+1}, t_{j0+m} = 0
   double t = 0.0;
   for (int i = m - 1; i >= 0; --i) {
     t = fma(rho, t, r[j0 + i]);
     r[j0 + i] = t;
   }
-  // carry C_l = z_{l m} = t_{l m} + rho^m C_{l+1}: reverse inclusive scan over the lanes
+  // carries within the warp: C_l = t_{l m} + rho^m C_{l+1} (reverse inclusive scan)
   double C = t;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const double up = __shfl_down_sync(0xffffffffu, C, d);
     if (lane + d < 32) C = fma(rp[m * d], up, C);
   }
-  const double z0 = __shfl_sync(0xffffffffu, C, 0) * inv_wrap;   // cyclic z_0
+  if (lane == 0) scratch[w] = C;   // the warp's chunk of z, without what lies above it
+  __syncthreads();
+  // z at the first index of warp w+1: Z = C_{w+1} + rho^(32m) Z_{w+2}
+  double Z = 0.0;
+  for (int v = NW - 1; v > w; --v) Z = fma(rho_w, Z, scratch[v]);
+  C = fma(rp[m * (32 - lane)], Z, C);           // full carry: z at this thread's first index
+  if (tid == 0) scratch[NW] = C;                // non-cyclic z_0
   double Cnext = __shfl_down_sync(0xffffffffu, C, 1);
-  if (lane == 31) Cnext = 0.0;
-  __syncwarp();
+  if (lane == 31) Cnext = Z;
+  __syncthreads();
+  const double z0 = scratch[NW] * corr;         // cyclic z_0 (periodic only)
   for (int i = 0; i < m; ++i) {
     const int j = j0 + i;
-    r[j] = fma(rp[n - j], z0, fma(rp[m - i], Cnext, r[j]));
+    double v = fma(rp[m - i], Cnext, r[j]);
+    if (cyclic && j < n) v = fma(rp[n - j], z0, v);
+    r[j] = v;
   }
-  __syncwarp();
-  // forward recurrence, local part: t_j = s z_j + rho t_{j-1}, t_{j0-1} = 0
+  // ---- forward recurrence, local part: t_j = s z_j + rho t_{j-1}, t_{j0-1} = 0
   t = 0.0;
   for (int i = 0; i < m; ++i) {
     t = fma(rho, t, s * r[j0 + i]);
     r[j0 + i] = t;
   }
-  // carry D_l = x_{(l+1)m-1} = t_{(l+1)m-1} + rho^m D_{l-1}: inclusive scan over the lanes
+  // carries within the warp: D_l = t_{(l+1)m-1} + rho^m D_{l-1} (inclusive scan)
   double D = t;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const double dn = __shfl_up_sync(0xffffffffu, D, d);
     if (lane >= d) D = fma(rp[m * d], dn, D);
   }
-  const double xl = __shfl_sync(0xffffffffu, D, 31) * inv_wrap;  // cyclic x_{N-1}
+  if (lane == 31) scratch[w] = D;
+  __syncthreads();
+  // y at the last index of warp w-1: Y = D_{w-1} + rho^(32m) Y_{w-2}
+  double Y = 0.0;
+  for (int v = 0; v < w; ++v) Y = fma(rho_w, Y, scratch[v]);
+  D = fma(rp[m * (lane + 1)], Y, D);            // full carry: y at this thread's last index
   double Dprev = __shfl_up_sync(0xffffffffu, D, 1);
-  if (lane == 0) Dprev = 0.0;
-  __syncwarp();
-  for (int i = 0; i < m; ++i) {
-    const int j = j0 + i;
-    r[j] = fma(rp[j + 1], xl, fma(rp[i + 1], Dprev, r[j]));
+  if (lane == 0) Dprev = Y;
+  for (int i = 0; i < m; ++i) r[j0 + i] = fma(rp[i + 1], Dprev, r[j0 + i]);
+  __syncthreads();
+  const double yl = r[n - 1];   // y_{n-1}, written by another thread
+  __syncthreads();
+  if (cyclic) {
+    const double wv = yl * corr;
+    for (int i = 0; i < m; ++i) {
+      const int j = j0 + i;
+      if (j < n) r[j] = fma(rp[j + 1], wv, r[j]);
+    }
+  } else {
+    const double wv = -corr * yl;
+    for (int i = 0; i < m; ++i) {
+      const int j = j0 + i;
+      if (j < n) r[j] = fma(wv, gvec[j], r[j]);
+    }
   }
-  __syncwarp();
+  __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) ridc1d_kernel(const __grid_constant__ OneDArgs a) {
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// every thread of every CTA of the cluster; release/acquire orders the ring writes in
+// global memory (and shared memory) before the other CTAs' reads in the next step
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_constant__ OneDArgs a) {
   extern __shared__ double sm[];
-  const int n = a.n, P = a.P;
-  double* R = sm;                    // [P][n] right-hand sides, then solutions
-  double* E = sm + (size_t)P * n;    // [P][n] new states
-  double* rp = E + (size_t)P * n;    // [n+1] powers rho^k
+  const int n = a.n, P = a.P, npad = a.npad;
+  const int rank = (int)cluster_rank(), CL = (int)cluster_size();
+  const int L = (P + CL - 1) / CL;      // levels of this CTA at most
+  double* R = sm;                       // [L][npad] right-hand sides, then solutions
+  double* E = sm + (size_t)L * npad;    // [L][n] new states
+  double* rp = E + (size_t)L * n;       // [npad+1] powers rho^k
   __shared__ long p[kMaxOrder];
   __shared__ int lev[kMaxOrder];
   __shared__ int na;
+  __shared__ double scratch[ONED_THREADS / 32 + 1];
 
   if (a.init_only) {
-    eval_state(a.eta[0], a.fN[0], a.F[0], n, a.a2h, a.c_lap);
+    if (rank == 0) eval_state(a, a.eta[0], a.fN[0], a.F[0]);
     return;
   }
-  for (int i = threadIdx.x; i <= n; i += blockDim.x) rp[i] = a.tri[i];
+  for (int i = threadIdx.x; i <= npad; i += blockDim.x) rp[i] = a.tri[i];
   if (threadIdx.x < kMaxOrder) p[threadIdx.x] = a.p_dev[threadIdx.x];
-  const double inv_wrap = a.tri[n + 1], sfac = a.tri[n + 2];
+  const double corr = a.tri[npad + 1], sfac = a.tri[npad + 2];
+  const double* gvec = a.tri + npad + 3;
+  const bool cyclic = a.kind != RIDC_BURGERS_1D_DIRICHLET;
   __syncthreads();
-  const int warp = threadIdx.x >> 5;
 
   for (long s = 0; s < a.nsteps_pipe; ++s) {
     const unsigned mask = a.sched[s];
     if (threadIdx.x == 0) {
       int k = 0;
-      for (int j = 0; j < P; ++j)
+      for (int j = rank; j < P; j += CL)
         if (mask & (1u << j)) lev[k++] = j;
       na = k;
     }
     __syncthreads();
-    // right-hand sides
+    // right-hand sides of this CTA's advancing levels
     for (int q = 0; q < na; ++q) {
       const int j = lev[q];
       const long nj = p[j];
-      double* r = R + (size_t)q * n;
+      double* r = R + (size_t)q * npad;
+      // ring reads bypass L1 (__ldcg): other SMs of the cluster wrote them
       if (j == 0) {
         const double* F0 = a.F[0] + (nj % a.cap[0]) * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = a.dt * F0[i];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = a.dt * __ldcg(F0 + i);
       } else {
         const double* ej = a.eta[j] + (nj % a.cap[j]) * n;
         const double* fj = a.fN[j] + (nj % a.cap[j]) * n;
@@ -143,25 +223,24 @@ __global__ void __launch_bounds__(256) ridc1d_kernel(const __grid_constant__ One
         const int m = (int)(nj - b);
         const double* w = a.wq + ((size_t)j * P + m) * P;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          double acc = fma(a.dt, fj[i] - fp[i], ej[i] - ep[i]);
+          double acc = fma(a.dt, __ldcg(fj + i) - __ldcg(fp + i), __ldcg(ej + i) - __ldcg(ep + i));
           for (int k = 0; k <= j; ++k)
-            acc = fma(a.dt * w[k], a.F[j - 1][((b + k) % a.cap[j - 1]) * n + i], acc);
+            acc = fma(a.dt * w[k], __ldcg(a.F[j - 1] + ((b + k) % a.cap[j - 1]) * n + i), acc);
           r[i] = acc;
         }
       }
     }
     __syncthreads();
-    // cyclic solves, one warp per level
-    for (int q = warp; q < na; q += (int)(blockDim.x >> 5))
-      cyclic_solve_warp(R + (size_t)q * n, n, rp, inv_wrap, sfac);
-    __syncthreads();
+    for (int q = 0; q < na; ++q)
+      tri_solve_block(R + (size_t)q * npad, n, npad, rp, corr, sfac, gvec, cyclic, scratch);
     // new states
     for (int q = 0; q < na; ++q) {
       const int j = lev[q];
       const long nj = p[j];
       const double* base = (j == 0) ? a.eta[0] + (nj % a.cap[0]) * n
                                     : a.eta[j - 1] + ((nj + 1) % a.cap[j - 1]) * n;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) E[(size_t)q * n + i] = base[i] + R[(size_t)q * n + i];
+      for (int i = threadIdx.x; i < n; i += blockDim.x)
+        E[(size_t)q * n + i] = __ldcg(base + i) + R[(size_t)q * npad + i];
     }
     __syncthreads();
     for (int q = 0; q < na; ++q) {
@@ -169,14 +248,16 @@ __global__ void __launch_bounds__(256) ridc1d_kernel(const __grid_constant__ One
       const long slot = ((p[j] + 1) % a.cap[j]) * n;
       const double* e = E + (size_t)q * n;
       for (int i = threadIdx.x; i < n; i += blockDim.x) a.eta[j][slot + i] = e[i];
-      eval_state(e, a.fN[j] + slot, a.F[j] ? a.F[j] + slot : nullptr, n, a.a2h, a.c_lap);
+      eval_state(a, e, a.fN[j] + slot, a.F[j] ? a.F[j] + slot : nullptr);
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-      for (int q = 0; q < na; ++q) p[lev[q]]++;
+    if (threadIdx.x == 0)   // every CTA follows every level's progress
+      for (int j = 0; j < P; ++j)
+        if (mask & (1u << j)) p[j]++;
     __syncthreads();
+    cluster_sync_all();
   }
-  if (threadIdx.x < kMaxOrder) a.p_dev[threadIdx.x] = p[threadIdx.x];
+  if (rank == 0 && threadIdx.x < kMaxOrder) a.p_dev[threadIdx.x] = p[threadIdx.x];
 }
 
 int launch_1d(Ctx* c, long nsteps_pipe, int init_only) {
@@ -194,23 +275,43 @@ int launch_1d(Ctx* c, long nsteps_pipe, int init_only) {
   a.p_dev = c->p_dev;
   a.P = c->P;
   a.n = c->n;
+  a.npad = c->npad;
   a.init_only = init_only;
+  a.kind = c->kind;
   a.dt = c->dt;
-  a.a2h = c->a / (2.0 * c->h);
   a.c_lap = c->nu[0] / (c->h * c->h);
+  if (c->kind == RIDC_ADV_DIFF_1D_PERIODIC) a.cadv = c->a / (2.0 * c->h);
+  else if (c->kind == RIDC_ADV_DIFF_1D_UPWIND_PERIODIC) a.cadv = c->a / c->h;
+  else a.cadv = 1.0 / (4.0 * c->h);
+  a.upwind_left = c->a >= 0.0;
   // the quadrature weights follow the solver constants: uploaded once per handle
-  a.wq = c->tri + c->n + 3;
-  const size_t smem = ((size_t)2 * c->P * c->n + (size_t)c->n + 1) * sizeof(double);
-  if (smem > 48 * 1024) {
+  a.wq = c->tri + c->npad + 3 + c->n;
+  const int CL = init_only ? 1 : oned_cluster(c->P);
+  const size_t smem = oned_smem_doubles(c->P, c->n, c->npad) * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(ridc1d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)(kOneDMaxSmemDoubles * sizeof(double)));
     if (e != cudaSuccess) return cuda_status(e);
+    attr_done = true;
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(ONED_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_1D, &e0);
-  ridc1d_kernel<<<1, 256, smem, c->stream>>>(a);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, ridc1d_kernel, a);
   prof_end(c, RIDC_KERNEL_1D, e0);
-  return cuda_status(cudaGetLastError());
+  return cuda_status(e);
 }
 
 }  // namespace ridc

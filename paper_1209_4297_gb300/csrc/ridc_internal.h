@@ -124,8 +124,14 @@ struct Ctx {
   // X/W share xh/xl and Y/Z share yh/yl, each plane at the same addresses in both layouts
   CUtensorMap tm_Xh, tm_Xl, tm_Yh, tm_Yl, tm_Wh, tm_Wl, tm_Zh, tm_Zl, tm_Bfh, tm_Bfl, tm_Bbh, tm_Bbl;
 
-  // 1D: constant factors of the cyclic tridiagonal solve
-  double* tri = nullptr;     // [4][N]: c', 1/pivot, z (Sherman-Morrison), misc
+  // 1D: constants of the tridiagonal solve and the quadrature weights, one table:
+  //   [0, npad]            rho^k
+  //   npad+1               periodic: 1 / (1 - rho^n);  Dirichlet: kappa (Sherman-Morrison)
+  //   npad+2               rho / mu
+  //   [npad+3, npad+3+n)   Dirichlet: g = M^-1 e_{n-1}  (zeros when periodic)
+  //   then                 quadrature weights [P][P][P]
+  double* tri = nullptr;
+  int npad = 0;              // n rounded up to a multiple of the 1D block size
   unsigned* sched_dev = nullptr;   // step masks of one 1D advance
   size_t sched_cap = 0;
   long* p_dev = nullptr;
@@ -174,6 +180,16 @@ int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int
 // column-tile width of the forward parity-split products for side n (the B box height)
 int gemm_sym_fwd_bn(int n);
 int launch_1d(Ctx* c, long nsteps_pipe, int init_only);
+// 1D launch shape: a cluster of min(order, 8) CTAs of ONED_THREADS threads, levels dealt
+// round-robin; rows padded to a multiple of ONED_THREADS
+constexpr int ONED_THREADS = 256;
+constexpr long kOneDMaxSmemDoubles = 28000;   // 224 KB of the 227 KB a CTA may use
+inline int oned_cluster(int P) { return P < 8 ? P : 8; }
+inline int oned_npad(int n) { return (n + ONED_THREADS - 1) / ONED_THREADS * ONED_THREADS; }
+inline long oned_smem_doubles(int P, int n, int npad) {
+  const long L = (P + oned_cluster(P) - 1) / oned_cluster(P);
+  return L * npad + L * n + npad + 1;
+}
 int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
 
 // epilogue kinds of the FP64 fast-diagonalisation GEMM

@@ -116,3 +116,43 @@ def test_split_runs_schedule_the_same_steps():
                 pairs.append((j, p[j]))
                 p[j] += 1
     assert sorted(pairs) == sorted((j, n) for j in range(4) for n in range(p[j]))
+
+
+def _reads_and_writes(order, p, m):
+    """(slots read, slots written) per ring in one step with mask m from progress p."""
+    P = order
+    cap = [j + 3 if j < P - 1 else 2 for j in range(P)]
+    reads = [set() for _ in range(P)]
+    writes = [set() for _ in range(P)]
+    for j in range(P):
+        if not (m >> j) & 1:
+            continue
+        n = p[j]
+        reads[j].add(n % cap[j])
+        if j > 0:
+            b = max(0, n + 1 - j)
+            for t in set(range(b, b + j + 1)) | {n + 1, n}:
+                reads[j - 1].add(t % cap[j - 1])
+        writes[j].add((n + 1) % cap[j])
+    return reads, writes
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 8, 12])
+@pytest.mark.parametrize("splits", [[40], [1, 1, 1, 37], [3, 7, 30], [2, 5, 5, 28]])
+def test_schedule_writes_never_hit_slots_read_in_the_same_step(order, splits):
+    """Levels of one pipeline step may run concurrently (one CTA per level): a level's new
+    slot must never be a slot that any level reads in that step, also across split advances."""
+    P = order
+    p = [0] * P
+    top = 0
+    for k in splits:
+        top += k
+        masks = R.schedule_plan_from(order, list(p), top)
+        for m in masks:
+            reads, writes = _reads_and_writes(order, p, int(m))
+            for j in range(P):
+                assert not (reads[j] & writes[j]), (order, p, int(m), j)
+            for j in range(P):
+                if (int(m) >> j) & 1:
+                    p[j] += 1
+        assert p[P - 1] == top
