@@ -71,7 +71,7 @@ def test_dirichlet_adv_diff_fp64_small_grids(n):
     assert rel_l2(got, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("order", [1, 2, 6])
+@pytest.mark.parametrize("order", [1, 2, 6, 8, 12])
 def test_gray_scott_fp64_other_orders(order):
     w = inputs.gray_scott_2d(n=32, nsteps=12, width=0.3, seed=5)
     got, _, _ = _run(w, order=order)
