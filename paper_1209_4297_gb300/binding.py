@@ -257,7 +257,8 @@ class Integrator:
                "ridc_solve_planes")
         return out
 
-    def set_profiling(self, enable: bool) -> None:
+    def set_profiling(self, enable) -> None:
+        """False/0 off, True/1 every launch, k > 1 every launch of every k-th 2D step."""
         _check(lib().ridc_set_profiling(self._h, int(enable)), "ridc_set_profiling")
 
     def kernel_stats(self, name: str) -> tuple[int, float]:

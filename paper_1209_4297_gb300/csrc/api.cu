@@ -144,13 +144,13 @@ void prof_begin(Ctx* c, int kind, cudaEvent_t* e0) {
   (void)kind;
   c->launches++;
   *e0 = nullptr;
-  if (!c->profiling) return;
+  if (!c->prof_now) return;
   *e0 = ev_get(c);
   if (*e0) cudaEventRecord(*e0, c->stream);
 }
 
 void prof_end(Ctx* c, int kind, cudaEvent_t e0) {
-  if (!c->profiling || !e0) return;
+  if (!c->prof_now || !e0) return;
   cudaEvent_t e1 = ev_get(c);
   if (!e1) return;
   cudaEventRecord(e1, c->stream);
@@ -485,6 +485,7 @@ extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, i
   Ctx* c = ctx_of(h);
   if (!c || !u0 || count != (size_t)c->plane) return RIDC_ERR_ARG;
   c->seg_base = 0;
+  c->prof_steps = 0;
   return start_from(c, u0, on_device);
 }
 
@@ -574,7 +575,18 @@ static inline double* slot_ptr(Ctx* c, double* ring, int j, long t) {
   return ring + (size_t)(t % c->cap[j]) * c->plane;
 }
 
+static int step_2d_launch(Ctx* c, unsigned mask);
+
 static int step_2d(Ctx* c, unsigned mask) {
+  // with a sampling period k > 1 only every k-th step of an integration is timed
+  c->prof_now = c->profiling == 1 || (c->profiling > 1 && c->prof_steps % c->profiling == 0);
+  c->prof_steps++;
+  const int rc = step_2d_launch(c, mask);
+  c->prof_now = c->profiling > 0;
+  return rc;
+}
+
+static int step_2d_launch(Ctx* c, unsigned mask) {
   RhsArgs ra{};
   FinArgs fa{};
   fa.n = c->n;
@@ -940,7 +952,9 @@ extern "C" int ridc_set_profiling(ridc_handle h, int enable) {
   if (!c) return RIDC_ERR_ARG;
   prof_collect(c);
   for (int k = 0; k < RIDC_KERNEL_COUNT; ++k) { c->k_launch[k] = 0; c->k_ms[k] = 0.0; }
-  c->profiling = enable != 0;
+  if (enable < 0) return RIDC_ERR_ARG;
+  c->profiling = enable;
+  c->prof_now = enable > 0;
   return RIDC_OK;
 }
 

@@ -142,7 +142,9 @@ struct Ctx {
   int* err_dev = nullptr;    // device-side error flag (timeouts)
 
   // instrumentation
-  bool profiling = false;
+  int profiling = 0;         // 0 off; 1 every launch; k > 1 the launches of every k-th 2D step
+  bool prof_now = false;     // record the launches being issued now
+  long prof_steps = 0;       // 2D pipeline steps since ridc_set_initial
   long launches = 0;
   std::vector<cudaEvent_t> ev_pool;
   struct Rec { int kind; cudaEvent_t e0, e1; };

@@ -203,3 +203,21 @@ def test_dirichlet_4096_mixed_full_size_truncated():
     got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4)
     assert rel_l2(got, ref) <= 1e-8
+
+
+def test_profiling_samples_every_kth_step():
+    need_cuda()
+    w = inputs.gray_scott_2d(n=256, nsteps=10, seed=2)
+    with Integrator.from_workload(w, precision="mixed_bf16x3", n_refine=2) as it:
+        it.set_initial(w.u0)
+        it.set_profiling(1)
+        it.advance(4)   # 4 + 6 start-up steps = 10 pipeline steps
+        n_all, ms_all = it.kernel_stats("gemm_tc")
+        it.set_initial(w.u0)
+        it.set_profiling(4)
+        it.advance(4)
+        n_some, _ = it.kernel_stats("gemm_tc")
+        with pytest.raises(RidcError):
+            it.set_profiling(-1)
+    assert n_all == 10 * 12 and ms_all > 0
+    assert n_some == 3 * 12          # steps 0, 4 and 8
