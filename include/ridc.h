@@ -270,8 +270,7 @@ int ridc_quadrature_weights(int order, double* out, size_t cap);
 #define RIDC_KERNEL_RESIDUAL  3   /* FP64 refinement residual + split                      */
 #define RIDC_KERNEL_FINALIZE  4   /* solution accumulation + f^N, f of the new state       */
 #define RIDC_KERNEL_1D        5   /* persistent 1D pipeline kernel                         */
-#define RIDC_KERNEL_YBFLY     6   /* parity split between the first two tensor-core GEMMs  */
-#define RIDC_KERNEL_COUNT     7
+#define RIDC_KERNEL_COUNT     6
 
 /* CUDA-event timing of kernel launches on the handle's stream: enable = 0 off, 1 every
  * launch, k > 1 every launch of every k-th 2D pipeline step (steps 0, k, 2k, ... counted

@@ -20,8 +20,7 @@ KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dir
          "adv_diff_1d_upwind_periodic": 3, "burgers_1d_dirichlet": 4}
 KINDS_1D = ("adv_diff_1d_periodic", "adv_diff_1d_upwind_periodic", "burgers_1d_dirichlet")
 PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1, "fp32_solve": 2}
-KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5,
-           "ybfly": 6}
+KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5}
 
 
 class RidcError(RuntimeError):

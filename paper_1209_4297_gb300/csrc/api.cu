@@ -507,11 +507,10 @@ static int solve_group_mixed(Ctx* c, int p0, int np, bool rhs_split_done, const 
       RIDC_TRY(launch_residual(c, p0, np, tot, c->dinc, dst));
       tot = dst;
     }
-    // x forward (parity-split operand X from the right-hand side or residual kernel) -> FP32 T
+    // x forward of the operand split along both axes (right-hand side or residual kernel)
+    // -> Y, rows kx per y parity;  y forward, divided by the denominators -> W
     RIDC_TRY(launch_gemm_sym(c, &c->tm_Xh, &c->tm_Xl, &c->tm_Bfh, &c->tm_Bfl, p0, np,
-                             SYM_FWD_F32, nullptr, nullptr, c->dinc));
-    // y parity split of T -> Y;  y forward, divided by the denominators -> W
-    RIDC_TRY(launch_ybfly(c, p0, np, c->dinc));
+                             SYM_FWD_SPLIT, c->yh, c->yl, nullptr));
     RIDC_TRY(launch_gemm_sym(c, &c->tm_Yh, &c->tm_Yl, &c->tm_Bfh, &c->tm_Bfl, p0, np,
                              SYM_FWD_DEN, c->xh, c->xl, nullptr));
     // x inverse -> Z;  y inverse -> FP32 increment

@@ -10,9 +10,14 @@
 // so each transform is two (rows x H) x (H x H) products instead of one (rows x N) x (N x N):
 // half the tensor-core work. Spectral indices are kept in split order (even k, then odd k).
 //
+// The y parity split is applied to the right-hand side before the first transform (the
+// transforms are linear): its operand holds, per plane and x parity gx, the rows gy*N/2 + y'
+// of v[gx][gy][y'][x'] = (v[y'][x'] +- v[y'][N-1-x']) +- (v[N-1-y'][x'] +- v[N-1-y'][N-1-x']).
+// The first transform then writes each result row straight into the second's operand.
+//
 // Operands are BF16 hi/lo splits, C ~= Ah Bh + Ah Bl + Al Bh with FP32 accumulation in TMEM.
 // Every product contracts the contiguous axis of its A rows and stores transposed per plane.
-//   SYM_FWD_F32   forward, FP32 store                       (first transform, x)
+//   SYM_FWD_SPLIT forward, BF16 hi/lo store into [plane][gy][kx][y'] (first transform, x)
 //   SYM_FWD_DEN   forward, times 1/den, BF16 hi/lo store     (second transform, y)
 //   SYM_BWD_SPLIT inverse with the E +- O butterfly, BF16    (third transform, x)
 //   SYM_BWD_F32   inverse with the E +- O butterfly, FP32    (fourth transform, y: the increment)
@@ -330,6 +335,9 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
         const int cbase = T.g * a.H + T.c0;   // output column position (split order)
         const float dtnu = a.dtnu[plane % a.S];
         const float den_r = (a.mode == SYM_FWD_DEN) ? 1.0f - dtnu * lam_s[rl] : 0.f;
+        // first transform: row rl = gy N/2 + y' goes to row block gy of the next operand
+        const int gy = rl >= a.H ? 1 : 0, yp = rl - gy * a.H;
+        const size_t sbase = (size_t)(plane * 2 + gy) * n;
         for (int c = 0; c < BN; c += 16) {
           uint32_t v[16];
           s_ld16(acc + (uint32_t)c, v);
@@ -337,14 +345,13 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int m = cbase + c + jj;
-            const size_t idx = (pbase + m) * n + rl;
             float val = __uint_as_float(v[jj]);
-            if (a.mode == SYM_FWD_F32) {
-              a.o32[idx] = val;
+            if (a.mode == SYM_FWD_SPLIT) {
+              s_split(val, a.oh, a.ol, (sbase + m) * a.H + yp);
             } else {
               // the split keeps ~16 bits: a 2-ulp fast division is ample
               val = __fdividef(val, fmaf(-dtnu, lam_s[m], den_r));
-              s_split(val, a.oh, a.ol, idx);
+              s_split(val, a.oh, a.ol, (pbase + m) * n + rl);
             }
           }
         }
@@ -452,7 +459,7 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
   a.lam = c->lam_f;
   for (int s = 0; s < c->S; ++s) a.dtnu[s] = (float)(c->dt * c->nu[s]);
   a.err = c->err_dev;
-  const bool fwd = mode == SYM_FWD_F32 || mode == SYM_FWD_DEN;
+  const bool fwd = mode == SYM_FWD_SPLIT || mode == SYM_FWD_DEN;
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_TC, &e0);
   int rc;

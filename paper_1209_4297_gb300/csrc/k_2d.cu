@@ -4,8 +4,8 @@
 //   finalize_kernel  eta_{n+1} = base + delta, then f^N(eta) and f = f^N + D eta of the new
 //                    state (5-point stencil from a shared-memory tile with ghost cells).
 //   residual_kernel  refinement residual r - (I - dt nu L) delta of the mixed solve, parity-
-//                    split along x and split into BF16 hi/lo for the next tensor-core pass.
-//   ybfly_kernel     parity split along y between the first and second tensor-core products.
+//                    split along both axes and split into BF16 hi/lo for the next
+//                    tensor-core pass.
 //   gemm_f64_kernel  FP64 fast-diagonalisation GEMM (DFMA; GB300's DMMA is slower than DFMA).
 #include "ridc_internal.h"
 
@@ -102,28 +102,42 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
       r2[i] = rhs_at<NODES>(a, L, Fn, w, i);
     return;
   }
-  // mixed form: each thread takes cells (2q, 2q+1) of a row and their mirrors (n-2-2q, n-1-2q)
-  // and also writes the parity split along x, v+- = v[x'] +- v[n-1-x'], of the FP32 values as
-  // BF16 hi/lo (layout [plane][group][y][x'], x' < n/2)
+  // mixed form: each thread takes cells (2q, 2q+1) of rows y and n-1-y (y < n/2) and their
+  // mirrors (n-2-2q, n-1-2q), and also writes the parity split along both axes of the FP32
+  // values, v[gx][gy] = (v[y][x'] +- v[y][n-1-x']) +- (v[n-1-y][x'] +- v[n-1-y][n-1-x']),
+  // as BF16 hi/lo (layout [plane][gx][gy][y'][x'], x', y' < n/2)
   const int n = a.n, q4 = n / 4, H = n / 2;
-  const long nn = (long)n * n, cells = a.plane / 4;
+  const long nn = (long)n * n, cells = a.plane / 8;
   const long plane0 = out_off / nn;   // first plane of this level in the stacked operand
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < cells;
        e += (long)gridDim.x * blockDim.x) {
-    const long sp = e / ((long)n * q4), rem = e - sp * (long)n * q4;
+    const long sp = e / ((long)H * q4), rem = e - sp * (long)H * q4;
     const int y = (int)(rem / q4), q = (int)(rem - (long)y * q4);
-    const long rowoff = sp * nn + (long)y * n;
-    const long iL = (rowoff + 2 * q) >> 1, iR = (rowoff + n - 2 - 2 * q) >> 1;
-    const double2 vL = rhs_at<NODES>(a, L, Fn, w, iL);
-    const double2 vR = rhs_at<NODES>(a, L, Fn, w, iR);
-    r2[iL] = vL;
-    r2[iR] = vR;
-    const float l0 = f64_to_f32(vL.x), l1 = f64_to_f32(vL.y);
-    const float m1 = f64_to_f32(vR.x), m0 = f64_to_f32(vR.y);   // mirrors of 2q+1 and 2q
-    const long prow = (plane0 + sp) * 2 * n + y;   // group 0 row; group 1 is n rows further
-    const long ip = prow * H + 2 * q, im = (prow + n) * H + 2 * q;
-    store_split2(a.r_hi, a.r_lo, ip, l0 + m0, l1 + m1);
-    store_split2(a.r_hi, a.r_lo, im, l0 - m0, l1 - m1);
+    float v[2][4];   // [row: y, n-1-y][x: 2q, 2q+1, n-1-2q, n-2-2q]
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const long rowoff = sp * nn + (long)(side ? n - 1 - y : y) * n;
+      const long iL = (rowoff + 2 * q) >> 1, iR = (rowoff + n - 2 - 2 * q) >> 1;
+      const double2 vL = rhs_at<NODES>(a, L, Fn, w, iL);
+      const double2 vR = rhs_at<NODES>(a, L, Fn, w, iR);
+      r2[iL] = vL;
+      r2[iR] = vR;
+      v[side][0] = f64_to_f32(vL.x);
+      v[side][1] = f64_to_f32(vL.y);
+      v[side][2] = f64_to_f32(vR.y);   // mirror of 2q
+      v[side][3] = f64_to_f32(vR.x);   // mirror of 2q+1
+    }
+    const long p = plane0 + sp;
+#pragma unroll
+    for (int gx = 0; gx < 2; ++gx) {
+      // x butterfly of each row, then y butterfly
+      const float s = gx ? -1.f : 1.f;
+      const float a0 = v[0][0] + s * v[0][2], a1 = v[0][1] + s * v[0][3];
+      const float b0 = v[1][0] + s * v[1][2], b1 = v[1][1] + s * v[1][3];
+      const long base = ((p * 2 + gx) * n + y) * H + 2 * q;   // gy = 0 block; gy = 1 is H rows on
+      store_split2(a.r_hi, a.r_lo, base, a0 + b0, a1 + b1);
+      store_split2(a.r_hi, a.r_lo, base + (long)H * H, a0 - b0, a1 - b1);
+    }
   }
 }
 
@@ -147,7 +161,7 @@ __global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArg
 }
 
 int launch_rhs(Ctx* c, const RhsArgs& a) {
-  const long half = a.r_hi ? a.plane / 4 : a.plane / 2;
+  const long half = a.r_hi ? a.plane / 8 : a.plane / 2;
   long bx = (half + 255) / 256;
   const long cap = 148L * 16 / (a.nlev > 0 ? a.nlev : 1) + 1;
   if (bx > cap * 8) bx = cap * 8;
@@ -262,29 +276,32 @@ struct ResArgs {
   const double* dprev;
   const float* inc;
   double* dout;
-  __nv_bfloat16* hi;        // parity-split operand [plane][group][y][x'], x' < n/2
+  __nv_bfloat16* hi;        // parity-split operand [plane][gx][gy][y'][x'], x', y' < n/2
   __nv_bfloat16* lo;
   int n, S, plane0;
   double c[kMaxSpecies];    // c_s
   double c1[kMaxSpecies];   // -(1 + 4 c_s)
 };
 
-// One block covers a 32 x 32 tile at x0 < n/2 and its mirror tile at n-32-x0: it forms r' on
-// both, then the parity split r'[x'] +- r'[n-1-x'] (FP32) as BF16 hi/lo.
+// One block covers a 32 x 32 tile at (x0, y0), x0, y0 < n/2, and its three mirror tiles
+// (n-32-x0 and/or n-32-y0): it forms r' on all four, then the parity split along both axes,
+// (r'[y'][x'] +- r'[y'][n-1-x']) +- (r'[n-1-y'][x'] +- r'[n-1-y'][n-1-x']) (FP32), as BF16
+// hi/lo in the layout [plane][gx][gy][y'][x'].
 template <bool ODD>
 __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant__ ResArgs a) {
   __shared__ double tile[TY + 2][TX + 2];
-  __shared__ float rv[2][TY][TX + 1];
+  __shared__ float rv[4][TY][TX + 1];   // [sy * 2 + sx]
   const int n = a.n;
   const long nn = (long)n * n;
   const int p = a.plane0 + blockIdx.z;
   const long off = (long)p * nn;
-  const int y0 = blockIdx.y * TY;
   const bool has_d = a.dprev || a.inc;
   const int sp = p % a.S;
   const double cs = a.c[sp], c1 = a.c1[sp];
-  for (int side = 0; side < 2; ++side) {
-    const int x0 = side == 0 ? blockIdx.x * TX : n - TX - blockIdx.x * TX;
+  for (int side = 0; side < 4; ++side) {
+    const int sx = side & 1, sy = side >> 1;
+    const int x0 = sx == 0 ? blockIdx.x * TX : n - TX - blockIdx.x * TX;
+    const int y0 = sy == 0 ? blockIdx.y * TY : n - TY - blockIdx.y * TY;
     if (has_d) {
       __syncthreads();
       load_tile<ODD>(tile, nullptr, a.dprev ? a.dprev + off : nullptr,
@@ -295,7 +312,6 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
       const int ty = threadIdx.y + rr * BY + 1, gy = y0 + ty - 1;
-      if (gy >= n) break;
       const long o = off + (long)gy * n + gx;
       double v = a.r[o];
       if (has_d) {
@@ -310,21 +326,27 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
   }
   __syncthreads();
   const int H = n / 2;
-  const int xp = blockIdx.x * TX + threadIdx.x;   // x' < n/2; its mirror is column 31 - tx of side 1
+  const int xp = blockIdx.x * TX + threadIdx.x;   // x' < n/2; its mirror is column 31 - tx
 #pragma unroll
   for (int rr = 0; rr < RPT; ++rr) {
-    const int ly = threadIdx.y + rr * BY, gy = y0 + ly;
-    if (gy >= n) break;
-    const float u = rv[0][ly][threadIdx.x], m = rv[1][ly][TX - 1 - threadIdx.x];
-    const long prow = (long)p * 2 * n + gy;
-    const long ip = prow * H + xp, im = (prow + n) * H + xp;
-    const float vp = u + m, vm = u - m;
-    __nv_bfloat16 h = __float2bfloat16_rn(vp);
-    a.hi[ip] = h;
-    a.lo[ip] = __float2bfloat16_rn(vp - __bfloat162float(h));
-    h = __float2bfloat16_rn(vm);
-    a.hi[im] = h;
-    a.lo[im] = __float2bfloat16_rn(vm - __bfloat162float(h));
+    const int ly = threadIdx.y + rr * BY, yp = blockIdx.y * TY + ly;   // y' < n/2
+    const int mx = TX - 1 - threadIdx.x, my = TY - 1 - ly;
+    const float v00 = rv[0][ly][threadIdx.x], v01 = rv[1][ly][mx];
+    const float v10 = rv[2][my][threadIdx.x], v11 = rv[3][my][mx];
+#pragma unroll
+    for (int gxp = 0; gxp < 2; ++gxp) {
+      const float s = gxp ? -1.f : 1.f;
+      const float top = v00 + s * v01, bot = v10 + s * v11;
+      const long i0 = ((long)(p * 2 + gxp) * n + yp) * H + xp;   // gy = 0; gy = 1 is H rows on
+      const long i1 = i0 + (long)H * H;
+      const float vp = top + bot, vm = top - bot;
+      __nv_bfloat16 h = __float2bfloat16_rn(vp);
+      a.hi[i0] = h;
+      a.lo[i0] = __float2bfloat16_rn(vp - __bfloat162float(h));
+      h = __float2bfloat16_rn(vm);
+      a.hi[i1] = h;
+      a.lo[i1] = __float2bfloat16_rn(vm - __bfloat162float(h));
+    }
   }
 }
 
@@ -344,8 +366,8 @@ int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const 
     a.c[s] = c->dt * c->nu[s] / (c->h * c->h);
     a.c1[s] = -(1.0 + 4.0 * a.c[s]);
   }
-  if (c->n % (2 * TX) != 0) return RIDC_ERR_UNSUPPORTED;
-  dim3 grid(c->n / (2 * TX), (c->n + TY - 1) / TY, nplanes);
+  if (c->n % (2 * TX) != 0 || c->n % (2 * TY) != 0) return RIDC_ERR_UNSUPPORTED;
+  dim3 grid(c->n / (2 * TX), c->n / (2 * TY), nplanes);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_RESIDUAL, &e0);
   if (c->kind == RIDC_ADV_DIFF_2D_DIRICHLET)
@@ -353,42 +375,6 @@ int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const 
   else
     residual_kernel<false><<<grid, dim3(TX, BY), 0, c->stream>>>(a);
   prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
-  return cuda_status(cudaGetLastError());
-}
-
-// Parity split along y of the first transform's output T[plane][k][y] (FP32):
-// Y[plane][group][k][y'] = T[..][y'] +- T[..][n-1-y'], y' < n/2, as BF16 hi/lo.
-__global__ void __launch_bounds__(256) ybfly_kernel(const float* __restrict__ in,
-                                                    __nv_bfloat16* __restrict__ hi,
-                                                    __nv_bfloat16* __restrict__ lo, int n,
-                                                    long rows) {
-  const int q4 = n / 4, H = n / 2;
-  const long total = rows * q4;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const long row = e / q4;
-    const int q = (int)(e - row * q4);
-    const float2 L = *reinterpret_cast<const float2*>(in + row * n + 2 * q);
-    const float2 R = *reinterpret_cast<const float2*>(in + row * n + n - 2 - 2 * q);
-    const long pl = row / n, k = row - pl * n;
-    const long prow = pl * 2 * n + k;
-    const long ip = prow * H + 2 * q, im = (prow + n) * H + 2 * q;
-    store_split2(hi, lo, ip, L.x + R.y, L.y + R.x);
-    store_split2(hi, lo, im, L.x - R.y, L.y - R.x);
-  }
-}
-
-int launch_ybfly(Ctx* c, int plane0, int nplanes, const float* in) {
-  const long rows = (long)nplanes * c->n;
-  long blocks = (rows * (c->n / 4) + 255) / 256;
-  if (blocks > 152L * 16) blocks = 152L * 16;
-  const long r0 = (long)plane0 * c->n;
-  cudaEvent_t e0;
-  prof_begin(c, RIDC_KERNEL_YBFLY, &e0);
-  // plane p's split operand starts at element p * n * n, like its unsplit form
-  ybfly_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(in + r0 * c->n, c->yh + r0 * c->n,
-                                                     c->yl + r0 * c->n, c->n, rows);
-  prof_end(c, RIDC_KERNEL_YBFLY, e0);
   return cuda_status(cudaGetLastError());
 }
 

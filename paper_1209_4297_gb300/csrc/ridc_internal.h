@@ -37,8 +37,8 @@ struct RhsArgs {
   long plane;             // S * N * N values per level
   double dt;
   double* r;              // [nlev*S][N][N]
-  __nv_bfloat16* r_hi;    // x-butterflied split of r for the tensor-core solve (nullptr: FP64)
-  __nv_bfloat16* r_lo;    //   layout [plane][parity group][N rows][N/2]
+  __nv_bfloat16* r_hi;    // split of r along both axes for the tensor-core solve (nullptr:
+  __nv_bfloat16* r_lo;    //   FP64), layout [plane][gx][gy][N/2][N/2]
   int n;
 };
 
@@ -120,8 +120,9 @@ struct Ctx {
   //   Bf = [Qe^T; Qo^T] (forward products), Bb = [Qe; Qo] (inverse products)
   __nv_bfloat16 *Bfh = nullptr, *Bfl = nullptr, *Bbh = nullptr, *Bbl = nullptr;
   long grows = 0;            // P*S*N: rows of an inverse operand (half those of a forward one)
-  // A operands: X, Y = [plane][parity group][N][N/2] (forward), W, Z = [plane][N][N] (inverse);
-  // X/W share xh/xl and Y/Z share yh/yl, each plane at the same addresses in both layouts
+  // A operands: X = [plane][gx][gy][N/2][N/2] (right-hand side split along both axes),
+  // Y = [plane][gy][N][N/2] (first transform, rows kx), W, Z = [plane][N][N] (inverse);
+  // X/W share xh/xl and Y/Z share yh/yl, each plane at the same addresses in every layout
   CUtensorMap tm_Xh, tm_Xl, tm_Yh, tm_Yl, tm_Wh, tm_Wl, tm_Zh, tm_Zl, tm_Bfh, tm_Bfl, tm_Bbh, tm_Bbl;
 
   // 1D: constants of the tridiagonal solve and the quadrature weights, one table:
@@ -176,8 +177,6 @@ int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int n
 int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                     const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
                     __nv_bfloat16* ol, float* o32);
-// y-butterfly of the first transform's FP32 output into the second's split operand
-int launch_ybfly(Ctx* c, int plane0, int nplanes, const float* in);
 int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
 // column-tile width of the forward parity-split products for side n (the B box height)
 int gemm_sym_fwd_bn(int n);
@@ -197,6 +196,6 @@ int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
 // epilogue kinds of the FP64 fast-diagonalisation GEMM
 enum { EPI_STORE = 0, EPI_SCALE_DEN = 1, EPI_DELTA = 2 };
 // modes of the parity-split tensor-core GEMM
-enum { SYM_FWD_F32 = 0, SYM_FWD_DEN = 1, SYM_BWD_SPLIT = 2, SYM_BWD_F32 = 3 };
+enum { SYM_FWD_SPLIT = 0, SYM_FWD_DEN = 1, SYM_BWD_SPLIT = 2, SYM_BWD_F32 = 3 };
 
 }  // namespace ridc
