@@ -130,8 +130,8 @@ class ClockSampler:
 # DRAM traffic of one full (8-plane) gemm_sym launch from one ncu capture
 # (profiles/gemm_sym_gray_scott_2048_mixed.md: dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the four modes), valid only for the kernel source it was taken on.
-GEMM_TRAFFIC = {"bytes": 2.326e8,
-                "source_sha256": "a2609d96631d2e43fc5601e3f793b649b5167d482c658e7384c080bd5e97a425"}
+GEMM_TRAFFIC = {"bytes": 2.321e8,
+                "source_sha256": "3d9f9b93ba55ce53f322f4ab84e65454494006107a515387a77d2ed81a434e92"}
 
 
 def gemm_traffic():

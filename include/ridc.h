@@ -273,9 +273,9 @@ int ridc_quadrature_weights(int order, double* out, size_t cap);
 #define RIDC_KERNEL_COUNT     6
 
 /* CUDA-event timing of kernel launches on the handle's stream: enable = 0 off, 1 every
- * launch, k > 1 every launch of every k-th 2D pipeline step (steps 0, k, 2k, ... counted
- * from ridc_set_initial; other launches are always timed), which keeps the events' own
- * cost small. Any call clears the counters; enable < 0 is RIDC_ERR_ARG.                    */
+ * launch, k > 1 only the launches of every k-th 2D pipeline step (steps 0, k, 2k, ...
+ * counted from ridc_set_initial), which keeps the events' own cost small. Any call clears
+ * the counters; enable < 0 is RIDC_ERR_ARG.                                                 */
 int ridc_set_profiling(ridc_handle h, int enable);
 
 /* Launch count and summed device time (ms) of one kernel kind since profiling was enabled.

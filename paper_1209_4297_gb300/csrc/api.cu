@@ -581,7 +581,7 @@ static int step_2d(Ctx* c, unsigned mask) {
   c->prof_now = c->profiling == 1 || (c->profiling > 1 && c->prof_steps % c->profiling == 0);
   c->prof_steps++;
   const int rc = step_2d_launch(c, mask);
-  c->prof_now = c->profiling > 0;
+  c->prof_now = c->profiling == 1;
   return rc;
 }
 
@@ -953,7 +953,7 @@ extern "C" int ridc_set_profiling(ridc_handle h, int enable) {
   for (int k = 0; k < RIDC_KERNEL_COUNT; ++k) { c->k_launch[k] = 0; c->k_ms[k] = 0.0; }
   if (enable < 0) return RIDC_ERR_ARG;
   c->profiling = enable;
-  c->prof_now = enable > 0;
+  c->prof_now = enable == 1;
   return RIDC_OK;
 }
 
