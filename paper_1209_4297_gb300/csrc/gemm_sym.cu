@@ -341,20 +341,9 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
         for (int c = 0; c < BN; c += 16) {
           uint32_t v[16];
           s_ld16(acc + (uint32_t)c, v);
-          // eigenvalues of the 16 columns: four 16-byte broadcast loads (shared-memory
-          // bandwidth is what the tensor cores of this kernel run short of)
-          float lm[16];
-          if (a.mode == SYM_FWD_DEN) {
-            const float4* l4 = reinterpret_cast<const float4*>(lam_s + cbase + c);
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-              const float4 t = l4[q4];
-              lm[4 * q4] = t.x;
-              lm[4 * q4 + 1] = t.y;
-              lm[4 * q4 + 2] = t.z;
-              lm[4 * q4 + 3] = t.w;
-            }
-          }
+          // eigenvalues of the 16 columns: one shared-memory wavefront (a lane per column),
+          // then shuffles; shared-memory bandwidth is what the tensor cores run short of
+          const float lam_lane = (a.mode == SYM_FWD_DEN) ? lam_s[cbase + c + (lane & 15)] : 0.f;
           s_ld_wait();
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
@@ -364,7 +353,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
               s_split(val, a.oh, a.ol, (sbase + m) * a.H + yp);
             } else {
               // the split keeps ~16 bits: a 2-ulp fast division is ample
-              val = __fdividef(val, fmaf(-dtnu, lm[jj], den_r));
+              val = __fdividef(val, fmaf(-dtnu, __shfl_sync(0xffffffffu, lam_lane, jj), den_r));
               s_split(val, a.oh, a.ol, (pbase + m) * n + rl);
             }
           }
