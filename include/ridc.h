@@ -285,6 +285,21 @@ int ridc_get_kernel_stats(ridc_handle h, int kernel, long* launches, double* tot
 /* Kernel launches issued so far by the handle (all kinds, counted on the host).            */
 long ridc_launch_count(ridc_handle h);
 
+/* ---- test hooks: failures made on purpose, for the error paths ---------------------------- */
+
+/* Make the k-th device allocation from now on (k >= 1) fail as if the device were out of
+ * memory; 0 disarms. Process-wide. Every entry point that allocates then returns
+ * RIDC_ERR_OOM and releases what it had allocated. RIDC_ERR_ARG for k < 0.                */
+int ridc_debug_fail_alloc(int k);
+
+/* Make the next tensor-core GEMM launch of the handle leave one operand stage unloaded, so
+ * that the barrier its consumer waits on never completes. Every device-side wait is bounded
+ * (2 s of %globaltimer): the launch gives up, flags the handle's error and frees its tensor
+ * memory, and the next call that synchronises (ridc_solve_planes, ridc_get_solution, ...)
+ * returns RIDC_ERR_TIMEOUT and clears the flag. The context stays usable. Mixed-precision
+ * 2D handles only (RIDC_ERR_UNSUPPORTED otherwise).                                         */
+int ridc_debug_stall_next_gemm(ridc_handle h);
+
 #ifdef __cplusplus
 }
 #endif

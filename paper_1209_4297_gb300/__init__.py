@@ -4,8 +4,10 @@ The integrator runs entirely in the CUDA kernels of libridc.so (built in-tree fo
 `python -m paper_1209_4297_gb300.build`); this package only marshals arguments. Importing it
 does not load the library; the first call does, and raises if the library is missing.
 """
-from .binding import (Batch, Integrator, RidcError, error_string, lib, quadrature_weights,
+from .binding import (Batch, Integrator, RidcError, debug_fail_alloc, error_string, lib,
+                      quadrature_weights,
                       schedule_plan, schedule_plan_from, LIB_PATH, KERNELS)
 
-__all__ = ["Batch", "Integrator", "RidcError", "error_string", "lib", "quadrature_weights",
+__all__ = ["Batch", "Integrator", "RidcError", "debug_fail_alloc", "error_string", "lib",
+           "quadrature_weights",
            "schedule_plan", "schedule_plan_from", "LIB_PATH", "KERNELS"]

@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
         "ridc_error_string": (ctypes.c_char_p, [i]),
         "ridc_solve_planes": (i, [vp, vp, vp, i, i]),
         "ridc_save_state": (i, [vp, vp, POINTER(sz)]),
+        "ridc_debug_fail_alloc": (i, [i]),
+        "ridc_debug_stall_next_gemm": (i, [vp]),
         "ridc_load_state": (i, [vp, vp, sz]),
         "ridc_schedule_plan": (i, [i, lg, POINTER(c_uint), sz, POINTER(sz)]),
         "ridc_schedule_plan_from": (i, [i, POINTER(lg), lg, POINTER(c_uint), sz, POINTER(sz)]),
@@ -139,6 +141,11 @@ def schedule_plan_from(order: int, start, nsteps: int) -> np.ndarray:
     _check(L.ridc_schedule_plan_from(order, st, nsteps, out, cnt.value, byref(cnt)),
            "ridc_schedule_plan_from")
     return np.array(out[:cnt.value], dtype=np.uint32)
+
+
+def debug_fail_alloc(k: int) -> None:
+    """Test hook: the k-th device allocation from now on fails (0 disarms)."""
+    _check(lib().ridc_debug_fail_alloc(k), "ridc_debug_fail_alloc")
 
 
 def quadrature_weights(order: int) -> np.ndarray:
@@ -227,6 +234,10 @@ class Integrator:
         t = c_double(0)
         _check(lib().ridc_get_time(self._h, byref(t)), "ridc_get_time")
         return t.value
+
+    def debug_stall_next_gemm(self) -> None:
+        """Test hook: the next tensor-core GEMM's bounded waits run out (RIDC_ERR_TIMEOUT)."""
+        _check(lib().ridc_debug_stall_next_gemm(self._h), "ridc_debug_stall_next_gemm")
 
     def save_state(self) -> np.ndarray:
         """The whole integrator state (ridc_save_state) as a host byte array."""

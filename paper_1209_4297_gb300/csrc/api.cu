@@ -6,6 +6,7 @@
 //   Section III-B eq. (pred), III-C eq. (corr): predictor / corrector; quadrature weights.
 //   Section III-E: staggered start-up (level j waits j(j+1)/2 steps), idle tail.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -33,6 +34,23 @@ extern "C" const char* ridc_error_string(int code) {
 }
 
 namespace ridc {
+
+// ---- host-side fault injection (tests): the k-th device allocation from now on fails -------
+static std::atomic<long> g_fail_alloc{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+extern "C" int ridc_debug_fail_alloc(int k) {
+  if (k < 0) return RIDC_ERR_ARG;
+  g_fail_alloc.store(k);
+  return RIDC_OK;
+}
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return RIDC_OK;
@@ -208,7 +226,7 @@ static void split_bf16(const std::vector<double>& src, std::vector<__nv_bfloat16
 
 template <class T>
 static int upload(Ctx* c, T** dst, const std::vector<T>& src) {
-  RIDC_CUDA(cudaMalloc((void**)dst, src.size() * sizeof(T)));
+  RIDC_CUDA(dev_malloc((void**)dst, src.size() * sizeof(T)));
   return cuda_status(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
 }
 
@@ -326,29 +344,29 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
   const size_t pb = (size_t)c->plane * sizeof(double);
   for (int j = 0; j < order; ++j) {
     c->cap[j] = ring_cap(order, j);
-    RIDC_CUDA(cudaMalloc((void**)&c->eta[j], c->cap[j] * pb));
-    RIDC_CUDA(cudaMalloc((void**)&c->fN[j], c->cap[j] * pb));
-    if (j < order - 1 || j == 0) RIDC_CUDA(cudaMalloc((void**)&c->Fq[j], c->cap[j] * pb));
+    RIDC_CUDA(dev_malloc((void**)&c->eta[j], c->cap[j] * pb));
+    RIDC_CUDA(dev_malloc((void**)&c->fN[j], c->cap[j] * pb));
+    if (j < order - 1 || j == 0) RIDC_CUDA(dev_malloc((void**)&c->Fq[j], c->cap[j] * pb));
   }
-  RIDC_CUDA(cudaMalloc((void**)&c->r, (size_t)order * pb));
-  RIDC_CUDA(cudaMalloc((void**)&c->delta, (size_t)order * pb));
-  RIDC_CUDA(cudaMalloc((void**)&c->err_dev, sizeof(int)));
+  RIDC_CUDA(dev_malloc((void**)&c->r, (size_t)order * pb));
+  RIDC_CUDA(dev_malloc((void**)&c->delta, (size_t)order * pb));
+  RIDC_CUDA(dev_malloc((void**)&c->err_dev, sizeof(int)));
   RIDC_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
   if (c->dim == 1) {
     RIDC_TRY(build_tables_1d(c));
-    RIDC_CUDA(cudaMalloc((void**)&c->p_dev, kMaxOrder * sizeof(long)));
+    RIDC_CUDA(dev_malloc((void**)&c->p_dev, kMaxOrder * sizeof(long)));
   } else {
     if (c->prec == RIDC_FP64) {
-      RIDC_CUDA(cudaMalloc((void**)&c->t1, (size_t)order * pb));
-      RIDC_CUDA(cudaMalloc((void**)&c->t2, (size_t)order * pb));
+      RIDC_CUDA(dev_malloc((void**)&c->t1, (size_t)order * pb));
+      RIDC_CUDA(dev_malloc((void**)&c->t2, (size_t)order * pb));
     } else {
-      RIDC_CUDA(cudaMalloc((void**)&c->delta2, (size_t)order * pb));
-      RIDC_CUDA(cudaMalloc((void**)&c->dinc, (size_t)order * c->plane * sizeof(float)));
+      RIDC_CUDA(dev_malloc((void**)&c->delta2, (size_t)order * pb));
+      RIDC_CUDA(dev_malloc((void**)&c->dinc, (size_t)order * c->plane * sizeof(float)));
       const size_t hb = (size_t)order * c->plane * sizeof(__nv_bfloat16);
-      RIDC_CUDA(cudaMalloc((void**)&c->xh, hb));
-      RIDC_CUDA(cudaMalloc((void**)&c->xl, hb));
-      RIDC_CUDA(cudaMalloc((void**)&c->yh, hb));
-      RIDC_CUDA(cudaMalloc((void**)&c->yl, hb));
+      RIDC_CUDA(dev_malloc((void**)&c->xh, hb));
+      RIDC_CUDA(dev_malloc((void**)&c->xl, hb));
+      RIDC_CUDA(dev_malloc((void**)&c->yh, hb));
+      RIDC_CUDA(dev_malloc((void**)&c->yl, hb));
     }
     RIDC_TRY(build_tables_2d(c));
     if (c->prec == RIDC_MIXED_BF16X3) {
@@ -455,6 +473,18 @@ static int start_from(Ctx* c, const double* u0, int on_device) {
     RIDC_TRY(ensure_pinned(c, (size_t)c->plane));
     memcpy(c->pinned, u0, bytes);
     RIDC_CUDA(cudaMemcpyAsync(c->eta[0], c->pinned, bytes, cudaMemcpyHostToDevice, c->stream));
+  }
+  // every other ring slot is filled with NaN (all bits set): a read of a slot the schedule
+  // has not written yet would show up as NaN in the results instead of passing unnoticed
+  const size_t slot_bytes = (size_t)c->plane * sizeof(double);
+  for (int j = 0; j < c->P; ++j) {
+    double* rings[3] = {c->eta[j], c->fN[j], c->Fq[j]};
+    for (double* ring : rings) {
+      if (!ring) continue;
+      const size_t skip = (ring == c->eta[0]) ? 1 : 0;   // keeps the new initial state
+      RIDC_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(ring) + skip * slot_bytes, 0xFF,
+                                (c->cap[j] - skip) * slot_bytes, c->stream));
+    }
   }
   // f^N and F of the initial state, written into slot 0 of level 0
   if (c->dim == 2) {
@@ -564,7 +594,11 @@ extern "C" int ridc_solve_planes(ridc_handle h, const double* r, double* delta, 
   RIDC_CUDA(cudaStreamSynchronize(c->stream));
   int err = 0;
   RIDC_CUDA(cudaMemcpy(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
-  return err ? RIDC_ERR_TIMEOUT : RIDC_OK;
+  if (err) {   // reported once: the flag is cleared for the calls that follow
+    RIDC_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+    return RIDC_ERR_TIMEOUT;
+  }
+  return RIDC_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -669,7 +703,7 @@ static int advance_run(Ctx* c, long nsteps) {
       if (c->sched_dev) cudaFree(c->sched_dev);
       c->sched_dev = nullptr;
       c->sched_cap = 0;
-      RIDC_CUDA(cudaMalloc((void**)&c->sched_dev, masks.size() * sizeof(unsigned)));
+      RIDC_CUDA(dev_malloc((void**)&c->sched_dev, masks.size() * sizeof(unsigned)));
       c->sched_cap = masks.size();
     }
     RIDC_CUDA(cudaMemcpyAsync(c->sched_dev, masks.data(), masks.size() * sizeof(unsigned),
@@ -946,6 +980,14 @@ extern "C" int ridc_quadrature_weights(int order, double* out, size_t cap) {
 // ------------------------------------------------------------------------------------------
 // instrumentation
 // ------------------------------------------------------------------------------------------
+extern "C" int ridc_debug_stall_next_gemm(ridc_handle h) {
+  Ctx* c = ctx_of(h);
+  if (!c) return RIDC_ERR_ARG;
+  if (c->dim != 2 || c->prec != RIDC_MIXED_BF16X3) return RIDC_ERR_UNSUPPORTED;
+  c->stall_next_gemm = 1;
+  return RIDC_OK;
+}
+
 extern "C" int ridc_set_profiling(ridc_handle h, int enable) {
   Ctx* c = ctx_of(h);
   if (!c) return RIDC_ERR_ARG;

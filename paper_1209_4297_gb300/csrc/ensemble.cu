@@ -417,7 +417,7 @@ struct BatchCtx {
 };
 
 static int b_alloc(BatchCtx* b, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = dev_malloc(p, bytes);
   if (e != cudaSuccess) return cuda_status(e);
   b->allocs.push_back(*p);
   return RIDC_OK;
@@ -486,7 +486,7 @@ static int batch_run(BatchCtx* b, long nsteps, int cl, int per_sm, const int* or
       if (b->masks_dev[I.P]) cudaFree(b->masks_dev[I.P]);
       b->masks_dev[I.P] = nullptr;
       b->masks_cap[I.P] = 0;
-      cudaError_t e = cudaMalloc((void**)&b->masks_dev[I.P], (masks.size() + 1) * sizeof(unsigned));
+      cudaError_t e = dev_malloc((void**)&b->masks_dev[I.P], (masks.size() + 1) * sizeof(unsigned));
       if (e != cudaSuccess) return cuda_status(e);
       b->masks_cap[I.P] = masks.size();
     }

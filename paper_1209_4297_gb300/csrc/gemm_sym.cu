@@ -169,6 +169,7 @@ struct SymArgs {
   const float* lam;   // eigenvalues in split order
   float dtnu[kMaxSpecies];
   int* err;
+  int stall;            // test hook: CTA 0 leaves its first stage unloaded
 };
 
 // tile -> (A row base, B row base, output plane-row base, column base, group)
@@ -270,6 +271,8 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
             break;
           }
           uint8_t* st = smem + s * SY_STAGE;
+          // test hook: the stage is never loaded, so its consumer's bounded wait runs out
+          if (a.stall && blockIdx.x == 0 && issued == 0) continue;
           s_expect(full(s), SY_STAGE);
           s_tma(s_u32(st), &tAh, full(s), (fwd ? 0 : koff) + kb * SY_BK, T.arow);
           s_tma(s_u32(st + SY_TILE), &tAl, full(s), (fwd ? 0 : koff) + kb * SY_BK, T.arow);
@@ -462,6 +465,8 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
   a.lam = c->lam_f;
   for (int s = 0; s < c->S; ++s) a.dtnu[s] = (float)(c->dt * c->nu[s]);
   a.err = c->err_dev;
+  a.stall = c->stall_next_gemm;
+  c->stall_next_gemm = 0;
   const bool fwd = mode == SYM_FWD_SPLIT || mode == SYM_FWD_DEN;
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_TC, &e0);

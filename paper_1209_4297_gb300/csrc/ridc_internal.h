@@ -141,6 +141,7 @@ struct Ctx {
   double* pinned = nullptr;
   size_t pinned_count = 0;
   int* err_dev = nullptr;    // device-side error flag (timeouts)
+  int stall_next_gemm = 0;   // test hook: the next tensor-core GEMM leaves one stage unloaded
 
   // instrumentation
   int profiling = 0;         // 0 off; 1 every launch; k > 1 the launches of every k-th 2D step
@@ -157,6 +158,8 @@ struct Ctx {
 
 // ---- host helpers -------------------------------------------------------------------------------
 int cuda_status(cudaError_t e);
+// cudaMalloc behind the allocation-failure hook of ridc_debug_fail_alloc
+cudaError_t dev_malloc(void** p, size_t bytes);
 void prof_begin(Ctx* c, int kind, cudaEvent_t* e0);
 void prof_end(Ctx* c, int kind, cudaEvent_t e0);
 

@@ -156,3 +156,10 @@ def test_schedule_writes_never_hit_slots_read_in_the_same_step(order, splits):
                 if (int(m) >> j) & 1:
                     p[j] += 1
         assert p[P - 1] == top
+
+
+def test_fault_hooks_reject_bad_arguments():
+    L = R.lib()
+    assert L.ridc_debug_fail_alloc(-1) == -1
+    assert L.ridc_debug_fail_alloc(0) == 0
+    assert L.ridc_debug_stall_next_gemm(None) == -1
