@@ -233,9 +233,15 @@ long ridc_batch_cells(ridc_batch b);
  * instance) and the CTAs per SM (1 or 2) that run the whole batch fastest; each trial
  * advances `nsteps` steps of the real batch. The choice is kept for later advances. Requires
  * an initial state and leaves the state undefined: call ridc_batch_set_initial afterwards.
- * *choice = CTAs per SM * 256 + cluster size * 16 + bit c set when side class c (ascending
- * sides) uses 128 x 128 tiles; *best_ms = the fastest whole-batch trial.                    */
+ * *choice = CTAs per SM * 16 + cluster size (the launch shape; the tile per side stays in
+ * the batch); *best_ms = the fastest whole-batch trial.                                    */
 int ridc_batch_autotune(ridc_batch b, long nsteps, int* choice, float* best_ms);
+
+/* Use launch shape `choice` (CTAs per SM * 16 + cluster size, as ridc_batch_autotune reports
+ * it: 1 or 2 CTAs per SM, clusters of 1, 2 or 4 CTAs) for later advances, e.g. one tuned
+ * earlier on the same batch. Tiles keep the autotuner's choice, or before any autotuning
+ * 128 x 128 for sides >= 128. RIDC_ERR_ARG for another value.                              */
+int ridc_batch_set_launch(ridc_batch b, int choice);
 
 /* Release everything the batch holds (synchronises its stream). NULL is ok.                */
 void ridc_batch_destroy(ridc_batch b);

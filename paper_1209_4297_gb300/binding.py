@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         "ridc_batch_get_solution": (i, [vp, i, vp, sz, i]),
         "ridc_batch_cells": (lg, [vp]),
         "ridc_batch_autotune": (i, [vp, lg, POINTER(c_int), POINTER(ctypes.c_float)]),
+        "ridc_batch_set_launch": (i, [vp, i]),
         "ridc_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -344,6 +345,10 @@ class Batch:
 
     def cells(self) -> int:
         return lib().ridc_batch_cells(self._h)
+
+    def set_launch(self, choice: int) -> None:
+        """Launch shape CTAs per SM * 16 + cluster size, as autotune() reports it."""
+        _check(lib().ridc_batch_set_launch(self._h, choice), "ridc_batch_set_launch")
 
     def autotune(self, nsteps: int = 4) -> tuple[int, float]:
         choice = c_int(0)

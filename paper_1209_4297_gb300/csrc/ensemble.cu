@@ -767,8 +767,7 @@ extern "C" long ridc_batch_cells(ridc_batch h) {
 // instances of that side fastest on their own (one-CTA clusters); then the cluster size (1, 2
 // or 4 CTAs per instance) and the CTAs per SM (1 or 2) that run the whole batch fastest with
 // those tiles. Each trial advances `nsteps` top-level steps from the current state. The
-// choice is kept for later advances; *choice = CTAs per SM * 256 + cluster size * 16 + (bit
-// c set: side class c uses 128 x 128 tiles).
+// choice is kept for later advances; *choice = CTAs per SM * 16 + cluster size.
 // The state is scrambled: call ridc_batch_set_initial afterwards.
 extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float* best_ms) {
   BatchCtx* b = bctx(h);
@@ -836,7 +835,18 @@ extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float
   b->cl = bcl;
   b->per_sm = bps;
   b->initialised = false;
-  if (choice) *choice = bps * 256 + bcl * 16 + mask;
+  (void)mask;
+  if (choice) *choice = bps * 16 + bcl;
   if (best_ms) *best_ms = best;
+  return RIDC_OK;
+}
+
+extern "C" int ridc_batch_set_launch(ridc_batch h, int choice) {
+  BatchCtx* b = bctx(h);
+  if (!b) return RIDC_ERR_ARG;
+  const int per_sm = choice / 16, cl = choice % 16;
+  if ((per_sm != 1 && per_sm != 2) || (cl != 1 && cl != 2 && cl != 4)) return RIDC_ERR_ARG;
+  b->per_sm = per_sm;
+  b->cl = cl;
   return RIDC_OK;
 }

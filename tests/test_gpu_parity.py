@@ -37,7 +37,7 @@ def test_1d_full_workload_matches_oracle():
     assert rel_l2(got, ref[-1]) <= 1e-12
 
 
-@pytest.mark.parametrize("order", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("order", [1, 2, 3, 5, 8, 12])
 @pytest.mark.parametrize("nsteps", [1, 4, 37])
 def test_1d_orders_and_short_runs(order, nsteps):
     w = inputs.adv_diff_1d(n=64, nsteps=nsteps, dt=1.0 / 256)
