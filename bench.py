@@ -130,8 +130,8 @@ class ClockSampler:
 # DRAM traffic of one full (8-plane) gemm_sym launch from one ncu capture
 # (profiles/gemm_sym_gray_scott_2048_mixed.md: dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the four modes), valid only for the kernel source it was taken on.
-GEMM_TRAFFIC = {"bytes": 2.321e8,
-                "source_sha256": "3d9f9b93ba55ce53f322f4ab84e65454494006107a515387a77d2ed81a434e92"}
+GEMM_TRAFFIC = {"bytes": 2.322e8,
+                "source_sha256": "2137ca4963b6707f42b231ce0b07e18d83ebb1178f2b491e7731bb57f085a1d8"}
 
 
 def gemm_traffic():
