@@ -286,6 +286,8 @@ def run_ensemble(args):
             "dtype": "f64+fp32 solves", "data": "synthetic",
             "config": {"workload": "ensemble_512_dirichlet_adv_diff", "instances": 512,
                        "steps": 256, "n_refine": args.ens_refine, "autotune_choice": choice,
+                       "launch": "one CUDA graph per advance (counter reset + persistent "
+                                 "cluster launch)",
                        "cells_per_step": cells}}
     print(json.dumps(line), flush=True)
 

@@ -243,6 +243,10 @@ int ridc_batch_autotune(ridc_batch b, long nsteps, int* choice, float* best_ms);
  * 128 x 128 for sides >= 128. RIDC_ERR_ARG for another value.                              */
 int ridc_batch_set_launch(ridc_batch b, int choice);
 
+/* CUDA-graph launches so far: every advance (and every autotuner trial) is one graph of a
+ * work-counter reset and the persistent cluster launch. -1 for NULL.                        */
+long ridc_batch_graph_launches(ridc_batch b);
+
 /* Release everything the batch holds (synchronises its stream). NULL is ok.                */
 void ridc_batch_destroy(ridc_batch b);
 

@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
         "ridc_batch_cells": (lg, [vp]),
         "ridc_batch_autotune": (i, [vp, lg, POINTER(c_int), POINTER(ctypes.c_float)]),
         "ridc_batch_set_launch": (i, [vp, i]),
+        "ridc_batch_graph_launches": (lg, [vp]),
         "ridc_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -345,6 +346,10 @@ class Batch:
 
     def cells(self) -> int:
         return lib().ridc_batch_cells(self._h)
+
+    def graph_launches(self) -> int:
+        """CUDA graphs launched so far (one per advance or autotuner trial)."""
+        return lib().ridc_batch_graph_launches(self._h)
 
     def set_launch(self, choice: int) -> None:
         """Launch shape CTAs per SM * 16 + cluster size, as autotune() reports it."""

@@ -1,5 +1,6 @@
 // Batched ensemble: many independent RIDC instances (2D Dirichlet advection-diffusion of
-// uneven grid sizes, orders and coefficients) advanced by one persistent launch.
+// uneven grid sizes, orders and coefficients) advanced by one persistent launch, replayed
+// as a CUDA graph.
 //
 // A cluster of CL CTAs (CL = 1, 2 or 4, chosen by the autotuner) takes instances from a shared
 // counter, largest work first (a longest-processing-time order fixed at creation), and
@@ -394,6 +395,12 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
 struct BatchCtx {
   int n = 0;
   cudaStream_t stream = nullptr;
+  // every advance is one CUDA graph (counter reset + the persistent cluster launch), captured
+  // on a private stream (the caller's may be the legacy default stream, which cannot be
+  // captured), updated in place while its shape holds and launched on the caller's stream
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long graph_launches = 0;
   int nref = 0;
   std::vector<EnsInst> inst;           // host mirror (progress kept in sync on the host)
   std::vector<EnsClass> cls;
@@ -429,12 +436,12 @@ static void b_free(BatchCtx* b) {
 }
 
 template <int CL>
-static int launch_cl(BatchCtx* b, const EnsArgs& a, int grid) {
+static int launch_cl(cudaStream_t stream, const EnsArgs& a, int grid) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(ENS_THREADS);
   cfg.dynamicSmemBytes = 0;
-  cfg.stream = b->stream;
+  cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
@@ -499,14 +506,42 @@ static int batch_run(BatchCtx* b, long nsteps, int cl, int per_sm, const int* or
     a.nmask[I.P] = (int)masks.size();
     for (int j = 0; j < I.P; ++j) newp[I.P][j] = p[j];
   }
-  cudaError_t e = cudaMemsetAsync(b->next_dev, 0, sizeof(int), b->stream);
-  if (e != cudaSuccess) return cuda_status(e);
   const int grid = grid_for(b, cl, per_sm, count);
-  int rc;
-  if (cl == 4) rc = launch_cl<4>(b, a, grid);
-  else if (cl == 2) rc = launch_cl<2>(b, a, grid);
-  else rc = launch_cl<1>(b, a, grid);
+  // capture: work-counter reset + the persistent launch
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_status(e);
+  int rc = cuda_status(cudaMemsetAsync(b->next_dev, 0, sizeof(int), b->cap_stream));
+  if (rc == RIDC_OK) {
+    if (cl == 4) rc = launch_cl<4>(b->cap_stream, a, grid);
+    else if (cl == 2) rc = launch_cl<2>(b->cap_stream, a, grid);
+    else rc = launch_cl<1>(b->cap_stream, a, grid);
+  }
+  e = cudaStreamEndCapture(b->cap_stream, &graph);
+  if (rc != RIDC_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc != RIDC_OK ? rc : cuda_status(e);
+  }
+  if (b->gexec) {   // same shape (same kernel instance): update the parameters in place
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(b->gexec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();   // the update is refused when the shape changed: rebuild
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+  }
+  if (!b->gexec) {
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    if (e != cudaSuccess) {
+      b->gexec = nullptr;
+      cudaGraphDestroy(graph);
+      return cuda_status(e);
+    }
+  }
+  cudaGraphDestroy(graph);
+  rc = cuda_status(cudaGraphLaunch(b->gexec, b->stream));
   if (rc != RIDC_OK) return rc;
+  b->graph_launches++;
   for (EnsInst& I : b->inst)
     for (int j = 0; j < I.P; ++j) I.p[j] = newp[I.P][j];
   return RIDC_OK;
@@ -545,9 +580,12 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     b_free(b);
     for (int p = 0; p <= EMaxP; ++p)
       if (b->masks_dev[p]) cudaFree(b->masks_dev[p]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     return code;
   };
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(RIDC_ERR_CUDA);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -680,7 +718,14 @@ extern "C" void ridc_batch_destroy(ridc_batch h) {
   b_free(b);
   for (int p = 0; p <= EMaxP; ++p)
     if (b->masks_dev[p]) cudaFree(b->masks_dev[p]);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
+}
+
+extern "C" long ridc_batch_graph_launches(ridc_batch h) {
+  BatchCtx* b = bctx(h);
+  return b ? b->graph_launches : -1;
 }
 
 // f^N and F of instance i's level-0 slot 0 (initial state), by a 1-step-free launch of the

@@ -104,3 +104,16 @@ def test_launch_shape_can_be_set_and_does_not_change_results():
         for bad in (0, 16 + 3, 3 * 16 + 1):
             with pytest.raises(RidcError):
                 b.set_launch(bad)
+
+
+def test_every_advance_is_one_cuda_graph_launch():
+    ws = inputs.ensemble(6, nsteps=5)
+    ref = _run_batch(ws, 5)
+    with Batch(ws) as b:
+        b.set_initial([w.u0[0].copy() for w in ws])
+        g0 = b.graph_launches()
+        for k in (1, 1, 1, 2):   # the graph is updated in place between these
+            b.advance(k)
+        assert b.graph_launches() - g0 == 4
+        for i in range(len(ws)):
+            np.testing.assert_array_equal(b.solution(i), ref[i])
