@@ -109,9 +109,9 @@ def test_fp64_batched_solve_matches_oracle(kind, n):
 # ---------------------------------------------------------------- 2D mixed (BF16x3 + refinement)
 @pytest.mark.parametrize("kind", ["neumann", "dirichlet"])
 @pytest.mark.parametrize("n_refine", [0, 1, 2])
-def test_mixed_batched_solve_accuracy(kind, n_refine):
+@pytest.mark.parametrize("n", [256, 768])   # 768: N/2 = 384, three 128-column forward tiles
+def test_mixed_batched_solve_accuracy(kind, n_refine, n):
     need_cuda()
-    n = 256
     g = np.random.default_rng(7)
     if kind == "neumann":
         w = inputs.gray_scott_2d(n=n, nsteps=1)
@@ -130,6 +130,13 @@ def test_mixed_batched_solve_accuracy(kind, n_refine):
     for p in range(planes):
         want = prob.solve(np.stack([r[p]] * S), w.dt)[p % S]
         assert rel_l2(got[p], want) <= bar, (p, rel_l2(got[p], want))
+
+
+def test_gray_scott_mixed_matches_oracle_768():
+    w = inputs.gray_scott_2d(n=768, nsteps=9, seed=8)
+    got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, w.order)
+    assert rel_l2(got, ref) <= 1e-8
 
 
 def test_gray_scott_mixed_matches_oracle_256():
