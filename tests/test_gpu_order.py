@@ -83,3 +83,14 @@ def test_gray_scott_order_reduction_on_noisy_data_is_the_methods():
     sols = [oracle.ridc_sequential(prob, w.u0, 16.0 / nt, nt, 4) for nt in nts]
     ref = [np.linalg.norm(sols[i] - sols[i + 1]) for i in range(len(sols) - 1)]
     np.testing.assert_allclose(gpu, ref, rtol=1e-6)
+
+
+@pytest.mark.parametrize("n", [1024, 2048, 4096])
+def test_dirichlet_workload_keeps_order_4_at_full_sizes(n):
+    """The 4096^2 workload's problem (a = b = 1, nu = 1e-3, modes k <= 16) at N = 1024,
+    2048 and 4096: self-convergence at fixed N with dt = 2/N, 1/N, 1/(2N) (64, 128 and 256
+    steps), mixed BF16x3 solves with 2 refinement passes."""
+    need_cuda()
+    w = inputs.adv_diff_2d(n=n, nsteps=64)
+    slopes, diffs = _self_convergence(w, 128.0 / n, (64, 128, 256), "mixed_bf16x3")
+    assert slopes[-1] > 3.6, (slopes, diffs)
