@@ -20,6 +20,8 @@
  *     Host pointers may be pageable or pinned.
  *   - A handle is used by one host thread at a time. Work is ordered on the CUDA stream given
  *     at creation; calls that return data to the caller synchronise that stream.
+ *   - A handle lives on the CUDA device that was current at its creation; every call on it
+ *     runs there and leaves the caller's current device as it found it.
  *   - Device memory belongs to the library and is released by ridc_destroy().
  */
 #ifndef RIDC_H

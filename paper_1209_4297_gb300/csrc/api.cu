@@ -59,12 +59,6 @@ int cuda_status(cudaError_t e) {
   return RIDC_ERR_CUDA;
 }
 
-#define RIDC_TRY(expr)                 \
-  do {                                 \
-    int rc__ = (expr);                 \
-    if (rc__ != RIDC_OK) return rc__;  \
-  } while (0)
-#define RIDC_CUDA(expr) RIDC_TRY(cuda_status(expr))
 
 // ------------------------------------------------------------------------------------------
 // lock-step schedule (Section III-E)
@@ -430,6 +424,7 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
 extern "C" void ridc_destroy(ridc_handle h) {
   if (!h) return;
   Ctx* c = reinterpret_cast<Ctx*>(h);
+  DeviceGuard dg(c->device);
   cudaStreamSynchronize(c->stream);
   free_all(c);
   delete c;
@@ -514,6 +509,7 @@ static int start_from(Ctx* c, const double* u0, int on_device) {
 extern "C" int ridc_set_initial(ridc_handle h, const double* u0, size_t count, int on_device) {
   Ctx* c = ctx_of(h);
   if (!c || !u0 || count != (size_t)c->plane) return RIDC_ERR_ARG;
+  DeviceGuard dg(c->device);
   c->seg_base = 0;
   c->prof_steps = 0;
   return start_from(c, u0, on_device);
@@ -575,6 +571,7 @@ extern "C" int ridc_solve_planes(ridc_handle h, const double* r, double* delta, 
                                  int on_device) {
   Ctx* c = ctx_of(h);
   if (!c || !r || !delta) return RIDC_ERR_ARG;
+  DeviceGuard dg(c->device);
   if (c->dim != 2) return RIDC_ERR_UNSUPPORTED;
   if (nplanes < 1 || nplanes > c->P * c->S) return RIDC_ERR_ARG;
   const long nn = (long)c->n * c->n;
@@ -726,6 +723,7 @@ static int advance_run(Ctx* c, long nsteps) {
 extern "C" int ridc_advance(ridc_handle h, long nsteps) {
   Ctx* c = ctx_of(h);
   if (!c || nsteps < 0) return RIDC_ERR_ARG;
+  DeviceGuard dg(c->device);
   if (!c->initialised) return RIDC_ERR_ARG;
   const long R = c->restart_every;
   while (nsteps > 0) {
@@ -794,6 +792,7 @@ extern "C" int ridc_get_level(ridc_handle h, int level, double* out, size_t coun
                               int out_on_device, long* step) {
   Ctx* c = ctx_of(h);
   if (!c || !out || level < 0 || level >= c->P || count != (size_t)c->plane) return RIDC_ERR_ARG;
+  DeviceGuard dg(c->device);
   if (!c->initialised) return RIDC_ERR_ARG;
   RIDC_TRY(check_device_error(c));
   if (step) *step = c->seg_base + c->p[level];
@@ -865,6 +864,7 @@ static void fill_header(const Ctx* c, StateHeader* hd) {
 extern "C" int ridc_save_state(ridc_handle h, void* buf, size_t* len) {
   Ctx* c = ctx_of(h);
   if (!c || !len) return RIDC_ERR_ARG;
+  DeviceGuard dg(c->device);
   if (!c->initialised) return RIDC_ERR_ARG;
   const size_t need = sizeof(StateHeader) + state_payload(c);
   if (!buf) {
@@ -898,6 +898,7 @@ extern "C" int ridc_save_state(ridc_handle h, void* buf, size_t* len) {
 extern "C" int ridc_load_state(ridc_handle h, const void* buf, size_t len) {
   Ctx* c = ctx_of(h);
   if (!c || !buf || len < sizeof(StateHeader)) return RIDC_ERR_ARG;
+  DeviceGuard dg(c->device);
   StateHeader hd, mine;
   memcpy(&hd, buf, sizeof(hd));
   fill_header(c, &mine);
@@ -991,6 +992,7 @@ extern "C" int ridc_debug_stall_next_gemm(ridc_handle h) {
 extern "C" int ridc_set_profiling(ridc_handle h, int enable) {
   Ctx* c = ctx_of(h);
   if (!c) return RIDC_ERR_ARG;
+  DeviceGuard dg(c->device);
   prof_collect(c);
   for (int k = 0; k < RIDC_KERNEL_COUNT; ++k) { c->k_launch[k] = 0; c->k_ms[k] = 0.0; }
   if (enable < 0) return RIDC_ERR_ARG;

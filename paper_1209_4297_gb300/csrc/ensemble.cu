@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
 // ---------------------------------------------------------------------------------------------
 struct BatchCtx {
   int n = 0;
+  int device = 0;                      // the device the batch lives on
   cudaStream_t stream = nullptr;
   // every advance is one CUDA graph (counter reset + the persistent cluster launch), captured
   // on a private stream (the caller's may be the legacy default stream, which cannot be
@@ -588,6 +589,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     return fail(RIDC_ERR_CUDA);
   int dev = 0;
   cudaGetDevice(&dev);
+  b->device = dev;
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
   if (b->sms <= 0) b->sms = 1;
   // side classes and their FP32 eigenvector tables
@@ -714,6 +716,7 @@ static BatchCtx* bctx(ridc_batch h) { return reinterpret_cast<BatchCtx*>(h); }
 extern "C" void ridc_batch_destroy(ridc_batch h) {
   BatchCtx* b = bctx(h);
   if (!b) return;
+  DeviceGuard dg(b->device);
   cudaStreamSynchronize(b->stream);
   b_free(b);
   for (int p = 0; p <= EMaxP; ++p)
@@ -754,6 +757,7 @@ __global__ void ens_init_kernel(EnsInst* inst, int ninst) {
 extern "C" int ridc_batch_set_initial(ridc_batch h, const double* const* u0, int on_device) {
   BatchCtx* b = bctx(h);
   if (!b || !u0) return RIDC_ERR_ARG;
+  DeviceGuard dg(b->device);
   for (int i = 0; i < b->n; ++i) {
     if (!u0[i]) return RIDC_ERR_ARG;
     EnsInst& I = b->inst[i];
@@ -779,6 +783,7 @@ extern "C" int ridc_batch_set_initial(ridc_batch h, const double* const* u0, int
 extern "C" int ridc_batch_advance(ridc_batch h, long nsteps) {
   BatchCtx* b = bctx(h);
   if (!b || nsteps < 0 || !b->initialised) return RIDC_ERR_ARG;
+  DeviceGuard dg(b->device);
   if (nsteps == 0) return RIDC_OK;
   return batch_run(b, nsteps, b->cl, b->per_sm, b->order_dev, b->n);
 }
@@ -787,6 +792,7 @@ extern "C" int ridc_batch_get_solution(ridc_batch h, int i, double* out, size_t 
                                        int out_on_device) {
   BatchCtx* b = bctx(h);
   if (!b || !out || i < 0 || i >= b->n || !b->initialised) return RIDC_ERR_ARG;
+  DeviceGuard dg(b->device);
   const EnsInst& I = b->inst[i];
   if (count != (size_t)I.s * I.s) return RIDC_ERR_ARG;
   const int top = I.P - 1;
@@ -817,6 +823,7 @@ extern "C" long ridc_batch_cells(ridc_batch h) {
 extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float* best_ms) {
   BatchCtx* b = bctx(h);
   if (!b || nsteps < 1) return RIDC_ERR_ARG;
+  DeviceGuard dg(b->device);
   if (!b->initialised) return RIDC_ERR_ARG;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

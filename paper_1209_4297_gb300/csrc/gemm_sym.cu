@@ -426,13 +426,8 @@ int gemm_sym_fwd_bn(int n) { return (n / 2) % 256 == 0 ? 256 : 128; }
 template <bool FWD, int BN>
 static int launch_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                       const CUtensorMap* bl, const SymArgs& a, int sms) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_sym_kernel<FWD, BN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM_MAX);
-    if (e != cudaSuccess) return cuda_status(e);
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  RIDC_TRY(raise_smem_limit_once(gemm_sym_kernel<FWD, BN>, SY_SMEM_MAX, &attr_done));
   const int ntiles = (FWD ? 2 : 1) * (a.rows / SY_BM) * (a.H / BN);
   dim3 grid(ntiles < sms ? ntiles : sms);
   const int smem = sy_smem_base<FWD, BN>() + (a.mode == SYM_FWD_DEN ? a.n * 4 : 0);
@@ -445,13 +440,7 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
                     __nv_bfloat16* ol, float* o32) {
   const int n = c->n;
   if (n % 256 != 0 || n > SY_MAXN) return RIDC_ERR_UNSUPPORTED;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  const int sms = current_sm_count();
   SymArgs a{};
   a.n = n;
   a.H = n / 2;

@@ -288,13 +288,9 @@ int launch_1d(Ctx* c, long nsteps_pipe, int init_only) {
   a.wq = c->tri + c->npad + 3 + c->n;
   const int CL = init_only ? 1 : oned_cluster(c->P);
   const size_t smem = oned_smem_doubles(c->P, c->n, c->npad) * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(ridc1d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kOneDMaxSmemDoubles * sizeof(double)));
-    if (e != cudaSuccess) return cuda_status(e);
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  RIDC_TRY(raise_smem_limit_once(ridc1d_kernel, (int)(kOneDMaxSmemDoubles * sizeof(double)),
+                                 &attr_done));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(ONED_THREADS);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -158,8 +159,60 @@ struct Ctx {
 
 // ---- host helpers -------------------------------------------------------------------------------
 int cuda_status(cudaError_t e);
+// return the RIDC_* code of a failed call / CUDA call from the enclosing int function
+#define RIDC_TRY(expr)                 \
+  do {                                 \
+    const int rc__ = (expr);           \
+    if (rc__ != RIDC_OK) return rc__;  \
+  } while (0)
+#define RIDC_CUDA(expr) RIDC_TRY(cuda_status(expr))
 // cudaMalloc behind the allocation-failure hook of ridc_debug_fail_alloc
 cudaError_t dev_malloc(void** p, size_t bytes);
+
+// The calls of a handle run on the device it was created on: the guard makes that device
+// current for the call and gives the caller's current device back on return.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess)
+      prev = cur;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// Kernel attributes are per device: raise a kernel's dynamic shared-memory limit once on
+// each device that launches it (bit d of *done: device d is set up).
+template <class Kernel>
+inline int raise_smem_limit_once(Kernel kernel, int bytes, std::atomic<unsigned long long>* done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done->load() & bit) return RIDC_OK;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_status(e);
+  done->fetch_or(bit);
+  return RIDC_OK;
+}
+
+// SM count of the current device (queried once per device)
+inline int current_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int s = cache[dev & 63].load();
+  if (s <= 0) {
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    if (s <= 0) s = 1;
+    cache[dev & 63].store(s);
+  }
+  return s;
+}
 void prof_begin(Ctx* c, int kind, cudaEvent_t* e0);
 void prof_end(Ctx* c, int kind, cudaEvent_t e0);
 
