@@ -205,15 +205,21 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
       na = k;
     }
     __syncthreads();
-    // right-hand sides of this CTA's advancing levels
+    // right-hand sides of this CTA's advancing levels; the base of each new state
+    // (eta^0_n, or eta^{j-1}_{n+1}, which the right-hand side reads anyway) is kept in E
     for (int q = 0; q < na; ++q) {
       const int j = lev[q];
       const long nj = p[j];
       double* r = R + (size_t)q * npad;
+      double* e = E + (size_t)q * n;
       // ring reads bypass L1 (__ldcg): other SMs of the cluster wrote them
       if (j == 0) {
         const double* F0 = a.F[0] + (nj % a.cap[0]) * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = a.dt * __ldcg(F0 + i);
+        const double* e0 = a.eta[0] + (nj % a.cap[0]) * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          r[i] = a.dt * __ldcg(F0 + i);
+          e[i] = __ldcg(e0 + i);
+        }
       } else {
         const double* ej = a.eta[j] + (nj % a.cap[j]) * n;
         const double* fj = a.fN[j] + (nj % a.cap[j]) * n;
@@ -223,25 +229,22 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
         const int m = (int)(nj - b);
         const double* w = a.wq + ((size_t)j * P + m) * P;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          double acc = fma(a.dt, __ldcg(fj + i) - __ldcg(fp + i), __ldcg(ej + i) - __ldcg(ep + i));
+          const double base = __ldcg(ep + i);
+          double acc = fma(a.dt, __ldcg(fj + i) - __ldcg(fp + i), __ldcg(ej + i) - base);
           for (int k = 0; k <= j; ++k)
             acc = fma(a.dt * w[k], __ldcg(a.F[j - 1] + ((b + k) % a.cap[j - 1]) * n + i), acc);
           r[i] = acc;
+          e[i] = base;
         }
       }
     }
     __syncthreads();
     for (int q = 0; q < na; ++q)
       tri_solve_block(R + (size_t)q * npad, n, npad, rp, corr, sfac, gvec, cyclic, scratch);
-    // new states
-    for (int q = 0; q < na; ++q) {
-      const int j = lev[q];
-      const long nj = p[j];
-      const double* base = (j == 0) ? a.eta[0] + (nj % a.cap[0]) * n
-                                    : a.eta[j - 1] + ((nj + 1) % a.cap[j - 1]) * n;
+    // new states: base + delta (each thread updates the entries it stored the base of)
+    for (int q = 0; q < na; ++q)
       for (int i = threadIdx.x; i < n; i += blockDim.x)
-        E[(size_t)q * n + i] = __ldcg(base + i) + R[(size_t)q * npad + i];
-    }
+        E[(size_t)q * n + i] += R[(size_t)q * npad + i];
     __syncthreads();
     for (int q = 0; q < na; ++q) {
       const int j = lev[q];
@@ -254,8 +257,7 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
     if (threadIdx.x == 0)   // every CTA follows every level's progress
       for (int j = 0; j < P; ++j)
         if (mask & (1u << j)) p[j]++;
-    __syncthreads();
-    cluster_sync_all();
+    cluster_sync_all();     // also orders this CTA's shared memory (p) for the next step
   }
   if (rank == 0 && threadIdx.x < kMaxOrder) a.p_dev[threadIdx.x] = p[threadIdx.x];
 }
