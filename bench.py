@@ -280,6 +280,17 @@ def run_ensemble(args):
         times.append(e0.elapsed_time(e1))
     b.close()
     ms = statistics.median(times)
+    # algorithmic FP32 work of the solves: per advancing level and pass, the four products
+    # of the fast diagonalisation, each 2 side^3 flop (full eigenvector tables)
+    from paper_1209_4297_gb300 import schedule_plan
+    passes = 1 + args.ens_refine
+    gemm_flops = 0.0
+    for w in ws:
+        levels = sum(bin(int(m)).count("1") for m in schedule_plan(w.order, 256))
+        gemm_flops += levels * 4 * 2.0 * w.n ** 3 * passes
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sms * 128 * 2 * 2070e6   # FP32 lanes per SM x FMA x max SM clock
+    gemm_tf = gemm_flops / (ms * 1e-3) / 1e12
     line = {"metric": "ensemble cell-updates/s (sum over instances of side^2 x 256 steps)",
             "value": cells * 256 / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -288,7 +299,15 @@ def run_ensemble(args):
                        "steps": 256, "n_refine": args.ens_refine, "autotune_choice": choice,
                        "launch": "one CUDA graph per advance (counter reset + persistent "
                                  "cluster launch)",
-                       "cells_per_step": cells}}
+                       "cells_per_step": cells},
+            "roofline": {"bound": "alu", "kernel": "ensemble_kernel (FP32 SIMT solves)",
+                         "achieved": gemm_tf, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                         "frac": gemm_tf * 1e12 / fp32_peak,
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz "
+                                        "(nominal)",
+                         "note": "algorithmic FP32 flops of the solves (4 products of "
+                                 "2 side^3 per level and pass) over the whole launch, which "
+                                 "also runs the FP64 right-hand sides, residuals and finalize"}}
     print(json.dumps(line), flush=True)
 
 
