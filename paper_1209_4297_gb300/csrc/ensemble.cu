@@ -10,9 +10,10 @@
 // visible to the others); different clusters never wait on one another. Per pipeline step of
 // an instance, for every advancing level (Section III, eq. (pred) / eq. (corr)):
 //   1. right-hand side in delta form, FP64 (defect + Lagrange quadrature, Section III-C);
-//   2. (I - dt nu L) delta = r by fast diagonalisation in FP32: four FP32 SIMT GEMMs with the
-//      sine eigenvectors of the cell-centred Dirichlet Laplacian (one table per grid side), in
-//      64 x 64 or 128 x 128 tiles (the autotuner picks one per side);
+//   2. (I - dt nu L) delta = r by fast diagonalisation in FP32: four transforms with the sine
+//      eigenvectors of the cell-centred Dirichlet Laplacian (tables per grid side), each a
+//      parity-split pair of FP32 SIMT products of half size, in 64 x 32 or 128 x 64 tiles of
+//      half-columns (the autotuner picks one per side);
 //   3. optional refinement: FP64 residual r - (I - dt nu L) delta, FP32 solve, FP64 update;
 //   4. eta = base + delta in FP64, then f^N = -a u_x - b u_y and f = f^N + nu L eta (FP64).
 // FP64 work uses integer bit operations for conversions and sign flips (GB300's FP64 pipe is
@@ -81,11 +82,12 @@ struct EnsInst {
 };
 
 struct EnsClass {
-  const float* Q;    // [s][s]  Q[x][k]
-  const float* Qt;   // [s][s]
-  const float* lam;  // [s]
+  const float* Qts;  // [s][s]  Qts[c][x] = Q[x][k]: rows of Q^T in split order c = g s/2 + k'
+  const float* Qs;   // [s][s]  Qs[x][c] = Q[x][k]: Q with its columns in split order
+  const float* lam;  // [s]     eigenvalues in split order
   int s;
-  int variant;       // GEMM tile: 0 = 64 x 64 (4 x 4 per thread), 1 = 128 x 128 (8 x 8)
+  int variant;       // GEMM tile: 0 = 64 rows x 32 half-columns (4 x 2+2 per thread),
+                     //            1 = 128 rows x 64 half-columns (8 x 4+4 per thread)
 };
 
 struct EnsArgs {
@@ -105,70 +107,112 @@ struct EnsArgs {
   int nref;
 };
 
-// ---- cluster-level FP32 GEMM: C[row][m] = sum_k A[row][k] B[m][k], rows = np * s, stored
-// transposed per plane out[plane][m][row % s], optionally times 1/(1 - dtnu (lam[row % s] +
-// lam[m])). Block tile (16 TM) x (16 TN), TM x TN per thread; tiles are dealt round-robin to
-// the CL CTAs of the cluster. 16-deep K slices: the next slice is fetched into registers
-// (float4) while the current one is multiplied out of shared memory (two buffers).
+// ---- cluster-level FP32 GEMMs of the fast diagonalisation, parity-split ----------------------
+// The sine eigenvectors obey Q[s-1-x][k] = (-1)^k Q[x][k]. With H = s/2 and spectral indices
+// in split order (even k, then odd k: c = g H + k', k = 2k' + g) every transform is two
+// (rows x H) x (H x H) products instead of one (rows x s) x (s x s): half the flops.
+//   forward (FWD): out[.][g H + k'] = sum_{x'<H} (A[x'] +- A[s-1-x']) Q[x'][2k'+g]; A is
+//                  butterflied as it is loaded, B rows are rows of Qts (Q^T in split order);
+//   inverse:       out[.][x'] = E + O, out[.][s-1-x'] = E - O with E = sum_{k'} A[k'] Q[x'][2k'],
+//                  O = sum_{k'} A[H+k'] Q[x'][2k'+1]; B rows are rows of Qs (Q, columns in
+//                  split order).
+// Every thread accumulates both halves (TM rows x TN/2 columns each), so a block tile covers
+// 16 TM rows x 8 TN half-columns. Results are stored transposed per plane, out[plane][m][row %
+// s], optionally times 1/(1 - dtnu (lam[row % s] + lam[m])) (forward, split order). Tiles are
+// dealt round-robin to the CL CTAs of the cluster. 16-deep K slices: the next slice is fetched
+// into registers (float4) while the current one is multiplied out of shared memory.
 template <int TM, int TN>
-struct SgSmem {
-  float A[2][16][16 * TM + 4];
-  float B[2][16][16 * TN + 4];
+struct DualSmem {
+  float A[2][2][16][16 * TM + 4];   // [half][buffer][k][row]
+  float B[2][2][16][8 * TN + 4];    // [half][buffer][k][column]
 };
+constexpr size_t ENS_SMEM_BYTES =
+    sizeof(DualSmem<8, 8>) > sizeof(DualSmem<4, 4>) ? sizeof(DualSmem<8, 8>) : sizeof(DualSmem<4, 4>);
 
-union EnsSmem {
-  SgSmem<4, 4> s44;
-  SgSmem<8, 8> s88;
-};
+__device__ __forceinline__ float4 f4_add(float4 a, float4 b, float sg) {
+  return make_float4(a.x + sg * b.x, a.y + sg * b.y, a.z + sg * b.z, a.w + sg * b.w);
+}
 
-template <int TM, int TN>
-__device__ void block_sgemm(const float* __restrict__ A, const float* __restrict__ B,
-                            float* __restrict__ out, int s, int rows, const float* lam,
-                            float dtnu, bool scale, SgSmem<TM, TN>& sm, int rank, int CL) {
-  constexpr int BM = 16 * TM, BN = 16 * TN;
-  constexpr int AV = BM * 4 / ENS_THREADS, BV = BN * 4 / ENS_THREADS;
+template <int TM, int TN, bool FWD>
+__device__ void dual_sgemm(const float* __restrict__ A, const float* __restrict__ B,
+                           float* __restrict__ out, int s, int rows, const float* lam,
+                           float dtnu, bool scale, DualSmem<TM, TN>& sm, int rank, int CL) {
+  constexpr int BM = 16 * TM, BH = 8 * TN, TH = TN / 2;
+  constexpr int AV = BM * 4 / ENS_THREADS;            // float4 of A per thread and half
+  constexpr int BV = (BH * 4 + ENS_THREADS - 1) / ENS_THREADS;
   const int t = threadIdx.x;
   const int tr = t & 15, tc = t >> 4;
-  const int nrt = (rows + BM - 1) / BM, nct = (s + BN - 1) / BN;
-  const int KT = s / 16;
+  const int H = s / 2;
+  const int nrt = (rows + BM - 1) / BM, nct = (H + BH - 1) / BH;
+  const int KT = H / 16;
   for (int tile = rank; tile < nrt * nct; tile += CL) {
-    const int row0 = (tile / nct) * BM, col0 = (tile % nct) * BN;
-    float acc[TM][TN];
+    const int row0 = (tile / nct) * BM, col0 = (tile % nct) * BH;
+    float acc[2][TM][TH];
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-    float4 ra[AV], rb[BV];
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TH; ++j) acc[h][i][j] = 0.f;
+    float4 ra[2][AV], rb[2][BV];
     auto fetch = [&](int kt) {
 #pragma unroll
       for (int v = 0; v < AV; ++v) {
         const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3, gr = row0 + lr;
-        ra[v] = (gr < rows) ? *reinterpret_cast<const float4*>(A + (long)gr * s + kt * 16 + q * 4)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int k0 = kt * 16 + q * 4;
+        if (gr < rows) {
+          const float* ar = A + (long)gr * s;
+          if (FWD) {
+            // x' = k0..k0+3 and their mirrors s-1-x' (a reversed float4)
+            const float4 x = *reinterpret_cast<const float4*>(ar + k0);
+            const float4 m4 = *reinterpret_cast<const float4*>(ar + s - 4 - k0);
+            const float4 m = make_float4(m4.w, m4.z, m4.y, m4.x);
+            ra[0][v] = f4_add(x, m, 1.f);
+            ra[1][v] = f4_add(x, m, -1.f);
+          } else {
+            ra[0][v] = *reinterpret_cast<const float4*>(ar + k0);
+            ra[1][v] = *reinterpret_cast<const float4*>(ar + H + k0);
+          }
+        } else {
+          ra[0][v] = ra[1][v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
 #pragma unroll
       for (int v = 0; v < BV; ++v) {
         const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3, gc = col0 + lr;
-        rb[v] = (gc < s) ? *reinterpret_cast<const float4*>(B + (long)gc * s + kt * 16 + q * 4)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int k0 = kt * 16 + q * 4;
+        if (e < BH * 4 && gc < H) {
+          // forward: rows k' and H + k' of Qts; inverse: row x' of Qs, columns k' and H + k'
+          const float* b0 = FWD ? B + (long)gc * s + k0 : B + (long)gc * s + k0;
+          const float* b1 = FWD ? B + (long)(H + gc) * s + k0 : B + (long)gc * s + H + k0;
+          rb[0][v] = *reinterpret_cast<const float4*>(b0);
+          rb[1][v] = *reinterpret_cast<const float4*>(b1);
+        } else {
+          rb[0][v] = rb[1][v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
     };
     auto stash = [&](int buf) {
 #pragma unroll
-      for (int v = 0; v < AV; ++v) {
-        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
-        sm.A[buf][q * 4 + 0][lr] = ra[v].x;
-        sm.A[buf][q * 4 + 1][lr] = ra[v].y;
-        sm.A[buf][q * 4 + 2][lr] = ra[v].z;
-        sm.A[buf][q * 4 + 3][lr] = ra[v].w;
-      }
+      for (int h = 0; h < 2; ++h) {
 #pragma unroll
-      for (int v = 0; v < BV; ++v) {
-        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
-        sm.B[buf][q * 4 + 0][lr] = rb[v].x;
-        sm.B[buf][q * 4 + 1][lr] = rb[v].y;
-        sm.B[buf][q * 4 + 2][lr] = rb[v].z;
-        sm.B[buf][q * 4 + 3][lr] = rb[v].w;
+        for (int v = 0; v < AV; ++v) {
+          const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
+          sm.A[h][buf][q * 4 + 0][lr] = ra[h][v].x;
+          sm.A[h][buf][q * 4 + 1][lr] = ra[h][v].y;
+          sm.A[h][buf][q * 4 + 2][lr] = ra[h][v].z;
+          sm.A[h][buf][q * 4 + 3][lr] = ra[h][v].w;
+        }
+#pragma unroll
+        for (int v = 0; v < BV; ++v) {
+          const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
+          if (e < BH * 4) {
+            sm.B[h][buf][q * 4 + 0][lr] = rb[h][v].x;
+            sm.B[h][buf][q * 4 + 1][lr] = rb[h][v].y;
+            sm.B[h][buf][q * 4 + 2][lr] = rb[h][v].z;
+            sm.B[h][buf][q * 4 + 3][lr] = rb[h][v].w;
+          }
+        }
       }
     };
     __syncthreads();
@@ -180,15 +224,18 @@ __device__ void block_sgemm(const float* __restrict__ A, const float* __restrict
       if (kt + 1 < KT) fetch(kt + 1);
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
-        float av[TM], bv[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) av[i] = sm.A[buf][kk][tr * TM + i];
+        for (int h = 0; h < 2; ++h) {
+          float av[TM], bv[TH];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) bv[j] = sm.B[buf][kk][tc * TN + j];
+          for (int i = 0; i < TM; ++i) av[i] = sm.A[h][buf][kk][tr * TM + i];
 #pragma unroll
-        for (int i = 0; i < TM; ++i)
+          for (int j = 0; j < TH; ++j) bv[j] = sm.B[h][buf][kk][tc * TH + j];
 #pragma unroll
-          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TH; ++j) acc[h][i][j] = fmaf(av[i], bv[j], acc[h][i][j]);
+        }
       }
       if (kt + 1 < KT) stash(buf ^ 1);
       __syncthreads();
@@ -198,13 +245,24 @@ __device__ void block_sgemm(const float* __restrict__ A, const float* __restrict
       const int gr = row0 + tr * TM + i;
       if (gr >= rows) continue;
       const int plane = gr / s, rl = gr - plane * s;
+      float* op = out + (long)plane * s * s;
 #pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        const int m = col0 + tc * TN + j;
-        if (m >= s) continue;
-        float v = acc[i][j];
-        if (scale) v = __fdividef(v, 1.0f - dtnu * (lam[rl] + lam[m]));
-        out[((long)plane * s + m) * s + rl] = v;
+      for (int j = 0; j < TH; ++j) {
+        const int c = col0 + tc * TH + j;   // k' (forward) or x' (inverse), < H
+        if (c >= H) continue;
+        if (FWD) {
+          float v0 = acc[0][i][j], v1 = acc[1][i][j];
+          if (scale) {
+            v0 = __fdividef(v0, 1.0f - dtnu * (lam[rl] + lam[c]));
+            v1 = __fdividef(v1, 1.0f - dtnu * (lam[rl] + lam[H + c]));
+          }
+          op[(long)c * s + rl] = v0;
+          op[(long)(H + c) * s + rl] = v1;
+        } else {
+          const float ev = acc[0][i][j], ov = acc[1][i][j];
+          op[(long)c * s + rl] = ev + ov;
+          op[(long)(s - 1 - c) * s + rl] = ev - ov;
+        }
       }
     }
   }
@@ -216,32 +274,35 @@ __device__ __forceinline__ void csync() {
   else __syncthreads();
 }
 
-// FP32 fast-diagonalisation solve of np planes: df = Q ((Q^T rf Q) ./ den) Q^T
+// FP32 fast-diagonalisation solve of np planes: df = Q ((Q^T rf Q) ./ den) Q^T, each transform
+// as a parity-split pair of half-size products (spectral indices in split order throughout)
 template <int CL, int TM, int TN>
 __device__ void cl_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf, float* t1,
-                         float* t2, float* df, SgSmem<TM, TN>& sm, int rank) {
+                         float* t2, float* df, DualSmem<TM, TN>& sm, int rank) {
   const int s = C.s, rows = np * s;
-  block_sgemm<TM, TN>(rf, C.Qt, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
+  dual_sgemm<TM, TN, true>(rf, C.Qts, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
   csync<CL>();
-  block_sgemm<TM, TN>(t1, C.Qt, t2, s, rows, C.lam, I.dtnu, true, sm, rank, CL);
+  dual_sgemm<TM, TN, true>(t1, C.Qts, t2, s, rows, C.lam, I.dtnu, true, sm, rank, CL);
   csync<CL>();
-  block_sgemm<TM, TN>(t2, C.Q, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
+  dual_sgemm<TM, TN, false>(t2, C.Qs, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
   csync<CL>();
-  block_sgemm<TM, TN>(t1, C.Q, df, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
+  dual_sgemm<TM, TN, false>(t1, C.Qs, df, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
   csync<CL>();
 }
 
 template <int CL>
 __device__ __forceinline__ void solve_any(const EnsClass& C, const EnsInst& I, int np,
                                           const float* rf, float* t1, float* t2, float* df,
-                                          EnsSmem& sm, int rank) {
-  if (C.variant == 1) cl_solve<CL, 8, 8>(C, I, np, rf, t1, t2, df, sm.s88, rank);
-  else cl_solve<CL, 4, 4>(C, I, np, rf, t1, t2, df, sm.s44, rank);
+                                          unsigned char* smem, int rank) {
+  if (C.variant == 1)
+    cl_solve<CL, 8, 8>(C, I, np, rf, t1, t2, df, *reinterpret_cast<DualSmem<8, 8>*>(smem), rank);
+  else
+    cl_solve<CL, 4, 4>(C, I, np, rf, t1, t2, df, *reinterpret_cast<DualSmem<4, 4>*>(smem), rank);
 }
 
 template <int CL>
 __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_constant__ EnsArgs a) {
-  __shared__ EnsSmem sm;
+  extern __shared__ __align__(16) unsigned char ens_smem[];   // ENS_SMEM_BYTES: GEMM tiles
   __shared__ int item;
   const int rank = (CL > 1) ? (int)cooperative_groups::this_cluster().block_rank() : 0;
   const long cid = blockIdx.x / CL;
@@ -332,7 +393,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
       // 2./3. FP32 solve (the increment overwrites rf, free after the first GEMM), then
       // refinement passes against the FP64 residual
       const float* df = rf;
-      solve_any<CL>(C, I, na, rf, t1, t2, rf, sm, rank);
+      solve_any<CL>(C, I, na, rf, t1, t2, rf, ens_smem, rank);
       for (int pass = 1; pass <= a.nref; ++pass) {
         for (long e = g0; e < na * ss; e += gs)
           dt_tot[e] = (pass == 1) ? e_f32_to_f64(df[e]) : dt_tot[e] + e_f32_to_f64(df[e]);
@@ -347,7 +408,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
           rf[e] = e_f64_to_f32(v);   // safe: df was folded into dt_tot above
         }
         csync<CL>();
-        solve_any<CL>(C, I, na, rf, t1, t2, rf, sm, rank);
+        solve_any<CL>(C, I, na, rf, t1, t2, rf, ens_smem, rank);
       }
       // 4a. new states eta = base + delta (FP64)
       for (int q = 0; q < na; ++q) {
@@ -438,10 +499,12 @@ static void b_free(BatchCtx* b) {
 
 template <int CL>
 static int launch_cl(cudaStream_t stream, const EnsArgs& a, int grid) {
+  static std::atomic<unsigned long long> attr_done{0};
+  RIDC_TRY(raise_smem_limit_once(ensemble_kernel<CL>, (int)ENS_SMEM_BYTES, &attr_done));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(ENS_THREADS);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = ENS_SMEM_BYTES;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -565,8 +628,8 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     if (pr.n_refine < 0 || pr.n_refine > 4) return RIDC_ERR_ARG;
     if (nref >= 0 && pr.n_refine != nref) return RIDC_ERR_ARG;   // one setting per batch
     nref = pr.n_refine;
-    if (grids[i].dim != 2 || grids[i].n < 16 || grids[i].n > 512) return RIDC_ERR_ARG;
-    if (grids[i].n % 16 != 0) return RIDC_ERR_UNSUPPORTED;   // 16-deep float4 K slices
+    if (grids[i].dim != 2 || grids[i].n < 32 || grids[i].n > 512) return RIDC_ERR_ARG;
+    if (grids[i].n % 32 != 0) return RIDC_ERR_UNSUPPORTED;   // 16-deep K slices of n/2
     if (order[i] < 1 || order[i] > EMaxP) return RIDC_ERR_UNSUPPORTED;
     if (!(dt[i] > 0.0) || !std::isfinite(dt[i]) || !(nu[i] > 0.0) || !std::isfinite(nu[i]))
       return RIDC_ERR_ARG;
@@ -601,29 +664,33 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   int smax = 0;
   for (int s : sides) {
     smax = std::max(smax, s);
-    std::vector<float> Q((size_t)s * s), Qt((size_t)s * s), lam(s);
+    // orthonormal sine eigenvectors Q[x][k] (k = 0..s-1 for the modes K = k + 1), stored with
+    // the spectral index in split order c = (k % 2) s/2 + k/2
+    std::vector<float> Qs((size_t)s * s), Qts((size_t)s * s), lam(s);
+    const int H = s / 2;
     for (int k = 0; k < s; ++k) {
       const long K = k + 1;
-      const double c = (K == s) ? std::sqrt(1.0 / s) : std::sqrt(2.0 / s);
+      const int c = (k % 2) * H + k / 2;
+      const double cn = (K == s) ? std::sqrt(1.0 / s) : std::sqrt(2.0 / s);
       const double sk = std::sin(pi * (double)K / (2.0 * s));
-      lam[k] = (float)(-4.0 * (double)s * s * sk * sk);
+      lam[c] = (float)(-4.0 * (double)s * s * sk * sk);
       for (int x = 0; x < s; ++x) {
         const long t = (K * (2L * x + 1)) % (4L * s);
-        const double q = c * std::sin(pi * (double)t / (2.0 * s));
-        Q[(size_t)x * s + k] = (float)q;
-        Qt[(size_t)k * s + x] = (float)q;
+        const double q = cn * std::sin(pi * (double)t / (2.0 * s));
+        Qs[(size_t)x * s + c] = (float)q;
+        Qts[(size_t)c * s + x] = (float)q;
       }
     }
     EnsClass C{};
     C.s = s;
     C.variant = s >= 128 ? 1 : 0;   // until the autotuner decides
     void* p;
-    if ((rc = b_alloc(b, &p, Q.size() * 4)) != RIDC_OK) return fail(rc);
-    cudaMemcpy(p, Q.data(), Q.size() * 4, cudaMemcpyHostToDevice);
-    C.Q = (const float*)p;
-    if ((rc = b_alloc(b, &p, Qt.size() * 4)) != RIDC_OK) return fail(rc);
-    cudaMemcpy(p, Qt.data(), Qt.size() * 4, cudaMemcpyHostToDevice);
-    C.Qt = (const float*)p;
+    if ((rc = b_alloc(b, &p, Qs.size() * 4)) != RIDC_OK) return fail(rc);
+    cudaMemcpy(p, Qs.data(), Qs.size() * 4, cudaMemcpyHostToDevice);
+    C.Qs = (const float*)p;
+    if ((rc = b_alloc(b, &p, Qts.size() * 4)) != RIDC_OK) return fail(rc);
+    cudaMemcpy(p, Qts.data(), Qts.size() * 4, cudaMemcpyHostToDevice);
+    C.Qts = (const float*)p;
     if ((rc = b_alloc(b, &p, lam.size() * 4)) != RIDC_OK) return fail(rc);
     cudaMemcpy(p, lam.data(), lam.size() * 4, cudaMemcpyHostToDevice);
     C.lam = (const float*)p;
@@ -814,7 +881,7 @@ extern "C" long ridc_batch_cells(ridc_batch h) {
   return b ? b->cells_per_step : -1;
 }
 
-// Autotuner. First, per grid side, the GEMM tile (64 x 64 or 128 x 128) that integrates the
+// Autotuner. First, per grid side, the GEMM tile (64 x 32 or 128 x 64) that integrates the
 // instances of that side fastest on their own (one-CTA clusters); then the cluster size (1, 2
 // or 4 CTAs per instance) and the CTAs per SM (1 or 2) that run the whole batch fastest with
 // those tiles. Each trial advances `nsteps` top-level steps from the current state. The
