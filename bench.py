@@ -241,8 +241,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * N * N * args.ref_steps / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "gray_scott_2048_ridc4", "grid": N, "order": ORDER,
-                       "steps_per_sample": args.ref_steps, "dt": 0.5},
+            "config": {"workload": "gray_scott_2048_ridc4_mixed", "grid": N, "species": 2,
+                       "order": ORDER, "top_level_steps": NT, "dt": 0.5, "n_refine": NREF,
+                       "parallelism": "replicas x1",
+                       "reference_sample": f"{args.ref_steps} top-level steps of the workload "
+                                           "per timed step: the FP64 CPU oracle (sequential "
+                                           "IDC order, exact FP64 solves)"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
