@@ -163,3 +163,20 @@ def test_fault_hooks_reject_bad_arguments():
     assert L.ridc_debug_fail_alloc(-1) == -1
     assert L.ridc_debug_fail_alloc(0) == 0
     assert L.ridc_debug_stall_next_gemm(None) == -1
+
+
+def test_binding_tables_match_the_header():
+    """The ctypes binding's kind, precision and kernel-id tables agree with include/ridc.h."""
+    from paper_1209_4297_gb300 import binding as B
+    txt = open(os.path.join(ROOT, "include", "ridc.h")).read()
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(RIDC_[A-Z0-9_]+)\s*=\s*(\d+)", txt))
+    defines = dict((k, int(v)) for k, v in re.findall(r"#define\s+(RIDC_[A-Z0-9_]+)\s+(-?\d+)", txt))
+    for name, val in B.KINDS.items():
+        assert enums["RIDC_" + name.upper()] == val, name
+    for name, val in B.PRECISIONS.items():
+        assert enums["RIDC_" + name.upper()] == val, name
+    ids = {"rhs": "RHS", "gemm_tc": "GEMM_TC", "gemm_f64": "GEMM_F64", "residual": "RESIDUAL",
+           "finalize": "FINALIZE", "ridc1d": "1D"}
+    for name, val in B.KERNELS.items():
+        assert defines["RIDC_KERNEL_" + ids[name]] == val, name
+    assert len(B.KERNELS) == defines["RIDC_KERNEL_COUNT"]
