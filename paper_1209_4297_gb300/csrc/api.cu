@@ -232,13 +232,27 @@ static int build_tables_2d(Ctx* c) {
   for (int x = 0; x < n; ++x)
     for (int k = 0; k < n; ++k) Qt[(size_t)k * n + x] = Q[(size_t)x * n + k];
   if (c->prec == RIDC_FP64) {
-    RIDC_TRY(upload(c, &c->Q, Q));
-    RIDC_TRY(upload(c, &c->Qt, Qt));
+    // even n: the parity-split transforms take Q^T with its rows and Q with its columns in
+    // split order c = (k % 2) n/2 + k/2 (even modes, then odd), and 1/den in split order too;
+    // odd n: plain Q^T and Q, natural order
+    const bool split = n % 2 == 0;
+    const int H = n / 2;
+    auto ord = [&](int k) { return split ? (k % 2) * H + k / 2 : k; };
+    std::vector<double> Qa((size_t)n * n), Qb((size_t)n * n), ls(n);
+    for (int k = 0; k < n; ++k) {
+      ls[ord(k)] = lam[k];
+      for (int x = 0; x < n; ++x) {
+        Qa[(size_t)x * n + ord(k)] = Q[(size_t)x * n + k];    // Q, columns reordered
+        Qb[(size_t)ord(k) * n + x] = Q[(size_t)x * n + k];    // Q^T, rows reordered
+      }
+    }
+    RIDC_TRY(upload(c, &c->Q, Qa));
+    RIDC_TRY(upload(c, &c->Qt, Qb));
     std::vector<double> inv((size_t)c->S * n * n);
     for (int s = 0; s < c->S; ++s)
       for (int ky = 0; ky < n; ++ky)
         for (int kx = 0; kx < n; ++kx)
-          inv[((size_t)s * n + ky) * n + kx] = 1.0 / (1.0 - c->dt * c->nu[s] * (lam[ky] + lam[kx]));
+          inv[((size_t)s * n + ky) * n + kx] = 1.0 / (1.0 - c->dt * c->nu[s] * (ls[ky] + ls[kx]));
     RIDC_TRY(upload(c, &c->inv_den, inv));
   } else {
     // parity split: Q[n-1-x][k] = (-1)^k Q[x][k]; Qe[x'][k'] = Q[x'][2k'], Qo[x'][k'] = Q[x'][2k'+1]
@@ -554,10 +568,11 @@ static int solve_group_mixed(Ctx* c, int p0, int np, bool rhs_split_done, const 
 // total) and solves for the next FP32 increment. The result stays split as total + increment.
 static int solve_planes_dev(Ctx* c, int nplanes, bool rhs_split_done, DeltaParts* out) {
   if (c->prec == RIDC_FP64) {
-    RIDC_TRY(launch_gemm_f64(c, c->r, c->Qt, c->t1, nplanes, EPI_STORE));
-    RIDC_TRY(launch_gemm_f64(c, c->t1, c->Qt, c->t2, nplanes, EPI_SCALE_DEN));
-    RIDC_TRY(launch_gemm_f64(c, c->t2, c->Q, c->t1, nplanes, EPI_STORE));
-    RIDC_TRY(launch_gemm_f64(c, c->t1, c->Q, c->delta, nplanes, EPI_DELTA));
+    // forward products take Q^T (rows in split order for even n), inverse products Q
+    RIDC_TRY(launch_gemm_f64(c, c->r, c->Qt, c->t1, nplanes, EPI_STORE, true));
+    RIDC_TRY(launch_gemm_f64(c, c->t1, c->Qt, c->t2, nplanes, EPI_SCALE_DEN, true));
+    RIDC_TRY(launch_gemm_f64(c, c->t2, c->Q, c->t1, nplanes, EPI_STORE, false));
+    RIDC_TRY(launch_gemm_f64(c, c->t1, c->Q, c->delta, nplanes, EPI_STORE, false));
     *out = {c->delta, nullptr};
     return RIDC_OK;
   }

@@ -6,7 +6,8 @@
 //   residual_kernel  refinement residual r - (I - dt nu L) delta of the mixed solve, parity-
 //                    split along both axes and split into BF16 hi/lo for the next
 //                    tensor-core pass.
-//   gemm_f64_kernel  FP64 fast-diagonalisation GEMM (DFMA; GB300's DMMA is slower than DFMA).
+//   gemm_f64_kernel  FP64 fast-diagonalisation GEMM (DFMA; GB300's DMMA is slower than DFMA),
+//                    parity-split for even n (gemm_f64_split_kernel).
 #include "ridc_internal.h"
 
 namespace ridc {
@@ -479,15 +480,133 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
   }
 }
 
-int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi) {
+// Parity-split form of the same transform for even n (H = n/2; spectral indices in split order
+// c = g H + k', k = 2k' + g; Q[n-1-x][k] = (-1)^k Q[x][k]):
+//   forward: out[.][g H + k'] = sum_{x'<H} (A[x'] +- A[n-1-x']) Q[x'][2k'+g], B = Q^T with its
+//            rows in split order (A is butterflied as it is loaded);
+//   inverse: out[.][x'] = E + O, out[.][n-1-x'] = E - O, E = sum_{k'} A[k'] Q[x'][2k'],
+//            O = sum_{k'} A[H+k'] Q[x'][2k'+1], B = Q with its columns in split order.
+// Half the DFMAs of the plain product. Tile: 64 rows x 32 half-columns, each thread 4 rows x
+// (2 + 2) columns, one accumulator set per half.
+template <bool FWD, int EPI>
+__global__ void __launch_bounds__(256) gemm_f64_split_kernel(const double* __restrict__ A,
+                                                             const double* __restrict__ B,
+                                                             double* __restrict__ out,
+                                                             const double* __restrict__ inv_den,
+                                                             int n, int rows, int S) {
+  constexpr int GH = GB / 2;
+  __shared__ __align__(16) double As[2][GK][GB + 2];
+  __shared__ __align__(16) double Bs[2][GK][GH + 2];
+  const int t = threadIdx.x;
+  const int tr = t & 15, tc = t >> 4;
+  const int H = n / 2;
+  const int row0 = blockIdx.x * GB, col0 = blockIdx.y * GH;
+  double acc[2][4][2] = {};
+  for (int k0 = 0; k0 < H; k0 += GK) {
+    {
+      // A: 64 rows x 16 k per half; thread t loads 4 consecutive k of one row (and mirrors)
+      const int lr = t >> 2, lk = (t & 3) * 4, gr = row0 + lr;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + lk + q;
+        double v0 = 0.0, v1 = 0.0;
+        if (gr < rows && k < H) {
+          const double* ar = A + (long)gr * n;
+          if (FWD) {
+            const double x = ar[k], m = ar[n - 1 - k];
+            v0 = x + m;
+            v1 = x - m;
+          } else {
+            v0 = ar[k];
+            v1 = ar[H + k];
+          }
+        }
+        As[0][lk + q][lr] = v0;
+        As[1][lk + q][lr] = v1;
+      }
+      // B: 32 columns x 16 k per half; thread t loads 2 consecutive k of one column
+      const int lc = t >> 3, lk2 = (t & 7) * 2, gc = col0 + lc;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int k = k0 + lk2 + q;
+        double b0 = 0.0, b1 = 0.0;
+        if (gc < H && k < H) {
+          b0 = FWD ? B[(long)gc * n + k] : B[(long)gc * n + k];
+          b1 = FWD ? B[(long)(H + gc) * n + k] : B[(long)gc * n + H + k];
+        }
+        Bs[0][lk2 + q][lc] = b0;
+        Bs[1][lk2 + q][lc] = b1;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        double a[4], b[2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[h][kk][tr * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) b[j] = Bs[h][kk][tc * 2 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) acc[h][i][j] = fma(a[i], b[j], acc[h][i][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = row0 + tr * 4 + i;
+    if (gr >= rows) continue;
+    const int plane = gr / n, rl = gr - plane * n;
+    double* op = out + (long)plane * n * n;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int cc = col0 + tc * 2 + j;
+      if (cc >= H) continue;
+      if (FWD) {
+        double v0 = acc[0][i][j], v1 = acc[1][i][j];
+        if (EPI == EPI_SCALE_DEN) {
+          const double* id = inv_den + (long)(plane % S) * n * n;
+          v0 *= id[(long)cc * n + rl];
+          v1 *= id[(long)(H + cc) * n + rl];
+        }
+        op[(long)cc * n + rl] = v0;
+        op[(long)(H + cc) * n + rl] = v1;
+      } else {
+        const double ev = acc[0][i][j], ov = acc[1][i][j];
+        op[(long)cc * n + rl] = ev + ov;
+        op[(long)(n - 1 - cc) * n + rl] = ev - ov;
+      }
+    }
+  }
+}
+
+int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi,
+                    bool forward) {
   const int n = c->n, rows = nplanes * n;
-  dim3 grid((rows + GB - 1) / GB, (n + GB - 1) / GB);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_F64, &e0);
-  if (epi == EPI_SCALE_DEN)
-    gemm_f64_kernel<EPI_SCALE_DEN><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, c->S);
-  else
-    gemm_f64_kernel<EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, c->S);
+  if (n % 2 == 0) {
+    dim3 grid((rows + GB - 1) / GB, (n / 2 + GB / 2 - 1) / (GB / 2));
+    if (forward && epi == EPI_SCALE_DEN)
+      gemm_f64_split_kernel<true, EPI_SCALE_DEN><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n,
+                                                                           rows, c->S);
+    else if (forward)
+      gemm_f64_split_kernel<true, EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n,
+                                                                       rows, c->S);
+    else
+      gemm_f64_split_kernel<false, EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n,
+                                                                        rows, c->S);
+  } else {
+    dim3 grid((rows + GB - 1) / GB, (n + GB - 1) / GB);
+    if (epi == EPI_SCALE_DEN)
+      gemm_f64_kernel<EPI_SCALE_DEN><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, c->S);
+    else
+      gemm_f64_kernel<EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, c->S);
+  }
   prof_end(c, RIDC_KERNEL_GEMM_F64, e0);
   return cuda_status(cudaGetLastError());
 }

@@ -113,9 +113,10 @@ struct Ctx {
   __nv_bfloat16* yl = nullptr;
 
   // fast-diagonalisation tables (2D): Q[x][k] orthonormal eigenvectors of the 1D Laplacian
-  double* Q = nullptr;       // [N][N]
-  double* Qt = nullptr;      // [N][N], transpose of Q
-  double* inv_den = nullptr; // [S][N][N]  1 / (1 - dt nu_s (lam_ky + lam_kx)), FP64 path
+  double* Q = nullptr;       // [N][N]   Q, its columns in split order when N is even
+  double* Qt = nullptr;      // [N][N]   Q^T, its rows in split order when N is even
+  double* inv_den = nullptr; // [S][N][N] 1 / (1 - dt nu_s (lam_ky + lam_kx)), FP64 path (split
+                             //           order for ky and kx when N is even)
   float* lam_f = nullptr;    // [N] eigenvalues in split order (even modes, then odd), FP32
   // parity-split eigenvector tables, BF16 hi/lo, each [N][N/2]:
   //   Bf = [Qe^T; Qo^T] (forward products), Bb = [Qe; Qo] (inverse products)
@@ -229,7 +230,10 @@ int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const 
                     double* dout);
 // out = d64 + d32 elementwise over count values (either part may be nullptr)
 int launch_combine(Ctx* c, const double* d64, const float* d32, double* out, long count);
-int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi);
+// one transform of the FP64 fast diagonalisation: forward (contract with Q, B = Q^T rows) or
+// inverse (B = Q); for even n parity-split (tables in split order), otherwise plain
+int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi,
+                    bool forward);
 int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                     const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
                     __nv_bfloat16* ol, float* o32);
@@ -250,7 +254,7 @@ inline long oned_smem_doubles(int P, int n, int npad) {
 int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
 
 // epilogue kinds of the FP64 fast-diagonalisation GEMM
-enum { EPI_STORE = 0, EPI_SCALE_DEN = 1, EPI_DELTA = 2 };
+enum { EPI_STORE = 0, EPI_SCALE_DEN = 1 };
 // modes of the parity-split tensor-core GEMM
 enum { SYM_FWD_SPLIT = 0, SYM_FWD_DEN = 1, SYM_BWD_SPLIT = 2, SYM_BWD_F32 = 3 };
 
