@@ -54,7 +54,7 @@ def test_1d_split_advance_is_bitwise_identical():
 
 
 # ---------------------------------------------------------------- 2D FP64
-@pytest.mark.parametrize("n", [24, 40, 64])
+@pytest.mark.parametrize("n", [24, 40, 64, 25, 39])   # odd n: the plain (unsplit) DFMA products
 def test_gray_scott_fp64_small_grids(n):
     w = inputs.gray_scott_2d(n=n, nsteps=25, width=0.3, seed=3)
     got, levels, _ = _run(w)
@@ -86,7 +86,8 @@ def test_gray_scott_fp64_split_advance_bitwise():
     np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("kind,n", [("neumann", 16), ("neumann", 72), ("dirichlet", 40)])
+@pytest.mark.parametrize("kind,n", [("neumann", 16), ("neumann", 72), ("dirichlet", 40),
+                                    ("neumann", 33), ("dirichlet", 27)])
 def test_fp64_batched_solve_matches_oracle(kind, n):
     need_cuda()
     g = np.random.default_rng(n)
