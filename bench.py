@@ -130,8 +130,8 @@ class ClockSampler:
 # DRAM traffic of one full (8-plane) gemm_sym launch from one ncu capture
 # (profiles/gemm_sym_gray_scott_2048_mixed.md: dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the four modes), valid only for the kernel source it was taken on.
-GEMM_TRAFFIC = {"bytes": 2.322e8,
-                "source_sha256": "2137ca4963b6707f42b231ce0b07e18d83ebb1178f2b491e7731bb57f085a1d8"}
+GEMM_TRAFFIC = {"bytes": 2.320e8,
+                "source_sha256": "cc09b2e7b63fe3d683bbdd5b1caf128b58c202f37f04f65109dfeef5b1493a16"}
 
 
 def gemm_traffic():
@@ -322,8 +322,10 @@ def run_single(args):
     integrations, CUDA events, inputs resident): the 1D periodic workload (512 steps, FP64),
     the paper's 1D runs (upwind advection-diffusion to T = 40 with 10 restart intervals;
     viscous Burgers to T = 1),
-    1024^2 Gray-Scott in FP64 (a truncated run: its 2000 steps take minutes) or the 4096^2
-    Dirichlet workload (512 steps, mixed BF16x3 with 2 refinement passes)."""
+    1024^2 Gray-Scott in FP64 (a truncated run: its 2000 steps take minutes), the 4096^2
+    Dirichlet workload (512 steps, mixed, by default BF16x3 with 2 refinement passes) or the
+    2048^2 Gray-Scott workload in a chosen split form and refinement count
+    (--mixed-precision, --n-refine)."""
     import torch
 
     import inputs
@@ -339,13 +341,15 @@ def run_single(args):
         w, prec, nt = inputs.burgers_1d(), "fp64", 2000
     elif args.workload == "gray_scott_1024_fp64":
         w, prec, nt = inputs.gray_scott_2d(n=1024, nsteps=2000), "fp64", args.nt_truncate
+    elif args.workload == "gray_scott_2048_mixed":
+        w, prec, nt = inputs.gray_scott_2d(n=2048, nsteps=1000), args.mixed_precision, args.nt
     else:
-        w, prec, nt = inputs.adv_diff_2d(n=4096, nsteps=512), "mixed_bf16x3", 512
+        w, prec, nt = inputs.adv_diff_2d(n=4096, nsteps=512), args.mixed_precision, 512
     u0 = torch.from_numpy(w.u0).cuda()
 
     def timed(order):
-        it = Integrator.from_workload(w, precision=prec, n_refine=2, stream=stream.cuda_stream,
-                                      order=order)
+        it = Integrator.from_workload(w, precision=prec, n_refine=args.n_refine,
+                                      stream=stream.cuda_stream, order=order)
         for _ in range(args.warmup):
             it.set_initial(u0)
             it.advance(nt)
@@ -381,12 +385,14 @@ def run_single(args):
     line = {"metric": f"RIDC-{w.order} cell-updates/s", "value": cells / (ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "us_per_pipeline_step": 1e3 * ms / (nt + w.order * (w.order - 1) // 2),
-            "higher_is_better": True, "dtype": "f64" if prec == "fp64" else "f64+bf16x3(fp32 acc)",
+            "higher_is_better": True,
+            "dtype": "f64" if prec == "fp64" else f"f64+{prec[6:]}(fp32 acc)",
             "data": "synthetic", "gpu_launches": int(launches),
             "fbe_ms": fbe_ms, "ridc_over_fbe_time": (ms / fbe_ms) if fbe_ms else None,
             "config": {"workload": args.workload, "grid": w.n, "order": w.order,
                        "top_level_steps": nt, "full_steps": w.nsteps, "dt": w.dt,
-                       "restart_every": w.restart_every},
+                       "restart_every": w.restart_every,
+                       "n_refine": None if prec == "fp64" else args.n_refine},
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
@@ -408,11 +414,11 @@ def run_accuracy(args):
     rng = np.random.default_rng(12345)
     toward = np.where(rng.random(w.u0.shape) < 0.5, -np.inf, np.inf)
     u0p = np.nextafter(w.u0, toward)
-    runs = {"mixed": (w.u0, "mixed_bf16x3"), "fp64": (w.u0, "fp64"),
-            "mixed_ulp": (u0p, "mixed_bf16x3")}
+    mp = args.mixed_precision
+    runs = {"mixed": (w.u0, mp), "fp64": (w.u0, "fp64"), "mixed_ulp": (u0p, mp)}
     its = {}
     for k, (u0, prec) in runs.items():
-        its[k] = Integrator.from_workload(w, precision=prec, n_refine=NREF,
+        its[k] = Integrator.from_workload(w, precision=prec, n_refine=args.n_refine,
                                           stream=stream.cuda_stream)
         its[k].set_initial(torch.from_numpy(u0).cuda())
     rows, done, t0 = [], 0, time.perf_counter()
@@ -431,11 +437,12 @@ def run_accuracy(args):
               flush=True)
     for it in its.values():
         it.close()
-    line = {"metric": "relative L2, mixed BF16x3 (2 refinements) vs FP64 GPU, 2048^2 Gray-Scott "
-                      "RIDC-4", "value": rows[-1]["mixed_vs_fp64"], "unit": "relative L2",
-            "higher_is_better": False, "data": "synthetic",
+    line = {"metric": f"relative L2, mixed {mp[6:].upper()} ({args.n_refine} refinements) vs "
+                      "FP64 GPU, 2048^2 Gray-Scott RIDC-4", "value": rows[-1]["mixed_vs_fp64"],
+            "unit": "relative L2", "higher_is_better": False, "data": "synthetic",
             "config": {"workload": "gray_scott_2048_ridc4", "grid": N, "order": ORDER,
-                       "top_level_steps": args.nt, "dt": 0.5, "n_refine": NREF},
+                       "top_level_steps": args.nt, "dt": 0.5, "n_refine": args.n_refine,
+                       "precision": mp},
             "checkpoints": rows}
     print(json.dumps(line), flush=True)
 
@@ -453,7 +460,13 @@ def main():
     ap.add_argument("--workload", default="gray_scott_2048",
                     choices=["gray_scott_2048", "ensemble", "adv_diff_1d", "adv_diff_upwind_1d",
                              "burgers_1d", "gray_scott_1024_fp64", "adv_diff_4096",
-                             "accuracy_2048"])
+                             "accuracy_2048", "gray_scott_2048_mixed"])
+    ap.add_argument("--mixed-precision", default="mixed_bf16x3",
+                    choices=["mixed_bf16x3", "mixed_fp16x3"],
+                    help="split form of the accuracy_2048, adv_diff_4096 and "
+                         "gray_scott_2048_mixed lines (the headline line is BF16x3)")
+    ap.add_argument("--n-refine", type=int, default=NREF,
+                    help="refinement passes of those lines (the headline line uses 2)")
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--ens-refine", type=int, default=1)
     ap.add_argument("--nt-truncate", type=int, default=60)

@@ -72,7 +72,18 @@ typedef enum {
     /* batched ensembles only: solves in FP32 on the CUDA cores, right-hand sides, quadrature
        sums and solution accumulation in FP64, plus n_refine refinement passes against the
        FP64 residual                                                                         */
-    RIDC_FP32_SOLVE = 2
+    RIDC_FP32_SOLVE = 2,
+    /* as RIDC_MIXED_BF16X3 with FP16 hi/lo operands: 22 significant bits per split instead
+       of 16. A pass of either form is also limited by the tensor cores' FP32 accumulation,
+       which grows with N: FP16 gains about 3x per pass at N = 256, little at N >= 1024.
+       FP16's exponent range is narrow, so each operand plane is scaled by a power of two,
+       2^k with max|v| 2^k in [2^(K0-1), 2^K0), K0 = 15 - ceil(log2 N), and the eigenvector
+       tables by 2^(13 + floor(log2(N/2)/2)). Every intermediate of the two-sided transform
+       is then at most N max|v| 2^k <= 2^15 (orthogonal transforms keep the Frobenius norm;
+       the denominators are >= 1). The scale needs the plane's maximum, so the right-hand
+       side and residual kernels stage FP32 values and a split kernel scales and splits them
+       (one more FP32 write and read per value than the BF16 form).                           */
+    RIDC_MIXED_FP16X3 = 3
 } ridc_precision;
 
 typedef struct {
@@ -279,12 +290,14 @@ int ridc_quadrature_weights(int order, double* out, size_t cap);
 /* ---- instrumentation ------------------------------------------------------------------------ */
 
 #define RIDC_KERNEL_RHS       0   /* fused defect + quadrature right-hand side             */
-#define RIDC_KERNEL_GEMM_TC   1   /* BF16x3 tcgen05 fast-diagonalisation GEMM              */
+#define RIDC_KERNEL_GEMM_TC   1   /* BF16x3 / FP16x3 tcgen05 fast-diagonalisation GEMM     */
 #define RIDC_KERNEL_GEMM_F64  2   /* FP64 fast-diagonalisation GEMM                        */
 #define RIDC_KERNEL_RESIDUAL  3   /* FP64 refinement residual + split                      */
 #define RIDC_KERNEL_FINALIZE  4   /* solution accumulation + f^N, f of the new state       */
 #define RIDC_KERNEL_1D        5   /* persistent 1D pipeline kernel                         */
-#define RIDC_KERNEL_COUNT     6
+#define RIDC_KERNEL_SPLIT     6   /* FP16 form: power-of-two scale + hi/lo split of staged
+                                     FP32 operands                                           */
+#define RIDC_KERNEL_COUNT     7
 
 /* CUDA-event timing of kernel launches on the handle's stream: enable = 0 off, 1 every
  * launch, k > 1 only the launches of every k-th 2D pipeline step (steps 0, k, 2k, ...

@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_HERE, "libridc.so")
 KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dirichlet": 2,
          "adv_diff_1d_upwind_periodic": 3, "burgers_1d_dirichlet": 4}
 KINDS_1D = ("adv_diff_1d_periodic", "adv_diff_1d_upwind_periodic", "burgers_1d_dirichlet")
-PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1, "fp32_solve": 2}
-KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5}
+PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1, "fp32_solve": 2, "mixed_fp16x3": 3}
+KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5,
+           "split_f16": 6}
 
 
 class RidcError(RuntimeError):

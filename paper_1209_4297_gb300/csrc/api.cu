@@ -207,14 +207,23 @@ static void build_eigen(int n, bool odd, std::vector<double>& Q, std::vector<dou
   }
 }
 
-static void split_bf16(const std::vector<double>& src, std::vector<__nv_bfloat16>& hi,
-                       std::vector<__nv_bfloat16>& lo) {
+// hi + lo ~= src * 2^e, as BF16 or FP16 pairs (16-bit words of the split operand tables)
+static void split_table(const std::vector<double>& src, bool f16, int e,
+                        std::vector<__nv_bfloat16>& hi, std::vector<__nv_bfloat16>& lo) {
   hi.resize(src.size());
   lo.resize(src.size());
+  const double sc = std::ldexp(1.0, e);
   for (size_t i = 0; i < src.size(); ++i) {
-    const float f = (float)src[i];
-    hi[i] = __float2bfloat16_rn(f);
-    lo[i] = __float2bfloat16_rn((float)(src[i] - (double)__bfloat162float(hi[i])));
+    const double v = src[i] * sc;
+    if (f16) {
+      const __half h = __float2half_rn((float)v);
+      const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
+      std::memcpy(&hi[i], &h, 2);
+      std::memcpy(&lo[i], &l, 2);
+    } else {
+      hi[i] = __float2bfloat16_rn((float)v);
+      lo[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi[i])));
+    }
   }
 }
 
@@ -264,11 +273,22 @@ static int build_tables_2d(Ctx* c) {
           bf[((size_t)g * H + i) * H + j] = Q[(size_t)j * n + 2 * i + g];   // Qe^T / Qo^T
           bb[((size_t)g * H + i) * H + j] = Q[(size_t)i * n + 2 * j + g];   // Qe / Qo
         }
+    // FP16 form: entries are at most sqrt(2/N) in magnitude; 2^qexp, qexp = 13 +
+    // floor(log2(N/2)/2), brings the largest to (2^13, 2^14], inside FP16's range, and keeps
+    // the low halves of all but the tiniest entries clear of its subnormals (the products
+    // accumulate in FP32, where 2^14 times an operand of at most 2^15 is harmless)
+    const bool f16 = c->prec == RIDC_MIXED_FP16X3;
+    c->qexp = 0;
+    c->k0 = f16_k0(n);
+    if (f16) {
+      while ((2L << (2 * (c->qexp + 1))) <= (long)n) ++c->qexp;   // 4^(qexp+1) <= n/2
+      c->qexp += 13;
+    }
     std::vector<__nv_bfloat16> h, l;
-    split_bf16(bf, h, l);
+    split_table(bf, f16, c->qexp, h, l);
     RIDC_TRY(upload(c, &c->Bfh, h));
     RIDC_TRY(upload(c, &c->Bfl, l));
-    split_bf16(bb, h, l);
+    split_table(bb, f16, c->qexp, h, l);
     RIDC_TRY(upload(c, &c->Bbh, h));
     RIDC_TRY(upload(c, &c->Bbl, l));
     std::vector<float> lf(n);   // eigenvalues in split order: even modes, then odd modes
@@ -320,6 +340,7 @@ static void free_all(Ctx* c) {
   for (int j = 0; j < kMaxOrder; ++j) { f(c->eta[j]); f(c->fN[j]); f(c->Fq[j]); }
   f(c->r); f(c->delta); f(c->delta2); f(c->dinc); f(c->t1); f(c->t2); f(c->xh); f(c->xl); f(c->yh); f(c->yl);
   f(c->Q); f(c->Qt); f(c->inv_den); f(c->lam_f); f(c->Bfh); f(c->Bfl); f(c->Bbh); f(c->Bbl);
+  f(c->xs); f(c->pmax);
   f(c->tri); f(c->sched_dev); f(c->p_dev); f(c->err_dev);
   if (c->pinned) cudaFreeHost(c->pinned);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -375,9 +396,13 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
       RIDC_CUDA(dev_malloc((void**)&c->xl, hb));
       RIDC_CUDA(dev_malloc((void**)&c->yh, hb));
       RIDC_CUDA(dev_malloc((void**)&c->yl, hb));
+      if (c->prec == RIDC_MIXED_FP16X3) {
+        RIDC_CUDA(dev_malloc((void**)&c->xs, (size_t)order * c->plane * sizeof(float)));
+        RIDC_CUDA(dev_malloc((void**)&c->pmax, (size_t)kMaxPasses * kMaxPlanes * sizeof(unsigned)));
+      }
     }
     RIDC_TRY(build_tables_2d(c));
-    if (c->prec == RIDC_MIXED_BF16X3) {
+    if (is_mixed(c->prec)) {
       const long rows = (long)order * c->S * n, H = n / 2;
       c->grows = rows;
       RIDC_TRY(make_tensor_map(&c->tm_Xh, c->xh, 2 * rows, H, 128));
@@ -405,7 +430,7 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
   if (!(dt > 0.0) || !std::isfinite(dt)) return RIDC_ERR_ARG;
   if (pr->restart_every < 0) return RIDC_ERR_ARG;
   if (pr->kind < 0 || pr->kind > 4) return RIDC_ERR_ARG;
-  if (pr->precision != RIDC_FP64 && pr->precision != RIDC_MIXED_BF16X3) return RIDC_ERR_ARG;
+  if (pr->precision != RIDC_FP64 && !is_mixed(pr->precision)) return RIDC_ERR_ARG;
   if (pr->n_refine < 0 || pr->n_refine > 4) return RIDC_ERR_ARG;
   const int S = (pr->kind == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
   for (int s = 0; s < S; ++s)
@@ -419,7 +444,7 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
       return RIDC_ERR_UNSUPPORTED;
   } else {
     if (g->dim != 2 || g->n < 4) return RIDC_ERR_ARG;
-    if (pr->precision == RIDC_MIXED_BF16X3 && ((g->n % 256) != 0 || g->n > 4096))
+    if (is_mixed(pr->precision) && ((g->n % 256) != 0 || g->n > 4096))
       return RIDC_ERR_UNSUPPORTED;
     if (g->n > 16384) return RIDC_ERR_UNSUPPORTED;
   }
@@ -541,23 +566,26 @@ static int solve_group_mixed(Ctx* c, int p0, int np, bool rhs_split_done, const 
   const double* tot = nullptr;
   for (int pass = 0; pass <= c->n_refine; ++pass) {
     if (pass == 0) {
-      if (!rhs_split_done) RIDC_TRY(launch_residual(c, p0, np, nullptr, nullptr, nullptr));
+      if (!rhs_split_done) {
+        if (c->prec == RIDC_MIXED_FP16X3) RIDC_TRY(reset_plane_max(c));
+        RIDC_TRY(launch_residual(c, p0, np, nullptr, nullptr, nullptr, 0));
+      }
     } else {
       double* dst = (tot == c->delta) ? c->delta2 : c->delta;
-      RIDC_TRY(launch_residual(c, p0, np, tot, c->dinc, dst));
+      RIDC_TRY(launch_residual(c, p0, np, tot, c->dinc, dst, pass));
       tot = dst;
     }
     // x forward of the operand split along both axes (right-hand side or residual kernel)
     // -> Y, rows kx per y parity;  y forward, divided by the denominators -> W
     RIDC_TRY(launch_gemm_sym(c, &c->tm_Xh, &c->tm_Xl, &c->tm_Bfh, &c->tm_Bfl, p0, np,
-                             SYM_FWD_SPLIT, c->yh, c->yl, nullptr));
+                             SYM_FWD_SPLIT, c->yh, c->yl, nullptr, pass));
     RIDC_TRY(launch_gemm_sym(c, &c->tm_Yh, &c->tm_Yl, &c->tm_Bfh, &c->tm_Bfl, p0, np,
-                             SYM_FWD_DEN, c->xh, c->xl, nullptr));
+                             SYM_FWD_DEN, c->xh, c->xl, nullptr, pass));
     // x inverse -> Z;  y inverse -> FP32 increment
     RIDC_TRY(launch_gemm_sym(c, &c->tm_Wh, &c->tm_Wl, &c->tm_Bbh, &c->tm_Bbl, p0, np,
-                             SYM_BWD_SPLIT, c->yh, c->yl, nullptr));
+                             SYM_BWD_SPLIT, c->yh, c->yl, nullptr, pass));
     RIDC_TRY(launch_gemm_sym(c, &c->tm_Zh, &c->tm_Zl, &c->tm_Bbh, &c->tm_Bbl, p0, np,
-                             SYM_BWD_F32, nullptr, nullptr, c->dinc));
+                             SYM_BWD_F32, nullptr, nullptr, c->dinc, pass));
   }
   *total = tot;
   return RIDC_OK;
@@ -680,9 +708,14 @@ static int step_2d_launch(Ctx* c, unsigned mask) {
   ra.r = c->r;
   ra.r_hi = (c->prec == RIDC_MIXED_BF16X3) ? c->xh : nullptr;
   ra.r_lo = (c->prec == RIDC_MIXED_BF16X3) ? c->xl : nullptr;
+  const bool f16 = c->prec == RIDC_MIXED_FP16X3;
+  ra.r_stage = f16 ? c->xs : nullptr;
+  ra.pmax = f16 ? c->pmax : nullptr;   // pass 0
   ra.n = c->n;
   fa.nlev = na;
+  if (f16) RIDC_TRY(reset_plane_max(c));
   RIDC_TRY(launch_rhs(c, ra));
+  if (f16) RIDC_TRY(launch_split_f16(c, 0, na * c->S, 0));
   DeltaParts parts;
   RIDC_TRY(solve_planes_dev(c, na * c->S, true, &parts));
   for (int q = 0; q < na; ++q) {
@@ -999,7 +1032,7 @@ extern "C" int ridc_quadrature_weights(int order, double* out, size_t cap) {
 extern "C" int ridc_debug_stall_next_gemm(ridc_handle h) {
   Ctx* c = ctx_of(h);
   if (!c) return RIDC_ERR_ARG;
-  if (c->dim != 2 || c->prec != RIDC_MIXED_BF16X3) return RIDC_ERR_UNSUPPORTED;
+  if (c->dim != 2 || !is_mixed(c->prec)) return RIDC_ERR_UNSUPPORTED;
   c->stall_next_gemm = 1;
   return RIDC_OK;
 }

@@ -15,12 +15,16 @@
 // of v[gx][gy][y'][x'] = (v[y'][x'] +- v[y'][N-1-x']) +- (v[N-1-y'][x'] +- v[N-1-y'][N-1-x']).
 // The first transform then writes each result row straight into the second's operand.
 //
-// Operands are BF16 hi/lo splits, C ~= Ah Bh + Ah Bl + Al Bh with FP32 accumulation in TMEM.
+// Operands are BF16 hi/lo splits, C ~= Ah Bh + Ah Bl + Al Bh with FP32 accumulation in TMEM,
+// or FP16 hi/lo splits of scaled values (the FP16 form): tables times 2^qexp, each plane of the
+// first operand times its own 2^k. Every epilogue then multiplies by 2^-qexp, and the last
+// also by 2^-k; the intermediates stay in the scaled units, which keeps them inside FP16's
+// range (at most N 2^3 <= 2^15) and above its subnormals.
 // Every product contracts the contiguous axis of its A rows and stores transposed per plane.
-//   SYM_FWD_SPLIT forward, BF16 hi/lo store into [plane][gy][kx][y'] (first transform, x)
-//   SYM_FWD_DEN   forward, times 1/den, BF16 hi/lo store     (second transform, y)
-//   SYM_BWD_SPLIT inverse with the E +- O butterfly, BF16    (third transform, x)
-//   SYM_BWD_F32   inverse with the E +- O butterfly, FP32    (fourth transform, y: the increment)
+//   SYM_FWD_SPLIT forward, hi/lo store into [plane][gy][kx][y'] (first transform, x)
+//   SYM_FWD_DEN   forward, times 1/den, hi/lo store     (second transform, y)
+//   SYM_BWD_SPLIT inverse with the E +- O butterfly, hi/lo (third transform, x)
+//   SYM_BWD_F32   inverse with the E +- O butterfly, FP32  (fourth transform, y: the increment)
 //
 // Persistent: one CTA per SM over a static tile list; a TMA producer thread and an MMA thread
 // run ahead over a ring of stages (Ah, Al, Bh, Bl tiles, K = 64, 128B swizzle): forward
@@ -50,8 +54,11 @@ struct SyCfg {
   static constexpr int STAGE = 2 * SY_TILE + 2 * BTILE;
   static constexpr int STAGES = (BN == 256) ? 2 : 3;
   static constexpr int NSEG = FWD ? 1 : 2;
+  // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5), A and B formats (bits
+  // 7-9 and 10-12: 1 = BF16, 0 = FP16; both operands always share one), N / 8, M / 16
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(SY_BM >> 4) << 24);
+  static constexpr uint32_t IDESC_F16 = IDESC & ~((7u << 7) | (7u << 10));
 };
 // dynamic shared memory: stages + barriers + alignment slack, plus the eigenvalues in the
 // denominator mode only
@@ -155,10 +162,18 @@ __device__ __forceinline__ void s_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void s_split(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, size_t idx) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  hi[idx] = h;
-  lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+// v = hi + lo to about 16 (BF16) or 22 (FP16) significant bits; v - hi is exact in FP32
+__device__ __forceinline__ void s_split(float v, __nv_bfloat16* hi, __nv_bfloat16* lo, size_t idx,
+                                        bool f16) {
+  if (f16) {
+    const __half h = __float2half_rn(v);
+    reinterpret_cast<__half*>(hi)[idx] = h;
+    reinterpret_cast<__half*>(lo)[idx] = __float2half_rn(v - __half2float(h));
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[idx] = h;
+    lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
 }
 
 struct SymArgs {
@@ -170,6 +185,10 @@ struct SymArgs {
   float dtnu[kMaxSpecies];
   int* err;
   int stall;            // test hook: CTA 0 leaves its first stage unloaded
+  int f16;              // FP16 form: FP16 operands and the power-of-two scales below
+  float tscale;         // 2^-qexp (1 for BF16)
+  const unsigned* pmax; // FP16 form: per-plane maxima of this solve pass (plane scales)
+  int k0;               // FP16 form: target exponent of the plane scales
 };
 
 // tile -> (A row base, B row base, output plane-row base, column base, group)
@@ -199,7 +218,9 @@ __device__ __forceinline__ SymTile sym_tile(const SymArgs& a, int t, bool fwd, i
   return T;
 }
 
-template <bool FWD, int BN>
+// F16: the FP16 form (FP16 operands, power-of-two scales in the epilogues), instantiated
+// apart so the BF16 code carries none of it
+template <bool FWD, int BN, bool F16>
 __global__ void __launch_bounds__(SY_THREADS, 1)
     gemm_sym_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                     const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
@@ -285,6 +306,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
       s_wait(full((int)(q % SY_STAGES)), (uint32_t)((q / SY_STAGES) & 1), a.err);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
+    constexpr uint32_t idesc = F16 ? Cfg::IDESC_F16 : Cfg::IDESC;
     long consumed = 0;
     int local = 0;
     bool ok = true;
@@ -308,9 +330,9 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < SY_BK / 16; ++kk) {
             const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-            s_mma(acc, ah + adv, bh + adv, Cfg::IDESC, (kb | kk) != 0);
-            s_mma(acc, ah + adv, bl + adv, Cfg::IDESC, 1);
-            s_mma(acc, al + adv, bh + adv, Cfg::IDESC, 1);
+            s_mma(acc, ah + adv, bh + adv, idesc, (kb | kk) != 0);
+            s_mma(acc, ah + adv, bl + adv, idesc, 1);
+            s_mma(acc, al + adv, bh + adv, idesc, 1);
           }
           s_commit(empty(s));
         }
@@ -353,15 +375,21 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
             const int m = cbase + c + jj;
             float val = __uint_as_float(v[jj]);
             if (a.mode == SYM_FWD_SPLIT) {
-              s_split(val, a.oh, a.ol, (sbase + m) * a.H + yp);
+              s_split(F16 ? val * a.tscale : val, a.oh, a.ol, (sbase + m) * a.H + yp, F16);
             } else {
-              // the split keeps ~16 bits: a 2-ulp fast division is ample
-              val = __fdividef(val, fmaf(-dtnu, __shfl_sync(0xffffffffu, lam_lane, jj), den_r));
-              s_split(val, a.oh, a.ol, (pbase + m) * n + rl);
+              const float den = fmaf(-dtnu, __shfl_sync(0xffffffffu, lam_lane, jj), den_r);
+              // a BF16 split keeps ~16 bits: a 2-ulp fast division is ample; an FP16 split
+              // keeps ~22, so it takes the correctly rounded quotient
+              val = F16 ? __fdiv_rn(val * a.tscale, den) : __fdividef(val, den);
+              s_split(val, a.oh, a.ol, (pbase + m) * n + rl, F16);
             }
           }
         }
       } else {
+        // the last transform also removes the plane's own scale
+        const float mult = !F16 ? 1.0f
+                           : (a.mode == SYM_BWD_F32)
+                               ? a.tscale * pow2f(-f16_plane_exp(a.pmax[plane], a.k0)) : a.tscale;
         for (int c = 0; c < BN; c += 16) {
           uint32_t e[16], o[16];
           s_ld16(acc + (uint32_t)c, e);
@@ -372,12 +400,14 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
             const int x = T.c0 + c + jj;
             const float ev = __uint_as_float(e[jj]), ov = __uint_as_float(o[jj]);
             const size_t i0 = (pbase + x) * n + rl, i1 = (pbase + (n - 1 - x)) * n + rl;
+            const float sum = F16 ? (ev + ov) * mult : ev + ov;
+            const float dif = F16 ? (ev - ov) * mult : ev - ov;
             if (a.mode == SYM_BWD_F32) {
-              a.o32[i0] = ev + ov;
-              a.o32[i1] = ev - ov;
+              a.o32[i0] = sum;
+              a.o32[i1] = dif;
             } else {
-              s_split(ev + ov, a.oh, a.ol, i0);
-              s_split(ev - ov, a.oh, a.ol, i1);
+              s_split(sum, a.oh, a.ol, i0, F16);
+              s_split(dif, a.oh, a.ol, i1, F16);
             }
           }
         }
@@ -423,21 +453,21 @@ int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int
 
 int gemm_sym_fwd_bn(int n) { return (n / 2) % 256 == 0 ? 256 : 128; }
 
-template <bool FWD, int BN>
+template <bool FWD, int BN, bool F16>
 static int launch_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                       const CUtensorMap* bl, const SymArgs& a, int sms) {
   static std::atomic<unsigned long long> attr_done{0};
-  RIDC_TRY(raise_smem_limit_once(gemm_sym_kernel<FWD, BN>, SY_SMEM_MAX, &attr_done));
+  RIDC_TRY(raise_smem_limit_once(gemm_sym_kernel<FWD, BN, F16>, SY_SMEM_MAX, &attr_done));
   const int ntiles = (FWD ? 2 : 1) * (a.rows / SY_BM) * (a.H / BN);
   dim3 grid(ntiles < sms ? ntiles : sms);
   const int smem = sy_smem_base<FWD, BN>() + (a.mode == SYM_FWD_DEN ? a.n * 4 : 0);
-  gemm_sym_kernel<FWD, BN><<<grid, SY_THREADS, smem, c->stream>>>(*ah, *al, *bh, *bl, a);
+  gemm_sym_kernel<FWD, BN, F16><<<grid, SY_THREADS, smem, c->stream>>>(*ah, *al, *bh, *bl, a);
   return cuda_status(cudaGetLastError());
 }
 
 int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                     const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
-                    __nv_bfloat16* ol, float* o32) {
+                    __nv_bfloat16* ol, float* o32, int pass) {
   const int n = c->n;
   if (n % 256 != 0 || n > SY_MAXN) return RIDC_ERR_UNSUPPORTED;
   const int sms = current_sm_count();
@@ -456,13 +486,24 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
   a.err = c->err_dev;
   a.stall = c->stall_next_gemm;
   c->stall_next_gemm = 0;
+  a.f16 = c->prec == RIDC_MIXED_FP16X3;
+  a.tscale = a.f16 ? pow2f(-c->qexp) : 1.0f;
+  a.pmax = a.f16 ? c->pmax + (size_t)pass * kMaxPlanes : nullptr;
+  a.k0 = c->k0;
   const bool fwd = mode == SYM_FWD_SPLIT || mode == SYM_FWD_DEN;
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_TC, &e0);
   int rc;
-  if (!fwd) rc = launch_sym<false, 128>(c, ah, al, bh, bl, a, sms);
-  else if (gemm_sym_fwd_bn(n) == 256) rc = launch_sym<true, 256>(c, ah, al, bh, bl, a, sms);
-  else rc = launch_sym<true, 128>(c, ah, al, bh, bl, a, sms);
+  const bool wide = gemm_sym_fwd_bn(n) == 256;
+  if (a.f16) {
+    if (!fwd) rc = launch_sym<false, 128, true>(c, ah, al, bh, bl, a, sms);
+    else if (wide) rc = launch_sym<true, 256, true>(c, ah, al, bh, bl, a, sms);
+    else rc = launch_sym<true, 128, true>(c, ah, al, bh, bl, a, sms);
+  } else {
+    if (!fwd) rc = launch_sym<false, 128, false>(c, ah, al, bh, bl, a, sms);
+    else if (wide) rc = launch_sym<true, 256, false>(c, ah, al, bh, bl, a, sms);
+    else rc = launch_sym<true, 128, false>(c, ah, al, bh, bl, a, sms);
+  }
   prof_end(c, RIDC_KERNEL_GEMM_TC, e0);
   return rc;
 }

@@ -1,11 +1,13 @@
-// 2D device kernels of one pipeline step, all FP64 except the BF16 split outputs:
+// 2D device kernels of one pipeline step, all FP64 except the split outputs:
 //   rhs_kernel       right-hand side of every advancing level in delta form (eq. (pred),
 //                    eq. (corr)), with the Lagrange quadrature of Section III-C; elementwise.
 //   finalize_kernel  eta_{n+1} = base + delta, then f^N(eta) and f = f^N + D eta of the new
 //                    state (5-point stencil from a shared-memory tile with ghost cells).
 //   residual_kernel  refinement residual r - (I - dt nu L) delta of the mixed solve, parity-
 //                    split along both axes and split into BF16 hi/lo for the next
-//                    tensor-core pass.
+//                    tensor-core pass (FP16 form: staged in FP32 with the plane maxima).
+//   split_f16_kernel FP16 form: scales each staged plane by its power of two and splits it
+//                    into FP16 hi/lo.
 //   gemm_f64_kernel  FP64 fast-diagonalisation GEMM (DFMA; GB300's DMMA is slower than DFMA),
 //                    parity-split for even n (gemm_f64_split_kernel).
 #include "ridc_internal.h"
@@ -86,7 +88,27 @@ __device__ __forceinline__ void store_split2(__nv_bfloat16* hi, __nv_bfloat16* l
   *reinterpret_cast<__nv_bfloat162*>(lo + idx) = lv;
 }
 
-template <int NODES>
+// FP16 form: v0, v1 staged in FP32 (8-byte aligned: idx is even)
+__device__ __forceinline__ void store_stage2(float* st, long idx, float v0, float v1) {
+  *reinterpret_cast<float2*>(st + idx) = make_float2(v0, v1);
+}
+
+// running maximum of |v| as FP32 bits (non-negative floats order like their bit patterns;
+// a NaN's bits exceed every finite value's, so a NaN plane keeps a non-finite maximum)
+__device__ __forceinline__ unsigned abs_bits_max(unsigned m, float v) {
+  const unsigned b = __float_as_uint(v) & 0x7FFFFFFFu;
+  return b > m ? b : m;
+}
+
+// warp-wide maximum, then one atomic per warp (every lane of the warp active)
+__device__ __forceinline__ void flush_plane_max(unsigned* pmax, unsigned m) {
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(pmax, m);
+}
+
+// STAGE: the FP16 form (FP32 staging and plane maxima); a separate instantiation keeps the
+// FP64 and BF16 code free of its branches and registers
+template <int NODES, bool STAGE>
 __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, long out_off) {
   const double2* Fn[NODES];
   double w[NODES];
@@ -96,7 +118,7 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
     w[k] = L.w[k];
   }
   double2* r2 = (double2*)(a.r + out_off);
-  if (!a.r_hi) {
+  if (!STAGE && !a.r_hi) {
     const long half = a.plane >> 1;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < half;
          i += (long)gridDim.x * blockDim.x)
@@ -110,6 +132,10 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
   const int n = a.n, q4 = n / 4, H = n / 2;
   const long nn = (long)n * n, cells = a.plane / 8;
   const long plane0 = out_off / nn;   // first plane of this level in the stacked operand
+  // FP16 form: running max of the staged values of plane `mp` (cells per plane, n^2 / 8, and
+  // the grid stride are multiples of 32, so a warp's lanes always share one plane)
+  unsigned mx = 0;
+  long mp = -1;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < cells;
        e += (long)gridDim.x * blockDim.x) {
     const long sp = e / ((long)H * q4), rem = e - sp * (long)H * q4;
@@ -129,6 +155,11 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
       v[side][3] = f64_to_f32(vR.x);   // mirror of 2q+1
     }
     const long p = plane0 + sp;
+    if (STAGE && p != mp) {
+      if (mp >= 0) flush_plane_max(a.pmax + mp, mx);
+      mp = p;
+      mx = 0;
+    }
 #pragma unroll
     for (int gx = 0; gx < 2; ++gx) {
       // x butterfly of each row, then y butterfly
@@ -136,40 +167,52 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
       const float a0 = v[0][0] + s * v[0][2], a1 = v[0][1] + s * v[0][3];
       const float b0 = v[1][0] + s * v[1][2], b1 = v[1][1] + s * v[1][3];
       const long base = ((p * 2 + gx) * n + y) * H + 2 * q;   // gy = 0 block; gy = 1 is H rows on
-      store_split2(a.r_hi, a.r_lo, base, a0 + b0, a1 + b1);
-      store_split2(a.r_hi, a.r_lo, base + (long)H * H, a0 - b0, a1 - b1);
+      if (STAGE) {
+        store_stage2(a.r_stage, base, a0 + b0, a1 + b1);
+        store_stage2(a.r_stage, base + (long)H * H, a0 - b0, a1 - b1);
+        mx = abs_bits_max(abs_bits_max(mx, a0 + b0), a1 + b1);
+        mx = abs_bits_max(abs_bits_max(mx, a0 - b0), a1 - b1);
+      } else {
+        store_split2(a.r_hi, a.r_lo, base, a0 + b0, a1 + b1);
+        store_split2(a.r_hi, a.r_lo, base + (long)H * H, a0 - b0, a1 - b1);
+      }
     }
   }
+  if (STAGE && mp >= 0) flush_plane_max(a.pmax + mp, mx);
 }
 
+template <bool STAGE>
 __global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArgs a) {
   const RhsLevel& L = a.lv[blockIdx.y];
   const long out_off = (long)blockIdx.y * a.plane;
   switch (L.nnodes) {
-    case 1: rhs_level<1>(a, L, out_off); break;
-    case 2: rhs_level<2>(a, L, out_off); break;
-    case 3: rhs_level<3>(a, L, out_off); break;
-    case 4: rhs_level<4>(a, L, out_off); break;
-    case 5: rhs_level<5>(a, L, out_off); break;
-    case 6: rhs_level<6>(a, L, out_off); break;
-    case 7: rhs_level<7>(a, L, out_off); break;
-    case 8: rhs_level<8>(a, L, out_off); break;
-    case 9: rhs_level<9>(a, L, out_off); break;
-    case 10: rhs_level<10>(a, L, out_off); break;
-    case 11: rhs_level<11>(a, L, out_off); break;
-    default: rhs_level<12>(a, L, out_off); break;
+    case 1: rhs_level<1, STAGE>(a, L, out_off); break;
+    case 2: rhs_level<2, STAGE>(a, L, out_off); break;
+    case 3: rhs_level<3, STAGE>(a, L, out_off); break;
+    case 4: rhs_level<4, STAGE>(a, L, out_off); break;
+    case 5: rhs_level<5, STAGE>(a, L, out_off); break;
+    case 6: rhs_level<6, STAGE>(a, L, out_off); break;
+    case 7: rhs_level<7, STAGE>(a, L, out_off); break;
+    case 8: rhs_level<8, STAGE>(a, L, out_off); break;
+    case 9: rhs_level<9, STAGE>(a, L, out_off); break;
+    case 10: rhs_level<10, STAGE>(a, L, out_off); break;
+    case 11: rhs_level<11, STAGE>(a, L, out_off); break;
+    default: rhs_level<12, STAGE>(a, L, out_off); break;
   }
 }
 
 int launch_rhs(Ctx* c, const RhsArgs& a) {
-  const long half = a.r_hi ? a.plane / 8 : a.plane / 2;
+  const long half = (a.r_hi || a.r_stage) ? a.plane / 8 : a.plane / 2;
   long bx = (half + 255) / 256;
   const long cap = 148L * 16 / (a.nlev > 0 ? a.nlev : 1) + 1;
   if (bx > cap * 8) bx = cap * 8;
   dim3 grid((unsigned)bx, a.nlev);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_RHS, &e0);
-  rhs_kernel<<<grid, 256, 0, c->stream>>>(a);
+  if (a.r_stage)
+    rhs_kernel<true><<<grid, 256, 0, c->stream>>>(a);
+  else
+    rhs_kernel<false><<<grid, 256, 0, c->stream>>>(a);
   prof_end(c, RIDC_KERNEL_RHS, e0);
   return cuda_status(cudaGetLastError());
 }
@@ -270,7 +313,8 @@ int launch_finalize(Ctx* c, const FinArgs& a) {
 // ---------------------------------------------------------------------------------------------
 // refinement residual of the mixed solve:
 //   d = dprev + inc  (written to dout),   r' = r - (I - c_s L) d = r - (1 + 4 c_s) d + c_s (N+S+W+E)
-// with c_s = dt nu_s / h^2, then r' split to BF16 hi/lo. Without dprev and inc: r' = r.
+// with c_s = dt nu_s / h^2, then r' split to BF16 hi/lo (FP16 form: staged in FP32, with the
+// plane maxima). Without dprev and inc: r' = r.
 // ---------------------------------------------------------------------------------------------
 struct ResArgs {
   const double* r;
@@ -279,6 +323,8 @@ struct ResArgs {
   double* dout;
   __nv_bfloat16* hi;        // parity-split operand [plane][gx][gy][y'][x'], x', y' < n/2
   __nv_bfloat16* lo;
+  float* stage;             // FP16 form: the same values in FP32 (else nullptr)
+  unsigned* pmax;           // FP16 form: per-plane maxima of this solve pass
   int n, S, plane0;
   double c[kMaxSpecies];    // c_s
   double c1[kMaxSpecies];   // -(1 + 4 c_s)
@@ -328,6 +374,7 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
   __syncthreads();
   const int H = n / 2;
   const int xp = blockIdx.x * TX + threadIdx.x;   // x' < n/2; its mirror is column 31 - tx
+  unsigned vmax = 0;
 #pragma unroll
   for (int rr = 0; rr < RPT; ++rr) {
     const int ly = threadIdx.y + rr * BY, yp = blockIdx.y * TY + ly;   // y' < n/2
@@ -341,6 +388,12 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
       const long i0 = ((long)(p * 2 + gxp) * n + yp) * H + xp;   // gy = 0; gy = 1 is H rows on
       const long i1 = i0 + (long)H * H;
       const float vp = top + bot, vm = top - bot;
+      if (a.stage) {
+        a.stage[i0] = vp;
+        a.stage[i1] = vm;
+        vmax = abs_bits_max(abs_bits_max(vmax, vp), vm);
+        continue;
+      }
       __nv_bfloat16 h = __float2bfloat16_rn(vp);
       a.hi[i0] = h;
       a.lo[i0] = __float2bfloat16_rn(vp - __bfloat162float(h));
@@ -349,10 +402,11 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
       a.lo[i1] = __float2bfloat16_rn(vm - __bfloat162float(h));
     }
   }
+  if (a.stage) flush_plane_max(a.pmax + p, vmax);   // every thread of the block gets here
 }
 
 int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const float* inc,
-                    double* dout) {
+                    double* dout, int pass) {
   ResArgs a{};
   a.plane0 = plane0;
   a.r = c->r;
@@ -361,6 +415,11 @@ int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const 
   a.dout = dout;
   a.hi = c->xh;
   a.lo = c->xl;
+  if (c->prec == RIDC_MIXED_FP16X3) {
+    if (pass < 0 || pass >= kMaxPasses) return RIDC_ERR_ARG;
+    a.stage = c->xs;
+    a.pmax = c->pmax + (size_t)pass * kMaxPlanes;
+  }
   a.n = c->n;
   a.S = c->S;
   for (int s = 0; s < c->S; ++s) {
@@ -376,7 +435,64 @@ int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const 
   else
     residual_kernel<false><<<grid, dim3(TX, BY), 0, c->stream>>>(a);
   prof_end(c, RIDC_KERNEL_RESIDUAL, e0);
+  RIDC_TRY(cuda_status(cudaGetLastError()));
+  return (c->prec == RIDC_MIXED_FP16X3) ? launch_split_f16(c, plane0, nplanes, pass) : RIDC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP16 form: v 2^k -> FP16 hi + lo for every staged value of a plane, k from the plane's
+// maximum (max|v| 2^k in [2^(K0-1), 2^K0)); scaling by a power of two is exact.
+// blockIdx.y = plane.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) split_f16_kernel(const float* __restrict__ st,
+                                                        __half* __restrict__ hi,
+                                                        __half* __restrict__ lo,
+                                                        const unsigned* __restrict__ pmax,
+                                                        int plane0, long per_plane, int k0) {
+  const int p = plane0 + blockIdx.y;
+  const float sc = pow2f(f16_plane_exp(pmax[p], k0));
+  const long off = (long)p * per_plane;
+  const float4* s4 = reinterpret_cast<const float4*>(st + off);
+  uint2* h4 = reinterpret_cast<uint2*>(hi + off);
+  uint2* l4 = reinterpret_cast<uint2*>(lo + off);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < per_plane / 4;
+       i += (long)gridDim.x * blockDim.x) {
+    const float4 v = s4[i];
+    const float f[4] = {v.x * sc, v.y * sc, v.z * sc, v.w * sc};
+    __half h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      h[k] = __float2half_rn(f[k]);
+      l[k] = __float2half_rn(f[k] - __half2float(h[k]));
+    }
+    uint2 ph, pl;
+    ph.x = (unsigned)__half_as_ushort(h[0]) | ((unsigned)__half_as_ushort(h[1]) << 16);
+    ph.y = (unsigned)__half_as_ushort(h[2]) | ((unsigned)__half_as_ushort(h[3]) << 16);
+    pl.x = (unsigned)__half_as_ushort(l[0]) | ((unsigned)__half_as_ushort(l[1]) << 16);
+    pl.y = (unsigned)__half_as_ushort(l[2]) | ((unsigned)__half_as_ushort(l[3]) << 16);
+    h4[i] = ph;
+    l4[i] = pl;
+  }
+}
+
+int launch_split_f16(Ctx* c, int plane0, int nplanes, int pass) {
+  if (pass < 0 || pass >= kMaxPasses || !c->xs || !c->pmax) return RIDC_ERR_ARG;
+  const long per_plane = (long)c->n * c->n;   // n is a multiple of 256: per_plane % 4 == 0
+  long bx = (per_plane / 4 + 255) / 256;
+  const long cap = 152L * 8 / nplanes + 1;
+  if (bx > cap) bx = cap;
+  cudaEvent_t e0;
+  prof_begin(c, RIDC_KERNEL_SPLIT, &e0);
+  split_f16_kernel<<<dim3((unsigned)bx, nplanes), 256, 0, c->stream>>>(
+      c->xs, reinterpret_cast<__half*>(c->xh), reinterpret_cast<__half*>(c->xl),
+      c->pmax + (size_t)pass * kMaxPlanes, plane0, per_plane, c->k0);
+  prof_end(c, RIDC_KERNEL_SPLIT, e0);
   return cuda_status(cudaGetLastError());
+}
+
+int reset_plane_max(Ctx* c) {
+  return cuda_status(
+      cudaMemsetAsync(c->pmax, 0, (size_t)kMaxPasses * kMaxPlanes * sizeof(unsigned), c->stream));
 }
 
 // out = d64 + d32 (either part may be absent)

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda.h>
 #include <atomic>
 #include <cstddef>
@@ -15,6 +16,37 @@ namespace ridc {
 
 constexpr int kMaxOrder = 12;
 constexpr int kMaxSpecies = 2;
+constexpr int kMaxPasses = 5;       // solve passes of the mixed forms: 1 + up to 4 refinements
+constexpr int kMaxPlanes = kMaxOrder * kMaxSpecies;
+// FP16 form: an operand plane is scaled by 2^k with max|v| 2^k in [2^(K0-1), 2^K0),
+// K0 = 15 - ceil(log2 N), so every intermediate of the transform, at most N 2^K0 <= 2^15,
+// stays finite in FP16 while small values keep clear of its subnormals
+inline int f16_k0(int n) {
+  int l = 0;
+  while ((1L << l) < (long)n) ++l;
+  return 15 - l;
+}
+
+inline bool is_mixed(int prec) { return prec == RIDC_MIXED_BF16X3 || prec == RIDC_MIXED_FP16X3; }
+
+// exponent k of the power-of-two scale of an FP16-form plane from the FP32 bits of its
+// maximum magnitude: max 2^k in [2^(K0-1), 2^K0). A zero, subnormal or non-finite maximum
+// gives k = 0 (zeros stay zeros; Inf and NaN pass through to the non-finite checks); k is
+// clamped to [-100, 100] so that 2^k and 2^-(k + table exponent) stay normal FP32 numbers.
+__host__ __device__ inline int f16_plane_exp(unsigned maxbits, int k0) {
+  const int e = (int)((maxbits >> 23) & 0xFF);
+  if (e == 0 || e == 255) return 0;
+  int k = k0 - 1 - (e - 127);
+  if (k > 100) k = 100;
+  if (k < -100) k = -100;
+  return k;
+}
+// 2^k as an FP32 number, |k| <= 126
+__host__ __device__ inline float pow2f(int k) {
+  union { unsigned u; float f; } v;
+  v.u = (unsigned)(127 + k) << 23;
+  return v.f;
+}
 
 // ---- launch descriptors ---------------------------------------------------------------
 
@@ -39,7 +71,9 @@ struct RhsArgs {
   double dt;
   double* r;              // [nlev*S][N][N]
   __nv_bfloat16* r_hi;    // split of r along both axes for the tensor-core solve (nullptr:
-  __nv_bfloat16* r_lo;    //   FP64), layout [plane][gx][gy][N/2][N/2]
+  __nv_bfloat16* r_lo;    //   FP64 and FP16 forms), layout [plane][gx][gy][N/2][N/2]
+  float* r_stage;         // FP16 form: the split values in FP32, same layout (else nullptr)
+  unsigned* pmax;         // FP16 form: per-plane max |staged value| (FP32 bits), pass 0
   int n;
 };
 
@@ -107,10 +141,19 @@ struct Ctx {
   float* dinc = nullptr;     // [P*S][N][N]  FP32 increment of the latest tensor-core pass
   double* t1 = nullptr;      // FP64 GEMM intermediates
   double* t2 = nullptr;
-  __nv_bfloat16* xh = nullptr;   // split operands, ping
+  // split operands, ping (xh/xl) and pong (yh/yl); 16-bit words holding BF16 values, or
+  // FP16 values in the FP16 form (the tensor maps only move 2-byte elements)
+  __nv_bfloat16* xh = nullptr;
   __nv_bfloat16* xl = nullptr;
-  __nv_bfloat16* yh = nullptr;   // pong
+  __nv_bfloat16* yh = nullptr;
   __nv_bfloat16* yl = nullptr;
+  // FP16 form: FP32 staging of the first operand ([P*S][gx][gy][N/2][N/2]), the per-plane
+  // maxima of every solve pass ([kMaxPasses][kMaxPlanes], FP32 bits, zeroed per solve) and
+  // the exponent of the eigenvector tables' scale 2^qexp
+  float* xs = nullptr;
+  unsigned* pmax = nullptr;
+  int qexp = 0;
+  int k0 = 0;                // f16_k0(n)
 
   // fast-diagonalisation tables (2D): Q[x][k] orthonormal eigenvectors of the 1D Laplacian
   double* Q = nullptr;       // [N][N]   Q, its columns in split order when N is even
@@ -118,7 +161,7 @@ struct Ctx {
   double* inv_den = nullptr; // [S][N][N] 1 / (1 - dt nu_s (lam_ky + lam_kx)), FP64 path (split
                              //           order for ky and kx when N is even)
   float* lam_f = nullptr;    // [N] eigenvalues in split order (even modes, then odd), FP32
-  // parity-split eigenvector tables, BF16 hi/lo, each [N][N/2]:
+  // parity-split eigenvector tables, BF16 (or scaled FP16) hi/lo, each [N][N/2]:
   //   Bf = [Qe^T; Qo^T] (forward products), Bb = [Qe; Qo] (inverse products)
   __nv_bfloat16 *Bfh = nullptr, *Bfl = nullptr, *Bbh = nullptr, *Bbl = nullptr;
   long grows = 0;            // P*S*N: rows of an inverse operand (half those of a forward one)
@@ -223,20 +266,27 @@ unsigned plan_step(int P, const long* p, long target_top);
 // ---- kernel launchers (each returns RIDC_OK or an error code) -------------------------------------
 int launch_rhs(Ctx* c, const RhsArgs& a);
 int launch_finalize(Ctx* c, const FinArgs& a);
-// r' = r - (I - dt nu_s L)(dprev + inc), split to BF16 hi/lo into xh/xl; the new total
-// dprev + inc is written to dout. dprev, inc may be nullptr (absent); with both absent the
-// kernel only splits r.
+// r' = r - (I - dt nu_s L)(dprev + inc), split to BF16 hi/lo into xh/xl (FP16 form: staged
+// in FP32 with the per-plane maxima of solve pass `pass`); the new total dprev + inc is
+// written to dout. dprev, inc may be nullptr (absent); with both absent the kernel only
+// splits r.
 int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const float* inc,
-                    double* dout);
+                    double* dout, int pass);
+// FP16 form: zero the per-plane maxima of every pass (before a solve's first producer)
+int reset_plane_max(Ctx* c);
+// FP16 form: scale the staged operand planes [plane0, plane0 + nplanes) by their powers of
+// two and split them to FP16 hi/lo into xh/xl (maxima of solve pass `pass`)
+int launch_split_f16(Ctx* c, int plane0, int nplanes, int pass);
 // out = d64 + d32 elementwise over count values (either part may be nullptr)
 int launch_combine(Ctx* c, const double* d64, const float* d32, double* out, long count);
 // one transform of the FP64 fast diagonalisation: forward (contract with Q, B = Q^T rows) or
 // inverse (B = Q); for even n parity-split (tables in split order), otherwise plain
 int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi,
                     bool forward);
+// pass: the solve pass whose per-plane scales the FP16 form undoes in the last transform
 int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                     const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
-                    __nv_bfloat16* ol, float* o32);
+                    __nv_bfloat16* ol, float* o32, int pass);
 int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
 // column-tile width of the forward parity-split products for side n (the B box height)
 int gemm_sym_fwd_bn(int n);

@@ -176,7 +176,7 @@ def test_binding_tables_match_the_header():
     for name, val in B.PRECISIONS.items():
         assert enums["RIDC_" + name.upper()] == val, name
     ids = {"rhs": "RHS", "gemm_tc": "GEMM_TC", "gemm_f64": "GEMM_F64", "residual": "RESIDUAL",
-           "finalize": "FINALIZE", "ridc1d": "1D"}
+           "finalize": "FINALIZE", "ridc1d": "1D", "split_f16": "SPLIT"}
     for name, val in B.KERNELS.items():
         assert defines["RIDC_KERNEL_" + ids[name]] == val, name
     assert len(B.KERNELS) == defines["RIDC_KERNEL_COUNT"]
