@@ -368,7 +368,8 @@ def run_single(args):
         it.close()
         return statistics.median(times), launches
 
-    ms, launches = timed(w.order)
+    order = args.order or w.order
+    ms, launches = timed(order)
     # the paper's claim in one-GPU form: the whole RIDC-4 pipeline against plain FBE (one
     # level) on the same workload and step count
     fbe_ms = timed(1)[0] if w.dim == 1 else None
@@ -378,18 +379,18 @@ def run_single(args):
         # the oracle on the whole workload (restarted where the workload restarts)
         import oracle
         t0 = time.perf_counter()
-        oracle.ridc_restarted(oracle.from_workload(w), w.u0, w.dt, nt, w.order, w.restart_every)
+        oracle.ridc_restarted(oracle.from_workload(w), w.u0, w.dt, nt, order, w.restart_every)
         s = time.perf_counter() - t0
         cpu = {"value": cells / s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the whole workload ({s:.1f} s, numpy/scipy FP64, dense LU solves)"}
-    line = {"metric": f"RIDC-{w.order} cell-updates/s", "value": cells / (ms * 1e-3), "unit": UNIT,
+    line = {"metric": f"RIDC-{order} cell-updates/s", "value": cells / (ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "us_per_pipeline_step": 1e3 * ms / (nt + w.order * (w.order - 1) // 2),
+            "us_per_pipeline_step": 1e3 * ms / (nt + order * (order - 1) // 2),
             "higher_is_better": True,
             "dtype": "f64" if prec == "fp64" else f"f64+{prec[6:]}(fp32 acc)",
             "data": "synthetic", "gpu_launches": int(launches),
             "fbe_ms": fbe_ms, "ridc_over_fbe_time": (ms / fbe_ms) if fbe_ms else None,
-            "config": {"workload": args.workload, "grid": w.n, "order": w.order,
+            "config": {"workload": args.workload, "grid": w.n, "order": order,
                        "top_level_steps": nt, "full_steps": w.nsteps, "dt": w.dt,
                        "restart_every": w.restart_every,
                        "n_refine": None if prec == "fp64" else args.n_refine},
@@ -465,6 +466,8 @@ def main():
                     choices=["mixed_bf16x3", "mixed_fp16x3"],
                     help="split form of the accuracy_2048, adv_diff_4096 and "
                          "gray_scott_2048_mixed lines (the headline line is BF16x3)")
+    ap.add_argument("--order", type=int, default=None,
+                    help="RIDC order of the single-workload lines (default: the workload's)")
     ap.add_argument("--n-refine", type=int, default=NREF,
                     help="refinement passes of those lines (the headline line uses 2)")
     ap.add_argument("--check-every", type=int, default=100)

@@ -213,6 +213,27 @@ def test_dirichlet_4096_mixed_full_size_truncated():
     assert rel_l2(got, ref) <= 1e-8
 
 
+# ---------------------------------------------------------------- higher orders in 2D (Section
+# III-E: 8th and 12th order RIDC do not suffer from the Runge phenomenon in double precision)
+def test_gray_scott_order8_mixed_512_through_startup():
+    """RIDC-8 on 512^2 Gray-Scott in the mixed form: 16 planes per solve; start-up takes
+    36 steps, so 44 steps reach the steady pipeline. Every level against the oracle."""
+    w = inputs.gray_scott_2d(n=512, nsteps=44, order=8, seed=3, width=0.3)
+    _, levels, prog = _run(w, precision="mixed_bf16x3", n_refine=2)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 8, all_levels=True)
+    assert prog[-1] == 44
+    for j in range(8):
+        assert rel_l2(levels[j][0], ref[j]) <= 1e-8, j
+
+
+def test_dirichlet_order12_mixed_512_through_startup():
+    """RIDC-12 on 512^2 Dirichlet advection-diffusion in the mixed form (78 start-up steps)."""
+    w = inputs.adv_diff_2d(n=512, nsteps=90, order=12, kmax=8, nu=1e-3)
+    got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 12)
+    assert rel_l2(got, ref) <= 1e-8
+
+
 def test_profiling_samples_every_kth_step():
     need_cuda()
     w = inputs.gray_scott_2d(n=256, nsteps=10, seed=2)
