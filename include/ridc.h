@@ -312,6 +312,25 @@ int ridc_get_kernel_stats(ridc_handle h, int kernel, long* launches, double* tot
 /* Kernel launches issued so far by the handle (all kinds, counted on the host).            */
 long ridc_launch_count(ridc_handle h);
 
+/* ---- device memory ------------------------------------------------------------------------ */
+
+/* Route the library's device allocations through the caller's allocator (for example a
+ * framework's caching pool) instead of cudaMalloc / cudaFree.
+ *   alloc(bytes, device, ctx): a device pointer to at least `bytes` bytes on `device` (the
+ *     handle's device, current during the call), aligned to 256 bytes, or NULL when out of
+ *     memory. The call that needed the memory then returns RIDC_ERR_OOM and gives back what
+ *     it had allocated. A pointer that is not 256-byte aligned is handed back to free and
+ *     the call returns RIDC_ERR_CUDA.
+ *   free(ptr, bytes, device, ctx): takes back a pointer alloc returned, with its size. The
+ *     library synchronises the stream (or, with no stream, the device) that used the memory
+ *     before it calls free, so the memory is idle when it is returned.
+ * Both NULL: cudaMalloc / cudaFree again (the default). Process-wide. RIDC_ERR_ARG when only
+ * one of the two is given, or while any handle or batch exists (every buffer is freed by
+ * the allocator that made it). Host staging memory (pinned) is not affected.              */
+typedef void* (*ridc_alloc_fn)(size_t bytes, int device, void* ctx);
+typedef void (*ridc_free_fn)(void* ptr, size_t bytes, int device, void* ctx);
+int ridc_set_allocator(ridc_alloc_fn alloc, ridc_free_fn free_fn, void* ctx);
+
 /* ---- test hooks: failures made on purpose, for the error paths ---------------------------- */
 
 /* Make the k-th device allocation from now on (k >= 1) fail as if the device were out of

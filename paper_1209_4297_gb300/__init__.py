@@ -5,9 +5,9 @@ The integrator runs entirely in the CUDA kernels of libridc.so (built in-tree fo
 does not load the library; the first call does, and raises if the library is missing.
 """
 from .binding import (Batch, Integrator, RidcError, debug_fail_alloc, error_string, lib,
-                      quadrature_weights,
+                      quadrature_weights, set_allocator, use_torch_allocator,
                       schedule_plan, schedule_plan_from, LIB_PATH, KERNELS)
 
 __all__ = ["Batch", "Integrator", "RidcError", "debug_fail_alloc", "error_string", "lib",
-           "quadrature_weights",
+           "quadrature_weights", "set_allocator", "use_torch_allocator",
            "schedule_plan", "schedule_plan_from", "LIB_PATH", "KERNELS"]

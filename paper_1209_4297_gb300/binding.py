@@ -40,6 +40,11 @@ class Grid(ctypes.Structure):
     _fields_ = [("dim", c_int), ("n", c_int)]
 
 
+# allocator callbacks of ridc_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_int, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_int, c_void_p)
+
+
 _lib_handle = None
 
 
@@ -85,6 +90,7 @@ def lib() -> ctypes.CDLL:
         "ridc_batch_set_launch": (i, [vp, i]),
         "ridc_batch_graph_launches": (lg, [vp]),
         "ridc_batch_destroy": (None, [vp]),
+        "ridc_set_allocator": (i, [ALLOC_FN, FREE_FN, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -149,6 +155,54 @@ def schedule_plan_from(order: int, start, nsteps: int) -> np.ndarray:
 def debug_fail_alloc(k: int) -> None:
     """Test hook: the k-th device allocation from now on fails (0 disarms)."""
     _check(lib().ridc_debug_fail_alloc(k), "ridc_debug_fail_alloc")
+
+
+_allocator_refs = None   # the installed callbacks must outlive every call that uses them
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """Route the library's device allocations through Python callables:
+    alloc(nbytes, device) -> int device pointer (0 or None when out of memory) and
+    free(ptr, nbytes, device). Both None: back to cudaMalloc / cudaFree. Raises while an
+    Integrator or Batch exists."""
+    global _allocator_refs
+    if alloc is None and free is None:
+        _check(lib().ridc_set_allocator(ALLOC_FN(), FREE_FN(), None), "ridc_set_allocator")
+        _allocator_refs = None
+        return
+    if alloc is None or free is None:
+        raise ValueError("give both alloc and free, or neither")
+
+    def _a(nbytes, device, _ctx):
+        try:
+            return alloc(nbytes, device) or None
+        except Exception:   # reported to the library as out of memory
+            return None
+
+    def _f(ptr, nbytes, device, _ctx):
+        free(ptr, nbytes, device)
+
+    refs = (ALLOC_FN(_a), FREE_FN(_f))
+    _check(lib().ridc_set_allocator(refs[0], refs[1], None), "ridc_set_allocator")
+    _allocator_refs = refs
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Let torch's CUDA caching allocator own the library's device memory (enable=False:
+    cudaMalloc / cudaFree again). The library synchronises its stream before it returns a
+    buffer, so torch may reuse it at once."""
+    if not enable:
+        set_allocator(None, None)
+        return
+    import torch
+
+    def alloc(nbytes, device):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device))
+
+    def free(ptr, nbytes, device):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    set_allocator(alloc, free)
 
 
 def quadrature_weights(order: int) -> np.ndarray:

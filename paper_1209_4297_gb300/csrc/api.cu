@@ -11,7 +11,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 
 #include "ridc_internal.h"
 
@@ -38,12 +40,65 @@ namespace ridc {
 // ---- host-side fault injection (tests): the k-th device allocation from now on fails -------
 static std::atomic<long> g_fail_alloc{0};
 
+// ---- the caller's allocator (ridc_set_allocator); sizes are kept for its free ------------
+static ridc_alloc_fn g_alloc = nullptr;
+static ridc_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+static std::mutex g_alloc_mu;
+static std::unordered_map<void*, size_t> g_alloc_sizes;
+static std::atomic<long> g_live{0};
+
+void live_handles_add(int d) { g_live.fetch_add(d); }
+
 cudaError_t dev_malloc(void** p, size_t bytes) {
-  if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) {
-    *p = nullptr;
-    return cudaErrorMemoryAllocation;
+  *p = nullptr;
+  if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) return cudaErrorMemoryAllocation;
+  if (!g_alloc) return cudaMalloc(p, bytes);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  void* q = g_alloc(bytes, dev, g_alloc_ctx);
+  if (!q) return cudaErrorMemoryAllocation;
+  if (reinterpret_cast<uintptr_t>(q) & 255u) {   // TMA and vector accesses need the alignment
+    g_free(q, bytes, dev, g_alloc_ctx);
+    return cudaErrorInvalidValue;
   }
-  return cudaMalloc(p, bytes);
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc_sizes[q] = bytes;
+  }
+  *p = q;
+  return cudaSuccess;
+}
+
+void dev_free(void* p, cudaStream_t used_on) {
+  if (!p) return;
+  if (!g_free) {
+    cudaFree(p);
+    return;
+  }
+  if (used_on) cudaStreamSynchronize(used_on);
+  else cudaDeviceSynchronize();
+  size_t bytes = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = g_alloc_sizes.find(p);
+    if (it != g_alloc_sizes.end()) {
+      bytes = it->second;
+      g_alloc_sizes.erase(it);
+    }
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  g_free(p, bytes, dev, g_alloc_ctx);
+}
+
+extern "C" int ridc_set_allocator(ridc_alloc_fn alloc, ridc_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return RIDC_ERR_ARG;
+  if (g_live.load() != 0) return RIDC_ERR_ARG;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = alloc ? ctx : nullptr;
+  return RIDC_OK;
 }
 
 extern "C" int ridc_debug_fail_alloc(int k) {
@@ -336,7 +391,7 @@ static int build_tables_1d(Ctx* c) {
 // lifetime
 // ------------------------------------------------------------------------------------------
 static void free_all(Ctx* c) {
-  auto f = [](void* p) { if (p) cudaFree(p); };
+  auto f = [c](void* p) { dev_free(p, c->stream); };
   for (int j = 0; j < kMaxOrder; ++j) { f(c->eta[j]); f(c->fN[j]); f(c->Fq[j]); }
   f(c->r); f(c->delta); f(c->delta2); f(c->dinc); f(c->t1); f(c->t2); f(c->xh); f(c->xl); f(c->yh); f(c->yl);
   f(c->Q); f(c->Qt); f(c->inv_den); f(c->lam_f); f(c->Bfh); f(c->Bfl); f(c->Bbh); f(c->Bbl);
@@ -457,6 +512,7 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
     return rc;
   }
   *out = reinterpret_cast<ridc_handle>(c);
+  live_handles_add(1);
   return RIDC_OK;
 }
 
@@ -467,6 +523,7 @@ extern "C" void ridc_destroy(ridc_handle h) {
   cudaStreamSynchronize(c->stream);
   free_all(c);
   delete c;
+  live_handles_add(-1);
 }
 
 static Ctx* ctx_of(ridc_handle h) { return reinterpret_cast<Ctx*>(h); }
@@ -745,7 +802,7 @@ static int advance_run(Ctx* c, long nsteps) {
     }
     if (p[c->P - 1] != target) return RIDC_ERR_CUDA;   // schedule stalled: cannot happen
     if (masks.size() > c->sched_cap) {
-      if (c->sched_dev) cudaFree(c->sched_dev);
+      dev_free(c->sched_dev, c->stream);   // the previous 1D launch may still read it
       c->sched_dev = nullptr;
       c->sched_cap = 0;
       RIDC_CUDA(dev_malloc((void**)&c->sched_dev, masks.size() * sizeof(unsigned)));

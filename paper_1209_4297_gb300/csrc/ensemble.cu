@@ -493,7 +493,7 @@ static int b_alloc(BatchCtx* b, void** p, size_t bytes) {
 }
 
 static void b_free(BatchCtx* b) {
-  for (void* p : b->allocs) cudaFree(p);
+  for (void* p : b->allocs) dev_free(p, b->stream);
   b->allocs.clear();
 }
 
@@ -554,7 +554,7 @@ static int batch_run(BatchCtx* b, long nsteps, int cl, int per_sm, const int* or
         if (m & (1u << j)) p[j]++;
     }
     if (masks.size() > b->masks_cap[I.P]) {
-      if (b->masks_dev[I.P]) cudaFree(b->masks_dev[I.P]);
+      dev_free(b->masks_dev[I.P], b->stream);   // an earlier replay may still read it
       b->masks_dev[I.P] = nullptr;
       b->masks_cap[I.P] = 0;
       cudaError_t e = dev_malloc((void**)&b->masks_dev[I.P], (masks.size() + 1) * sizeof(unsigned));
@@ -642,8 +642,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   int rc = RIDC_OK;
   auto fail = [&](int code) {
     b_free(b);
-    for (int p = 0; p <= EMaxP; ++p)
-      if (b->masks_dev[p]) cudaFree(b->masks_dev[p]);
+    for (int p = 0; p <= EMaxP; ++p) dev_free(b->masks_dev[p], b->stream);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     return code;
@@ -775,6 +774,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_status(e));
   *out = reinterpret_cast<ridc_batch>(b);
+  live_handles_add(1);
   return RIDC_OK;
 }
 
@@ -786,11 +786,11 @@ extern "C" void ridc_batch_destroy(ridc_batch h) {
   DeviceGuard dg(b->device);
   cudaStreamSynchronize(b->stream);
   b_free(b);
-  for (int p = 0; p <= EMaxP; ++p)
-    if (b->masks_dev[p]) cudaFree(b->masks_dev[p]);
+  for (int p = 0; p <= EMaxP; ++p) dev_free(b->masks_dev[p], b->stream);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
+  live_handles_add(-1);
 }
 
 extern "C" long ridc_batch_graph_launches(ridc_batch h) {

@@ -210,8 +210,14 @@ int cuda_status(cudaError_t e);
     if (rc__ != RIDC_OK) return rc__;  \
   } while (0)
 #define RIDC_CUDA(expr) RIDC_TRY(cuda_status(expr))
-// cudaMalloc behind the allocation-failure hook of ridc_debug_fail_alloc
+// device allocation behind the allocation-failure hook of ridc_debug_fail_alloc: cudaMalloc,
+// or the caller's allocator (ridc_set_allocator)
 cudaError_t dev_malloc(void** p, size_t bytes);
+// gives back a dev_malloc pointer (nullptr: nothing). With the caller's allocator the stream
+// that used it (nullptr: the device) is synchronised first; cudaFree synchronises by itself.
+void dev_free(void* p, cudaStream_t used_on);
+// live handles and batches (ridc_set_allocator refuses to switch while any exists)
+void live_handles_add(int d);
 
 // The calls of a handle run on the device it was created on: the guard makes that device
 // current for the call and gives the caller's current device back on return.

@@ -165,6 +165,18 @@ def test_fault_hooks_reject_bad_arguments():
     assert L.ridc_debug_stall_next_gemm(None) == -1
 
 
+def test_allocator_hook_arguments():
+    """ridc_set_allocator: both callbacks or neither (host-side checks, no device needed)."""
+    from paper_1209_4297_gb300 import binding as B
+    L = R.lib()
+    assert L.ridc_set_allocator(B.ALLOC_FN(), B.FREE_FN(), None) == 0
+    assert L.ridc_set_allocator(B.ALLOC_FN(lambda n, d, c: None), B.FREE_FN(), None) == -1
+    assert L.ridc_set_allocator(B.ALLOC_FN(), B.FREE_FN(lambda p, n, d, c: None), None) == -1
+    with pytest.raises(ValueError):
+        B.set_allocator(lambda n, d: 0, None)
+    B.set_allocator(None, None)
+
+
 def test_binding_tables_match_the_header():
     """The ctypes binding's kind, precision and kernel-id tables agree with include/ridc.h."""
     from paper_1209_4297_gb300 import binding as B
