@@ -100,11 +100,11 @@ typedef struct {
 
 typedef struct {
     int dim;              /* 1 or 2; must match the kind                                     */
-    int n;                /* unknowns per side: 1D n >= 8 with (2 L + 1) n256 <= 28000,
-                             L = ceil(order / min(order, 8)) levels per SM and n256 = n
-                             rounded up to a multiple of 256 (shared-memory rows; n <= 9216
-                             up to order 8); 2D FP64 4 <= n <= 16384; 2D mixed: n a
-                             multiple of 256, at most 4096                                   */
+    int n;                /* unknowns per side: 1D n >= 8 with (L + 1) n256 + L n + 1 <=
+                             28000 doubles of shared memory, L = ceil(order / min(order, 8))
+                             levels per SM and n256 = n rounded up to a multiple of 256
+                             (n <= 9216 up to order 8, n <= 5551 at orders 9-12); 2D FP64
+                             4 <= n <= 16384; 2D mixed: n a multiple of 256, at most 4096    */
 } ridc_grid;
 
 typedef struct ridc_ctx* ridc_handle;   /* opaque; owned by the library                      */

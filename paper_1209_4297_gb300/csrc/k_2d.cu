@@ -88,6 +88,20 @@ __device__ __forceinline__ void store_split2(__nv_bfloat16* hi, __nv_bfloat16* l
   *reinterpret_cast<__nv_bfloat162*>(lo + idx) = lv;
 }
 
+// one value, in the same operation order as rhs_at (the FP64 path of odd planes: one species
+// and odd n make n^2 odd, so ring slots are only 8-byte aligned and double2 cannot be used)
+template <int NODES>
+__device__ __forceinline__ double rhs_at1(const RhsArgs& a, const RhsLevel& L,
+                                          const double (&w)[NODES], long i) {
+  if (L.eta_j) {
+    double acc = fma(a.dt, L.fN_j[i] - L.fN_p[i], L.eta_j[i] - L.eta_pn[i]);
+#pragma unroll
+    for (int k = 0; k < NODES; ++k) acc = fma(w[k], __ldg(L.Fn[k] + i), acc);
+    return acc;
+  }
+  return w[0] * __ldg(L.Fn[0] + i);
+}
+
 // FP16 form: v0, v1 staged in FP32 (8-byte aligned: idx is even)
 __device__ __forceinline__ void store_stage2(float* st, long idx, float v0, float v1) {
   *reinterpret_cast<float2*>(st + idx) = make_float2(v0, v1);
@@ -118,6 +132,12 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
     w[k] = L.w[k];
   }
   double2* r2 = (double2*)(a.r + out_off);
+  if (!STAGE && !a.r_hi && (a.plane & 1)) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < a.plane;
+         i += (long)gridDim.x * blockDim.x)
+      a.r[out_off + i] = rhs_at1<NODES>(a, L, w, i);
+    return;
+  }
   if (!STAGE && !a.r_hi) {
     const long half = a.plane >> 1;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < half;

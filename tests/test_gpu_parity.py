@@ -63,7 +63,7 @@ def test_gray_scott_fp64_small_grids(n):
         assert rel_l2(levels[j][0], ref[j]) <= 1e-12, j
 
 
-@pytest.mark.parametrize("n", [20, 48])
+@pytest.mark.parametrize("n", [20, 48, 21, 33])   # odd n, one species: n^2 odd, scalar loads
 def test_dirichlet_adv_diff_fp64_small_grids(n):
     w = inputs.adv_diff_2d(n=n, nsteps=30, kmax=4, dt=1.0 / (2 * n), nu=2e-3)
     got, _, _ = _run(w)
