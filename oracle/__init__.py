@@ -20,8 +20,8 @@ a matrix-exponential solution of the 2D Dirichlet problem.
 from .quadrature import lagrange_weights, weight_table, stencil
 from .problems import (AdvDiff1DPeriodic, AdvDiff1DUpwindPeriodic, Burgers1DDirichlet,
                        GrayScott2DNeumann, AdvDiff2DDirichlet, from_workload)
-from .ridc import ridc_sequential, ridc_restarted, fbe
+from .ridc import ridc_sequential, ridc_restarted, ridc_lagged, fbe
 
 __all__ = ["lagrange_weights", "weight_table", "stencil", "AdvDiff1DPeriodic",
            "AdvDiff1DUpwindPeriodic", "Burgers1DDirichlet", "GrayScott2DNeumann",
-           "AdvDiff2DDirichlet", "from_workload", "ridc_sequential", "ridc_restarted", "fbe"]
+           "AdvDiff2DDirichlet", "from_workload", "ridc_sequential", "ridc_restarted", "ridc_lagged", "fbe"]

@@ -76,3 +76,59 @@ def ridc_restarted(problem, y0: np.ndarray, dt: float, nsteps: int, order: int,
         y = ridc_sequential(problem, y, dt, k, order)
         done += k
     return y
+
+
+def ridc_lagged(problem, y0: np.ndarray, dt: float, nsteps: int, order: int,
+                with_schedule: bool = False):
+    """The same RIDC, executed as the lagged pipeline of Section III-E: in every pipeline step
+    each level that has its inputs advances by one time step, all of them reading only values
+    that existed before the step. Level j computes eta^j_{n+1} from eta^{j-1}_{n+1} and the
+    stencil nodes b..b+j of level j-1 (b = max(0, n+1-j)), so it may advance once level j-1
+    has reached index max(n+1, j). Full histories are kept (no ring buffers): the identity
+    with ridc_sequential is about values, and each update repeats its arithmetic exactly, so
+    the two agree bit for bit.
+
+    Returns eta^{order-1}_{nsteps}; with with_schedule=True also the list of level sets that
+    advanced in each pipeline step.
+    """
+    if order < 1:
+        raise ValueError("order >= 1")
+    w = weight_table(order)
+    n_low = max(nsteps, order - 1)
+    last = [nsteps if (j == order - 1) else (nsteps if order == 1 else n_low)
+            for j in range(order)]
+    y = np.array(y0, dtype=np.float64, copy=True)
+    eta = [[y.copy()] for _ in range(order)]
+    fN = [[problem.fN(y)] for _ in range(order)]
+    F = [[fN[j][0] + problem.D(y)] for j in range(order)]
+    schedule = []
+    while len(eta[order - 1]) - 1 < last[order - 1]:
+        ready = []
+        for j in range(order):
+            n = len(eta[j]) - 1
+            if n >= last[j]:
+                continue
+            if j == 0 or len(eta[j - 1]) - 1 >= max(n + 1, j):
+                ready.append(j)
+        if not ready:
+            raise RuntimeError("pipeline stalled")
+        new = {}
+        for j in ready:                      # every update reads the state before this step
+            n = len(eta[j]) - 1
+            if j == 0:
+                new[j] = problem.solve(eta[0][n] + dt * fN[0][n], dt)
+                continue
+            b, m = stencil(j, n)
+            quad = np.zeros_like(y)
+            for i in range(j + 1):
+                quad += w[j][m][i] * F[j - 1][b + i]
+            rhs = (eta[j][n] + dt * (fN[j][n] - fN[j - 1][n])
+                   - dt * problem.D(eta[j - 1][n + 1]) + dt * quad)
+            new[j] = problem.solve(rhs, dt)
+        for j, e in new.items():
+            eta[j].append(e)
+            fN[j].append(problem.fN(e))
+            F[j].append(fN[j][-1] + problem.D(e))
+        schedule.append(ready)
+    out = eta[order - 1][nsteps]
+    return (out, schedule) if with_schedule else out

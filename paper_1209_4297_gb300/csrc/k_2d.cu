@@ -91,15 +91,14 @@ __device__ __forceinline__ void store_split2(__nv_bfloat16* hi, __nv_bfloat16* l
 // one value, in the same operation order as rhs_at (the FP64 path of odd planes: one species
 // and odd n make n^2 odd, so ring slots are only 8-byte aligned and double2 cannot be used)
 template <int NODES>
-__device__ __forceinline__ double rhs_at1(const RhsArgs& a, const RhsLevel& L,
-                                          const double (&w)[NODES], long i) {
+__device__ __forceinline__ double rhs_at1(const RhsArgs& a, const RhsLevel& L, long i) {
   if (L.eta_j) {
     double acc = fma(a.dt, L.fN_j[i] - L.fN_p[i], L.eta_j[i] - L.eta_pn[i]);
 #pragma unroll
-    for (int k = 0; k < NODES; ++k) acc = fma(w[k], __ldg(L.Fn[k] + i), acc);
+    for (int k = 0; k < NODES; ++k) acc = fma(L.w[k], __ldg(L.Fn[k] + i), acc);
     return acc;
   }
-  return w[0] * __ldg(L.Fn[0] + i);
+  return L.w[0] * __ldg(L.Fn[0] + i);
 }
 
 // FP16 form: v0, v1 staged in FP32 (8-byte aligned: idx is even)
@@ -132,12 +131,6 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
     w[k] = L.w[k];
   }
   double2* r2 = (double2*)(a.r + out_off);
-  if (!STAGE && !a.r_hi && (a.plane & 1)) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < a.plane;
-         i += (long)gridDim.x * blockDim.x)
-      a.r[out_off + i] = rhs_at1<NODES>(a, L, w, i);
-    return;
-  }
   if (!STAGE && !a.r_hi) {
     const long half = a.plane >> 1;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < half;
@@ -201,6 +194,34 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
   if (STAGE && mp >= 0) flush_plane_max(a.pmax + mp, mx);
 }
 
+// FP64 right-hand side of odd planes (one species, odd n), one value per thread and step
+template <int NODES>
+__device__ __forceinline__ void rhs_level_scalar(const RhsArgs& a, const RhsLevel& L,
+                                                 long out_off) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < a.plane;
+       i += (long)gridDim.x * blockDim.x)
+    a.r[out_off + i] = rhs_at1<NODES>(a, L, i);
+}
+
+__global__ void __launch_bounds__(256) rhs_scalar_kernel(const __grid_constant__ RhsArgs a) {
+  const RhsLevel& L = a.lv[blockIdx.y];
+  const long out_off = (long)blockIdx.y * a.plane;
+  switch (L.nnodes) {
+    case 1: rhs_level_scalar<1>(a, L, out_off); break;
+    case 2: rhs_level_scalar<2>(a, L, out_off); break;
+    case 3: rhs_level_scalar<3>(a, L, out_off); break;
+    case 4: rhs_level_scalar<4>(a, L, out_off); break;
+    case 5: rhs_level_scalar<5>(a, L, out_off); break;
+    case 6: rhs_level_scalar<6>(a, L, out_off); break;
+    case 7: rhs_level_scalar<7>(a, L, out_off); break;
+    case 8: rhs_level_scalar<8>(a, L, out_off); break;
+    case 9: rhs_level_scalar<9>(a, L, out_off); break;
+    case 10: rhs_level_scalar<10>(a, L, out_off); break;
+    case 11: rhs_level_scalar<11>(a, L, out_off); break;
+    default: rhs_level_scalar<12>(a, L, out_off); break;
+  }
+}
+
 template <bool STAGE>
 __global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArgs a) {
   const RhsLevel& L = a.lv[blockIdx.y];
@@ -231,6 +252,8 @@ int launch_rhs(Ctx* c, const RhsArgs& a) {
   prof_begin(c, RIDC_KERNEL_RHS, &e0);
   if (a.r_stage)
     rhs_kernel<true><<<grid, 256, 0, c->stream>>>(a);
+  else if (!a.r_hi && (a.plane & 1))   // FP64, odd plane: fields only 8-byte aligned
+    rhs_scalar_kernel<<<grid, 256, 0, c->stream>>>(a);
   else
     rhs_kernel<false><<<grid, 256, 0, c->stream>>>(a);
   prof_end(c, RIDC_KERNEL_RHS, e0);
