@@ -255,7 +255,8 @@ def run_reference(args):
 def run_ensemble(args):
     """The 512-instance ensemble (uneven Dirichlet advection-diffusion, FP32 solves with one
     FP64-residual refinement pass) advanced 256 steps by one persistent launch; the autotuner
-    picks the launch configuration first. Not the default line: a per-config measurement."""
+    picks the launch configuration first. Not the default line: a per-config measurement.
+    --ens-count / --ens-steps shrink it (for profiling a small case)."""
     import torch
 
     import inputs
@@ -263,7 +264,8 @@ def run_ensemble(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    ws = inputs.ensemble(512, nsteps=256)
+    count, nst = args.ens_count, args.ens_steps
+    ws = inputs.ensemble(count, nsteps=nst)
     u0s = [torch.from_numpy(w.u0[0].copy()).cuda() for w in ws]
     b = Batch(ws, n_refine=args.ens_refine, stream=stream.cuda_stream)
     b.set_initial(u0s)
@@ -271,14 +273,14 @@ def run_ensemble(args):
     cells = b.cells()
     for _ in range(args.warmup):
         b.set_initial(u0s)
-        b.advance(256)
+        b.advance(nst)
     torch.cuda.synchronize()
     times = []
     for _ in range(args.steps):
         b.set_initial(u0s)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        b.advance(256)
+        b.advance(nst)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -290,17 +292,17 @@ def run_ensemble(args):
     passes = 1 + args.ens_refine
     gemm_flops = 0.0
     for w in ws:
-        levels = sum(bin(int(m)).count("1") for m in schedule_plan(w.order, 256))
+        levels = sum(bin(int(m)).count("1") for m in schedule_plan(w.order, nst))
         gemm_flops += levels * 4 * 1.0 * w.n ** 3 * passes
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     fp32_peak = sms * 128 * 2 * 2070e6   # FP32 lanes per SM x FMA x max SM clock
     gemm_tf = gemm_flops / (ms * 1e-3) / 1e12
-    line = {"metric": "ensemble cell-updates/s (sum over instances of side^2 x 256 steps)",
-            "value": cells * 256 / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    line = {"metric": f"ensemble cell-updates/s (sum over instances of side^2 x {nst} steps)",
+            "value": cells * nst / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "dtype": "f64+fp32 solves", "data": "synthetic",
-            "config": {"workload": "ensemble_512_dirichlet_adv_diff", "instances": 512,
-                       "steps": 256, "n_refine": args.ens_refine, "autotune_choice": choice,
+            "config": {"workload": f"ensemble_{count}_dirichlet_adv_diff", "instances": count,
+                       "steps": nst, "n_refine": args.ens_refine, "autotune_choice": choice,
                        "launch": "one CUDA graph per advance (counter reset + persistent "
                                  "cluster launch)",
                        "cells_per_step": cells},
@@ -472,6 +474,10 @@ def main():
                     help="refinement passes of those lines (the headline line uses 2)")
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--ens-refine", type=int, default=1)
+    ap.add_argument("--ens-count", type=int, default=512,
+                    help="instances of the ensemble line (the configuration has 512)")
+    ap.add_argument("--ens-steps", type=int, default=256,
+                    help="steps of the ensemble line (the configuration has 256)")
     ap.add_argument("--nt-truncate", type=int, default=60)
     args = ap.parse_args()
     if args.impl == "reference":

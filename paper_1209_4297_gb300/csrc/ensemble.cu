@@ -268,6 +268,43 @@ __device__ void dual_sgemm(const float* __restrict__ A, const float* __restrict_
   }
 }
 
+// The FP64 phases below are latency-bound (16 warps per SM): each thread takes two elements
+// per iteration, i and i + gs, and issues all their loads before any arithmetic or store, so
+// twice as many loads are in flight. Every element's arithmetic is unchanged. When i + gs is
+// past the end the second element repeats the first and is not stored.
+
+// right-hand side with NJ quadrature terms (eq. (corr) in delta form) and its FP32 copy
+template <int NJ>
+__device__ __forceinline__ void ens_rhs(const double* ej, const double* fj, const double* ep,
+                                        const double* fp, const double* const (&Fb)[EMaxP],
+                                        const double (&wd)[EMaxP], double dt, double* rq,
+                                        float* fq, long ss, long g0, long gs) {
+  for (long i = g0; i < ss; i += 2 * gs) {
+    const bool two = i + gs < ss;
+    const long i1 = two ? i + gs : i;
+    const double e0 = ej[i], e1 = ej[i1], p0 = ep[i], p1 = ep[i1];
+    const double f0 = fj[i], f1 = fj[i1], q0 = fp[i], q1 = fp[i1];
+    double F0[NJ], F1[NJ];
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) {
+      F0[k] = Fb[k][i];
+      F1[k] = Fb[k][i1];
+    }
+    double a0 = fma(dt, f0 - q0, e0 - p0), a1 = fma(dt, f1 - q1, e1 - p1);
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) {
+      a0 = fma(wd[k], F0[k], a0);
+      a1 = fma(wd[k], F1[k], a1);
+    }
+    rq[i] = a0;
+    fq[i] = e_f64_to_f32(a0);
+    if (two) {
+      rq[i1] = a1;
+      fq[i1] = e_f64_to_f32(a1);
+    }
+  }
+}
+
 template <int CL>
 __device__ __forceinline__ void csync() {
   if (CL > 1) cooperative_groups::this_cluster().sync();
@@ -370,23 +407,9 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
             wd[k] = (k <= j) ? I.dt * w[k] : 0.0;
           }
           // exactly j+1 quadrature terms: no predicated-off FP64 work (it still costs pipe time)
-#define ENS_RHS_LOOP(EXTRA)                                          \
-  for (long i = g0; i < ss; i += gs) {                               \
-    double acc = fma(I.dt, fj[i] - fp[i], ej[i] - ep[i]);            \
-    acc = fma(wd[0], Fb[0][i], acc);                                 \
-    acc = fma(wd[1], Fb[1][i], acc);                                 \
-    EXTRA                                                            \
-    rq[i] = acc;                                                     \
-    fq[i] = e_f64_to_f32(acc);                                       \
-  }
-          if (j == 1) {
-            ENS_RHS_LOOP()
-          } else if (j == 2) {
-            ENS_RHS_LOOP(acc = fma(wd[2], Fb[2][i], acc);)
-          } else {
-            ENS_RHS_LOOP(acc = fma(wd[2], Fb[2][i], acc); acc = fma(wd[3], Fb[3][i], acc);)
-          }
-#undef ENS_RHS_LOOP
+          if (j == 1) ens_rhs<2>(ej, fj, ep, fp, Fb, wd, I.dt, rq, fq, ss, g0, gs);
+          else if (j == 2) ens_rhs<3>(ej, fj, ep, fp, Fb, wd, I.dt, rq, fq, ss, g0, gs);
+          else ens_rhs<4>(ej, fj, ep, fp, Fb, wd, I.dt, rq, fq, ss, g0, gs);
         }
       }
       csync<CL>();
@@ -398,14 +421,30 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
         for (long e = g0; e < na * ss; e += gs)
           dt_tot[e] = (pass == 1) ? e_f32_to_f64(df[e]) : dt_tot[e] + e_f32_to_f64(df[e]);
         csync<CL>();
-        for (long e = g0; e < na * ss; e += gs) {
-          const long q = e / ss, i = e - q * ss;
-          const int gy = (int)(i / s), gx = (int)(i - (long)gy * s);
-          const double* d = dt_tot + q * ss;
-          const double sum = (odd_at(d, s, gy - 1, gx) + odd_at(d, s, gy + 1, gx)) +
-                             (odd_at(d, s, gy, gx - 1) + odd_at(d, s, gy, gx + 1));
-          const double v = fma(I.cres, sum, fma(I.cres1, d[i], r[e]));
-          rf[e] = e_f64_to_f32(v);   // safe: df was folded into dt_tot above
+        const long tot = na * ss;
+        for (long e = g0; e < tot; e += 2 * gs) {
+          const bool two = e + gs < tot;
+          const long e1 = two ? e + gs : e;
+          double nb[2][4], dc[2], rr[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const long ee = u ? e1 : e;
+            const long q = ee / ss, i = ee - q * ss;
+            const int gy = (int)(i / s), gx = (int)(i - (long)gy * s);
+            const double* d = dt_tot + q * ss;
+            nb[u][0] = odd_at(d, s, gy - 1, gx);
+            nb[u][1] = odd_at(d, s, gy + 1, gx);
+            nb[u][2] = odd_at(d, s, gy, gx - 1);
+            nb[u][3] = odd_at(d, s, gy, gx + 1);
+            dc[u] = d[i];
+            rr[u] = r[ee];
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const double sum = (nb[u][0] + nb[u][1]) + (nb[u][2] + nb[u][3]);
+            const double v = fma(I.cres, sum, fma(I.cres1, dc[u], rr[u]));
+            if (u == 0 || two) rf[u ? e1 : e] = e_f64_to_f32(v);   // df is folded into dt_tot
+          }
         }
         csync<CL>();
         solve_any<CL>(C, I, na, rf, t1, t2, rf, ens_smem, rank);
@@ -419,10 +458,22 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
         double* out = I.eta[j] + ((n + 1) % I.cap[j]) * ss;
         const float* dq = df + q * ss;
         const double* tq = dt_tot + q * ss;
-        if (a.nref > 0) {
-          for (long i = g0; i < ss; i += gs) out[i] = base[i] + (e_f32_to_f64(dq[i]) + tq[i]);
-        } else {
-          for (long i = g0; i < ss; i += gs) out[i] = base[i] + e_f32_to_f64(dq[i]);
+        for (long i = g0; i < ss; i += 2 * gs) {
+          const bool two = i + gs < ss;
+          const long i1 = two ? i + gs : i;
+          const double b0 = base[i], b1 = base[i1];
+          const float d0 = dq[i], d1 = dq[i1];
+          double o0, o1;
+          if (a.nref > 0) {
+            const double t0 = tq[i], t1 = tq[i1];
+            o0 = b0 + (e_f32_to_f64(d0) + t0);
+            o1 = b1 + (e_f32_to_f64(d1) + t1);
+          } else {
+            o0 = b0 + e_f32_to_f64(d0);
+            o1 = b1 + e_f32_to_f64(d1);
+          }
+          out[i] = o0;
+          if (two) out[i1] = o1;
         }
       }
       csync<CL>();
@@ -433,13 +484,28 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
         const double* e = I.eta[j] + slot;
         double* fN = I.fN[j] + slot;
         double* F = I.F[j] ? I.F[j] + slot : nullptr;
-        for (long i = g0; i < ss; i += gs) {
-          const int gy = (int)(i / s), gx = (int)(i - (long)gy * s);
-          const double xe = odd_at(e, s, gy, gx + 1), xw = odd_at(e, s, gy, gx - 1);
-          const double yn = odd_at(e, s, gy + 1, gx), ys = odd_at(e, s, gy - 1, gx);
-          const double fn = -I.a2h * (xe - xw) - I.b2h * (yn - ys);
-          fN[i] = fn;
-          if (F) F[i] = fma(I.c_lap, (xe + xw) + (yn + ys), fma(I.c_lap4, e[i], fn));
+        for (long i = g0; i < ss; i += 2 * gs) {
+          const bool two = i + gs < ss;
+          const long i1 = two ? i + gs : i;
+          double xe[2], xw[2], yn[2], ys[2], ec[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const long ii = u ? i1 : i;
+            const int gy = (int)(ii / s), gx = (int)(ii - (long)gy * s);
+            xe[u] = odd_at(e, s, gy, gx + 1);
+            xw[u] = odd_at(e, s, gy, gx - 1);
+            yn[u] = odd_at(e, s, gy + 1, gx);
+            ys[u] = odd_at(e, s, gy - 1, gx);
+            ec[u] = e[ii];
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+            const long ii = u ? i1 : i;
+            const double fn = -I.a2h * (xe[u] - xw[u]) - I.b2h * (yn[u] - ys[u]);
+            fN[ii] = fn;
+            if (F) F[ii] = fma(I.c_lap, (xe[u] + xw[u]) + (yn[u] + ys[u]), fma(I.c_lap4, ec[u], fn));
+          }
         }
       }
       csync<CL>();
