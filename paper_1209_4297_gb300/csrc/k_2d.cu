@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) rhs_scalar_kernel(const __grid_constant__
 }
 
 template <bool STAGE>
-__global__ void __launch_bounds__(256) rhs_kernel(const __grid_constant__ RhsArgs a) {
+__global__ void __launch_bounds__(256, 4) rhs_kernel(const __grid_constant__ RhsArgs a) {
   const RhsLevel& L = a.lv[blockIdx.y];
   const long out_off = (long)blockIdx.y * a.plane;
   switch (L.nnodes) {
