@@ -9,7 +9,8 @@ Grids:
   * 1D periodic on [0, 1): nodes x_i = i / N.
   * 2D on [0, 1]^2 (Neumann or Dirichlet walls): cell centres x_i = (i + 1/2) / N.
 
-Workloads (the readings of the unstated details are listed in the design doc):
+Workloads (where the problem statement leaves a detail open, each generator's docstring
+states the choice made):
   * adv_diff_1d      N=256, a=1, nu=0.01, RIDC order 4, dt=1/512, T=1.
   * adv_diff_upwind_1d  the paper's advection-diffusion run (dx=1/1000, T=40, upwind).
   * burgers_1d       the paper's viscous Burgers run (dx=1/1000, T=1, Dirichlet walls).
