@@ -6,6 +6,8 @@
   * Gray-Scott: (u, v) = (1, 0) is a fixed point; a uniform field follows the reaction ODE
     (the Laplacian of a constant vanishes under zero flux), compared with scipy's
     high-accuracy ODE integrator.
+  * Gray-Scott with F = k = 0 and v = 0 is linear diffusion of u: one cosine mode under FBE
+    follows (1 - dt Du lambda)^-n, and RIDC4 converges at order 4 to the matrix exponential.
   * Dirichlet advection-diffusion: pure diffusion of one sine mode under FBE is the
     closed form (1 - dt nu lambda)^-n; with advection, RIDC4 converges at order 4 to
     the matrix exponential of the semi-discrete system.
@@ -126,6 +128,44 @@ def test_dirichlet_pure_diffusion_fbe_closed_form():
     got = fbe(p, q, dt, steps)[-1]
     factor = (1.0 - dt * nu * (_lam(n, kx) + _lam(n, ky))) ** (-steps)
     np.testing.assert_allclose(got, factor * q, atol=1e-14)
+
+
+@pytest.mark.parametrize("kx,ky", [(0, 0), (2, 1), (5, 7)])
+def test_gray_scott_pure_diffusion_fbe_closed_form(kx, ky):
+    """F = k = 0 and v = 0 leave u_t = Du Lap u: under FBE one cosine mode of u is scaled by
+    (1 - dt Du (lambda_kx + lambda_ky))^-1 per step, and v stays exactly 0."""
+    n, Du, Dv, dt, steps = 16, 2e-3, 1e-3, 0.5, 7
+    p = GrayScott2DNeumann(n, Du, Dv, 0.0, 0.0)
+    c = (np.arange(n) + 0.5) / n
+    q = np.cos(np.pi * ky * c)[:, None] * np.cos(np.pi * kx * c)[None, :]
+    y0 = np.stack([q, np.zeros((n, n))])
+    got = fbe(p, y0, dt, steps)[-1]
+    factor = (1.0 - dt * Du * (_lam(n, kx) + _lam(n, ky))) ** (-steps)
+    np.testing.assert_allclose(got[0], factor * q, atol=1e-14)
+    assert not np.any(got[1])
+
+
+def test_gray_scott_linear_part_order_4_against_matrix_exponential():
+    """With F = k = 0 and v = 0 the Gray-Scott system is linear diffusion of u: RIDC4 converges
+    at order 4 to the matrix exponential of the semi-discrete Neumann Laplacian."""
+    n, Du, T = 8, 5e-3, 4.0
+    p = GrayScott2DNeumann(n, Du, 1e-3, 0.0, 0.0)
+    g = np.random.default_rng(5)
+    u0 = g.standard_normal((n, n))
+    y0 = np.stack([u0, np.zeros((n, n))])
+    M = np.zeros((n * n, n * n))
+    for col in range(n * n):
+        e = np.zeros((2, n, n))
+        e[0].ravel()[col] = 1.0
+        M[:, col] = p.D(e)[0].ravel()
+    ref = (scipy.linalg.expm(T * M) @ u0.ravel()).reshape(n, n)
+    errs = []
+    for nt in (8, 16, 32):
+        got = ridc_sequential(p, y0, T / nt, nt, 4)
+        assert not np.any(got[1])
+        errs.append(np.linalg.norm(got[0] - ref) / np.linalg.norm(ref))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert slopes[-1] > 3.7, (errs, slopes)
 
 
 def test_dirichlet_adv_diff_order_4_against_matrix_exponential():
