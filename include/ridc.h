@@ -207,8 +207,10 @@ int ridc_solve_planes(ridc_handle h, const double* r, double* delta, int nplanes
  * and 1 <= nplanes <= 8; larger requests return RIDC_ERR_UNSUPPORTED. Every call rewrites
  * the whole array, so calls that overlap on the GPU (concurrent streams, other threads) race
  * and must be serialised by the caller. The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) and should therefore come before any stream capture.
- * No cudaMalloc, cudaFree or other allocating routine is called.                           */
+ * device address (cudaGetSymbolAddress) and should therefore come before any stream capture;
+ * after a cudaDeviceReset the next call looks it up again in the new context. A CUDA error
+ * that an earlier, unrelated call left pending is reported as RIDC_ERR_CUDA and left in place
+ * (nothing is launched). No cudaMalloc, cudaFree or other allocating routine is called.    */
 int ridc_solve_planes_fixed(int kind, int n, const double* nu, double dt, const double* r,
                             double* delta, int nplanes, void* stream);
 

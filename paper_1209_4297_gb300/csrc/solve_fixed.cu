@@ -12,8 +12,11 @@
 //
 // In host code the array's name stands for a host-side shadow, not a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and every kernel receives it as a pointer.
-#include <atomic>
+// current) and every kernel receives it as a pointer. The address is kept per device together
+// with the identity of the device's CUDA context; when that context has been replaced (the
+// caller ran cudaDeviceReset), the next call looks the address up again.
+#include <cuda.h>
+#include <mutex>
 
 #include "ridc_internal.h"
 
@@ -28,7 +31,13 @@ constexpr size_t kFixQ = 0, kFixQt = kFixNN, kFixInv = 2 * kFixNN, kFixT1 = 4 * 
                  kFixDoubles = kFixT2 + kFixMaxPlanes * kFixNN;   // 2.5 MiB
 
 constexpr int kFixMaxDevices = 64;
-std::atomic<double*> g_fix_addr[kFixMaxDevices];
+// per device: the array's device address and the id of the context it was looked up in
+struct FixAddr {
+  double* base = nullptr;
+  unsigned long long ctx_id = 0;
+};
+FixAddr g_fix_addr[kFixMaxDevices];
+std::mutex g_fix_mu;
 
 }  // namespace
 
@@ -106,6 +115,37 @@ __global__ void __launch_bounds__(256) fix_gemm_kernel(const double* __restrict_
   }
 }
 
+// Unique id of the current device's CUDA context (cuCtxGetCurrent + cuCtxGetId through the
+// runtime's driver entry points; ids are never reused within a process).
+int fix_current_context_id(int dev, unsigned long long* id) {
+  using namespace ridc;
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(f);
+  });
+  if (!get_current || !get_id) return RIDC_ERR_CUDA;
+  // cudaSetDevice initialises the device's primary context and makes it current (it
+  // allocates nothing; the device is the current one already)
+  const cudaError_t e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return RIDC_ERR_CUDA;
+  if (get_id(ctx, id) != CUDA_SUCCESS) return RIDC_ERR_CUDA;
+  return RIDC_OK;
+}
+
 }  // namespace
 
 extern "C" int ridc_solve_planes_fixed(int kind, int n, const double* nu, double dt,
@@ -120,18 +160,28 @@ extern "C" int ridc_solve_planes_fixed(int kind, int n, const double* nu, double
     if (!(nu[s] > 0.0) || !isfinite(nu[s])) return RIDC_ERR_ARG;
   if (n > kFixMaxN || nplanes > kFixMaxPlanes) return RIDC_ERR_UNSUPPORTED;
 
+  // an error left pending by an earlier, unrelated call is the caller's: report it and
+  // leave it in place instead of clearing it here
+  if (cudaPeekAtLastError() != cudaSuccess) return RIDC_ERR_CUDA;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
   if (dev < 0 || dev >= kFixMaxDevices) return RIDC_ERR_UNSUPPORTED;
-  double* base = g_fix_addr[dev].load();
-  if (!base) {
-    // set-up, once per device, with that device current
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_fix_scratch);
-    if (e != cudaSuccess) return cuda_status(e);
-    base = static_cast<double*>(p);
-    g_fix_addr[dev].store(base);
+  unsigned long long ctx_id = 0;
+  RIDC_TRY(fix_current_context_id(dev, &ctx_id));
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_fix_mu);
+    FixAddr& fa = g_fix_addr[dev];
+    if (!fa.base || fa.ctx_id != ctx_id) {
+      // set-up, once per device context, with that device current
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_fix_scratch);
+      if (e != cudaSuccess) return cuda_status(e);
+      fa.base = static_cast<double*>(p);
+      fa.ctx_id = ctx_id;
+    }
+    base = fa.base;
   }
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -148,5 +198,6 @@ extern "C" int ridc_solve_planes_fixed(int kind, int n, const double* nu, double
   fix_gemm_kernel<true><<<grid, 256, 0, st>>>(t1, Qt, t2, inv, n, rows, S);
   fix_gemm_kernel<false><<<grid, 256, 0, st>>>(t2, Q, t1, inv, n, rows, S);
   fix_gemm_kernel<false><<<grid, 256, 0, st>>>(t1, Q, delta, inv, n, rows, S);
-  return cuda_status(cudaGetLastError());
+  // nothing was pending on entry, so an error now comes from these launches
+  return cuda_status(cudaPeekAtLastError());
 }

@@ -13,7 +13,7 @@ from ctypes import POINTER, c_double, c_int, c_void_p
 import numpy as np
 import pytest
 
-from paper_1209_4297_gb300 import Integrator, lib
+from paper_1209_4297_gb300 import Integrator, debug_fail_alloc, lib
 from tests.gpu_util import need_cuda, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -62,3 +62,30 @@ def test_fixed_scratch_rejects_requests_beyond_its_capacity():
     assert _call(f, "adv_diff_2d_dirichlet", 256, (1e-3,), 0.01, big, big, 1, stream) == -6
     many = torch.zeros((9, 32, 32), dtype=torch.float64, device="cuda")
     assert _call(f, "adv_diff_2d_dirichlet", 32, (1e-3,), 0.01, many, many, 9, stream) == -6
+
+
+def test_fixed_scratch_solve_in_place_allocates_nothing():
+    """r and delta may be the same buffer; with the next device allocation armed to fail, the
+    call still succeeds (it makes none) and the device's free memory does not change."""
+    torch = need_cuda()
+    f = _entry()
+    stream = torch.cuda.current_stream().cuda_stream
+    kind, n, planes, nu, dt = "gray_scott_2d_neumann", 64, 6, (2e-5, 1e-5), 0.5
+    r = np.random.default_rng(5).standard_normal((planes, n, n))
+    with Integrator(kind, n, nu, dt, 4) as it:
+        want = it.solve_planes(r)
+    buf = torch.from_numpy(r).cuda()
+    _call(f, kind, n, nu, dt, buf, buf, planes, stream)     # set-up call on this device
+    torch.cuda.synchronize()
+    buf.copy_(torch.from_numpy(r))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    debug_fail_alloc(1)
+    try:
+        rc = _call(f, kind, n, nu, dt, buf, buf, planes, stream)
+        torch.cuda.synchronize()
+    finally:
+        debug_fail_alloc(0)
+    assert rc == 0
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert rel_l2(buf.cpu().numpy(), want) <= 1e-13
