@@ -64,16 +64,32 @@ def test_batch_agrees_with_single_instance_fp64_path():
         assert rel_l2(g, ref) <= 1e-10
 
 
-def test_full_ensemble_512_instances_sampled_against_oracle():
-    """The 512-instance workload over its 256 steps with one refinement pass. Four instances
-    are recomputed by the oracle: smallest work, a middle one, the largest, and instance 303,
-    whose central advection at cell Peclet ~18 towards the walls grows ~50x (a property of the
-    semi-discrete operator that the oracle shows too; FP32 solves without refinement lose
-    about 1e-4 relative there). Every instance must stay finite."""
+def test_full_ensemble_512_instances_against_fp64_path_and_oracle():
+    """The 512-instance workload over its 256 steps with two refinement passes, as benchmarked.
+    Every instance is compared with the single-instance FP64 GPU path (held to the oracle at
+    1e-12 by the parity tests), so an indexing or scheduling fault that touched only some
+    instances would show. With one refinement pass the worst instance (118: side 256, order 3)
+    ends 1.9e-8 from the FP64 path, above the 1e-8 bar, while the median is 5e-15: central
+    advection at high cell Peclet makes some instances' operators strongly non-normal, and a
+    pass of FP32 solves gains only about 1e-4 there. Four instances are also recomputed by the
+    oracle: smallest work, a middle one, the largest, and instance 303 (cell Peclet ~18
+    towards the walls, growing ~50x, a property of the semi-discrete operator that the oracle
+    shows too)."""
     need_cuda()
     ws = inputs.ensemble(512, nsteps=256)
-    got = _run_batch(ws, 256, 1)
+    got = _run_batch(ws, 256, 2)
     assert all(np.isfinite(g).all() for g in got)
+    errs = []
+    for w, g in zip(ws, got):
+        with Integrator.from_workload(w) as it:
+            it.set_initial(w.u0)
+            it.advance(256)
+            errs.append(rel_l2(g, it.solution()[0]))
+    errs = np.array(errs)
+    print("ensemble vs FP64 path: rel L2 quantiles (0, 50, 90, 99, 100):",
+          np.quantile(errs, [0, 0.5, 0.9, 0.99, 1.0]))
+    worst = int(np.argmax(errs))
+    assert errs.max() <= 1e-8, (worst, ws[worst].n, ws[worst].order, errs.max())
     work = [w.order * w.n ** 3 for w in ws]
     picks = [int(np.argmin(work)), int(np.argsort(work)[len(ws) // 2]), int(np.argmax(work)), 303]
     for i in picks:

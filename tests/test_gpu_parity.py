@@ -1,7 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the sequential FP64 oracle.
 
 Bars: FP64 path <= 1e-12 relative L2 (delta form and lagged order change only rounding);
-mixed BF16x3 path <= 1e-8 relative L2.
+mixed BF16x3 path <= 1e-8 relative L2 (the contract). With two refinement passes the mixed
+path lands at the FP64 rounding level (about 3e-15 against the oracle), so every mixed test
+also holds a regression bar near that level (MIXED_TIGHT): a refinement pass or epilogue that
+lost accuracy would fail it long before it reached the contract bar.
 """
 import numpy as np
 import pytest
@@ -12,6 +15,11 @@ from paper_1209_4297_gb300 import Integrator, RidcError
 from tests.gpu_util import need_cuda, rel_l2
 
 pytestmark = pytest.mark.gpu
+
+# regression bar of the mixed path with two refinement passes, against the FP64 oracle: the
+# observed level is 1e-15 to 3e-15; the oracle's own rounding over these short runs is of the
+# same size, so the bar leaves a margin of about 300
+MIXED_TIGHT = 1e-12
 
 
 def _run(w, precision="fp64", order=None, n_refine=2, splits=None):
@@ -128,9 +136,14 @@ def test_mixed_batched_solve_accuracy(kind, n_refine, n):
     with Integrator.from_workload(w, precision="mixed_bf16x3", n_refine=n_refine) as it:
         got = it.solve_planes(r)
     bar = {0: 1e-4, 1: 1e-7, 2: 1e-9}[n_refine]
+    # regression bars near the observed levels: one pass 7e-6 to 1e-5 (FP32 accumulation in
+    # the tensor cores), one refinement about 2e-10, two refinements the FP64 floor (< 4e-15)
+    tight = {0: 4e-5, 1: 3e-9, 2: 1e-13}[n_refine]
     for p in range(planes):
         want = prob.solve(np.stack([r[p]] * S), w.dt)[p % S]
-        assert rel_l2(got[p], want) <= bar, (p, rel_l2(got[p], want))
+        err = rel_l2(got[p], want)
+        assert err <= bar, (p, err)
+        assert err <= tight, (p, err)
 
 
 def test_gray_scott_mixed_matches_oracle_768():
@@ -138,6 +151,7 @@ def test_gray_scott_mixed_matches_oracle_768():
     got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, w.order)
     assert rel_l2(got, ref) <= 1e-8
+    assert rel_l2(got, ref) <= MIXED_TIGHT
 
 
 def test_gray_scott_mixed_matches_oracle_256():
@@ -146,6 +160,7 @@ def test_gray_scott_mixed_matches_oracle_256():
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4, all_levels=True)
     for j in range(4):
         assert rel_l2(levels[j][0], ref[j]) <= 1e-8, j
+        assert rel_l2(levels[j][0], ref[j]) <= MIXED_TIGHT, j
 
 
 def test_dirichlet_mixed_matches_oracle_256():
@@ -153,6 +168,7 @@ def test_dirichlet_mixed_matches_oracle_256():
     got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4)
     assert rel_l2(got, ref) <= 1e-8
+    assert rel_l2(got, ref) <= MIXED_TIGHT
 
 
 # ---------------------------------------------------------------- errors
@@ -185,6 +201,7 @@ def test_mixed_batched_solve_1024_many_tiles_per_cta():
     for p in range(8):
         want = prob.solve(np.stack([r[p]] * 2), w.dt)[p % 2]
         assert rel_l2(got[p], want) <= 1e-9, p
+        assert rel_l2(got[p], want) <= 1e-13, (p, rel_l2(got[p], want))
 
 
 def test_gray_scott_1024_fp64_full_size_truncated():
@@ -203,6 +220,7 @@ def test_gray_scott_2048_mixed_full_size_truncated():
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4, all_levels=True)
     for j in range(4):
         assert rel_l2(levels[j][0], ref[j]) <= 1e-8, j
+        assert rel_l2(levels[j][0], ref[j]) <= MIXED_TIGHT, j
 
 
 def test_dirichlet_4096_mixed_full_size_truncated():
@@ -211,6 +229,19 @@ def test_dirichlet_4096_mixed_full_size_truncated():
     got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4)
     assert rel_l2(got, ref) <= 1e-8
+    assert rel_l2(got, ref) <= MIXED_TIGHT
+
+
+def test_gray_scott_2048_mixed_against_fp64_gpu_over_100_steps():
+    """The benchmark's workload, mixed BF16x3 with two refinements against the FP64 GPU path
+    (itself held to the oracle at 1e-12) over 100 steps: the mixed path stays at the FP64
+    rounding level of the problem (about 1.4e-15 after 100 steps; moving every initial value
+    by one ulp moves the solution by about as much)."""
+    w = inputs.gray_scott_2d(n=2048, nsteps=100)
+    mixed, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    fp64, _, _ = _run(w)
+    assert np.isfinite(mixed).all()
+    assert rel_l2(mixed, fp64) <= 1e-13, rel_l2(mixed, fp64)
 
 
 # ---------------------------------------------------------------- higher orders in 2D (Section
@@ -224,6 +255,7 @@ def test_gray_scott_order8_mixed_512_through_startup():
     assert prog[-1] == 44
     for j in range(8):
         assert rel_l2(levels[j][0], ref[j]) <= 1e-8, j
+        assert rel_l2(levels[j][0], ref[j]) <= MIXED_TIGHT, j
 
 
 def test_dirichlet_order12_mixed_512_through_startup():
@@ -232,6 +264,8 @@ def test_dirichlet_order12_mixed_512_through_startup():
     got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 12)
     assert rel_l2(got, ref) <= 1e-8
+    # order 12's start-up weights (sum |w| up to 30) amplify rounding on both sides
+    assert rel_l2(got, ref) <= 1e-11
 
 
 def test_profiling_samples_every_kth_step():
