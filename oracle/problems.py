@@ -13,6 +13,15 @@ Grids and boundary ghosts (the paper treats 1D periodic and 1D Dirichlet problem
   * 2D Neumann:  cell centres (i + 1/2) h, even ghost u_{-1} = u_0, u_N = u_{N-1}.
   * 2D Dirichlet: cell centres, odd ghost u_{-1} = -u_0, u_N = -u_{N-1} (zero on the wall).
 Arrays are [x] in 1D and [species][y][x] in 2D.
+
+Extended precision (1D problems, dtype=np.longdouble): the same problem with its constants
+and every operation in long double. The FP64 parameters (a, nu and h = 1/N rounded to FP64)
+are converted exactly, so a long-double run evaluates the very algorithm the FP64 oracle runs
+with a smaller rounding unit. Its implicit solve is mixed-precision iterative refinement
+(Wilkinson): an FP64 LU solve, then `refine_passes` passes of x += LU^-1 (r - (I - dt D) x)
+with the residual formed in long double. Each pass shrinks the error by about
+cond(I - dt D) * 2^-53, so three passes reach the long-double rounding level for
+cond <= 1e4 (mu = nu dt / h^2 up to about 2500).
 """
 from __future__ import annotations
 
@@ -21,12 +30,40 @@ import scipy.fft
 import scipy.linalg
 
 
-class AdvDiff1DPeriodic:
+class _Solve1D:
+    """Dense LU solve of (I - dt D) for the 1D problems, with the extended-precision
+    refinement described in the module docstring when the right-hand side is long double."""
+    refine_passes = 3
+
+    def _scalar(self, v):
+        # FP64 problems keep Python floats (the oracle's arithmetic); extended ones convert
+        # the FP64 value exactly
+        return float(v) if self.dtype == np.float64 else self.dtype.type(float(v))
+
+    def _solve64(self, r: np.ndarray, dt: float) -> np.ndarray:
+        # dense LU with partial pivoting of I - dt D, factored once per dt (in FP64)
+        if dt not in self._lu:
+            self._lu[dt] = scipy.linalg.lu_factor(np.eye(self.n) - dt * self.matrix_D())
+        return scipy.linalg.lu_solve(self._lu[dt], r)
+
+    def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
+        if r.dtype == np.float64:
+            return self._solve64(r, dt)
+        x = self._solve64(r.astype(np.float64), dt).astype(r.dtype)
+        for _ in range(self.refine_passes):
+            res = r - (x - dt * self.D(x))
+            x = x + self._solve64(res.astype(np.float64), dt).astype(r.dtype)
+        return x
+
+
+class AdvDiff1DPeriodic(_Solve1D):
     """u_t + a u_x = nu u_xx on periodic [0,1): f^N = -a (u_{i+1} - u_{i-1}) / (2h), D = nu L."""
 
-    def __init__(self, n: int, a: float, nu: float):
-        self.n, self.a, self.nu = n, float(a), float(nu)
-        self.h = 1.0 / n
+    def __init__(self, n: int, a: float, nu: float, dtype=np.float64):
+        self.dtype = np.dtype(dtype)
+        self.n = n
+        self.a, self.nu = self._scalar(a), self._scalar(nu)
+        self.h = self._scalar(1.0 / n)
         self._lu: dict[float, tuple] = {}
 
     def fN(self, u: np.ndarray) -> np.ndarray:
@@ -36,19 +73,14 @@ class AdvDiff1DPeriodic:
         return self.nu * (np.roll(u, -1) - 2.0 * u + np.roll(u, 1)) / self.h ** 2
 
     def matrix_D(self) -> np.ndarray:
+        """D as a dense FP64 matrix (the circulant of the periodic second difference)."""
         n = self.n
         L = np.zeros((n, n))
         for i in range(n):
             L[i, i] = -2.0
             L[i, (i + 1) % n] += 1.0
             L[i, (i - 1) % n] += 1.0
-        return self.nu * L / self.h ** 2
-
-    def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
-        # dense LU with partial pivoting of the circulant I - dt D, factored once per dt
-        if dt not in self._lu:
-            self._lu[dt] = scipy.linalg.lu_factor(np.eye(self.n) - dt * self.matrix_D())
-        return scipy.linalg.lu_solve(self._lu[dt], r)
+        return float(self.nu) * L / float(self.h) ** 2
 
 
 class AdvDiff1DUpwindPeriodic(AdvDiff1DPeriodic):
@@ -63,20 +95,23 @@ class AdvDiff1DUpwindPeriodic(AdvDiff1DPeriodic):
         return -self.a * (np.roll(u, -1) - u) / self.h
 
 
-class Burgers1DDirichlet:
+class Burgers1DDirichlet(_Solve1D):
     """Viscous Burgers, u_t + (u^2 / 2)_x = nu u_xx on [0,1] with u(0) = u(1) = 0 (Section
     IV-B). Unknowns at the n interior nodes x_i = i h, h = 1/(n+1), i = 1..n. The paper's
     numerical flux f_{i+1/2} = (u_{i+1}^2 + u_i^2) / 2 gives
         f^N_i = -(1/2) (f_{i+1/2} - f_{i-1/2}) / h,
     and D = nu L with the centred second difference; the wall values are the zero ghosts."""
 
-    def __init__(self, n: int, nu: float):
-        self.n, self.nu = n, float(nu)
-        self.h = 1.0 / (n + 1)
+    def __init__(self, n: int, nu: float, dtype=np.float64):
+        self.dtype = np.dtype(dtype)
+        self.n = n
+        self.nu = self._scalar(nu)
+        self.h = self._scalar(1.0 / (n + 1))
         self._lu: dict[float, tuple] = {}
 
     def _ghosted(self, u: np.ndarray) -> np.ndarray:
-        return np.concatenate(([0.0], u, [0.0]))
+        z = np.zeros(1, dtype=u.dtype)
+        return np.concatenate((z, u, z))
 
     def fN(self, u: np.ndarray) -> np.ndarray:
         g = self._ghosted(u)
@@ -88,15 +123,10 @@ class Burgers1DDirichlet:
         return self.nu * (g[2:] - 2.0 * g[1:-1] + g[:-2]) / self.h ** 2
 
     def matrix_D(self) -> np.ndarray:
+        """D as a dense FP64 matrix (zero wall ghosts)."""
         n = self.n
         L = -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
-        return self.nu * L / self.h ** 2
-
-    def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
-        # dense LU with partial pivoting of I - dt D, factored once per dt
-        if dt not in self._lu:
-            self._lu[dt] = scipy.linalg.lu_factor(np.eye(self.n) - dt * self.matrix_D())
-        return scipy.linalg.lu_solve(self._lu[dt], r)
+        return float(self.nu) * L / float(self.h) ** 2
 
 
 def _pad(u: np.ndarray, odd: bool) -> np.ndarray:
@@ -186,14 +216,16 @@ class AdvDiff2DDirichlet(_Separable2D):
         return -self.a * ux - self.b * uy
 
 
-def from_workload(w) -> object:
-    """Build the oracle problem for an inputs.Workload."""
+def from_workload(w, dtype=np.float64) -> object:
+    """Build the oracle problem for an inputs.Workload (dtype: 1D problems only)."""
     if w.kind == "adv_diff_1d_periodic":
-        return AdvDiff1DPeriodic(w.n, w.a, w.nu[0])
+        return AdvDiff1DPeriodic(w.n, w.a, w.nu[0], dtype)
     if w.kind == "adv_diff_1d_upwind_periodic":
-        return AdvDiff1DUpwindPeriodic(w.n, w.a, w.nu[0])
+        return AdvDiff1DUpwindPeriodic(w.n, w.a, w.nu[0], dtype)
     if w.kind == "burgers_1d_dirichlet":
-        return Burgers1DDirichlet(w.n, w.nu[0])
+        return Burgers1DDirichlet(w.n, w.nu[0], dtype)
+    if np.dtype(dtype) != np.float64:
+        raise ValueError("extended precision is provided for the 1D problems only")
     if w.kind == "gray_scott_2d_neumann":
         return GrayScott2DNeumann(w.n, w.nu[0], w.nu[1], w.F, w.k)
     if w.kind == "adv_diff_2d_dirichlet":

@@ -62,3 +62,11 @@ def stencil(j: int, n: int) -> tuple[int, int]:
     """(b, m): first node index b and interval offset m of corrector j's step n -> n+1."""
     b = max(0, n + 1 - j)
     return b, n - b
+
+
+def stencil_nodes(K: int, n: int) -> tuple[int, int]:
+    """(b, m) of a K-node stencil for the step n -> n+1: the window t_b..t_{b+K-1} ends at
+    t_{n+1} once n >= K-2, and is the fixed start-up window t_0..t_{K-1} before that. The
+    weights are those of `lagrange_weights(K - 1, m)`. stencil(j, n) is the case K = j + 1."""
+    b = max(0, n + 2 - K)
+    return b, n - b

@@ -2,6 +2,9 @@
 grids each path accepts (and the first ones it refuses), the degenerate orders, exact fixed
 points, and non-finite data.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -9,6 +12,8 @@ import inputs
 import oracle
 from paper_1209_4297_gb300 import Batch, Integrator, RidcError
 from tests.gpu_util import need_cuda, rel_l2
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
 
 pytestmark = pytest.mark.gpu
 
@@ -109,6 +114,22 @@ def test_largest_1d_grids(n, order, nsteps):
         it.advance(nsteps)
         got = it.solution()
     assert rel_l2(got, _oracle(w, nsteps, order)) <= (1e-12 if order <= 8 else 5e-12)
+
+
+def test_order12_against_the_extended_precision_solution():
+    """RIDC-12 at mu = 1 (n = 256, 70 steps): both the FP64 oracle and the CUDA path sit about
+    2-3e-12 from the long-double evaluation of the same algorithm (stored by
+    tests/golden/make_extended.py; the oracle's distance is bounded on the CPU by
+    tests/test_oracle_extended.py), which is why order 12 is compared with the oracle at 5e-12."""
+    need_cuda()
+    import make_extended
+    w, _ = make_extended.cases()["order12_n256"]
+    with Integrator.from_workload(w, order=12) as it:
+        it.set_initial(w.u0)
+        it.advance(w.nsteps)
+        got = it.solution()
+    assert rel_l2(got, make_extended.load("order12_n256")) <= 3.5e-12
+    assert rel_l2(got, _oracle(w, w.nsteps, 12)) <= 5e-12
 
 
 @pytest.mark.parametrize("kind,n,order,prec", [
