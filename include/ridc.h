@@ -86,6 +86,17 @@ typedef enum {
     RIDC_MIXED_FP16X3 = 3
 } ridc_precision;
 
+typedef enum {
+    /* first-order IMEX step (forward-backward Euler), eq. (pred): RIDC-FBE, Theorem 1      */
+    RIDC_PRED_FBE = 0,
+    /* the third-order IMEX additive Runge-Kutta method of Section II (five stages, four
+       implicit with diagonals 1/2, 2/3, 2, 1)                                              */
+    RIDC_PRED_ARK3 = 1,
+    /* the fourth-order IMEX additive Runge-Kutta method of Section II (seven stages, six
+       implicit, every diagonal 1/2 except the last, 2/3)                                   */
+    RIDC_PRED_ARK4 = 2
+} ridc_predictor;
+
 typedef struct {
     int    kind;          /* ridc_kind                                                      */
     double a, b;          /* advection velocity along x and y (unused by Gray-Scott)        */
@@ -96,6 +107,12 @@ typedef struct {
                              corrected level, all levels restart from its solution and re-enter
                              start-up; 0 = no restarts. Single integrators only (a batch
                              requires 0).                                                    */
+    int    predictor;     /* ridc_predictor of level 0 (0 = RIDC-FBE). With a p0-th order ARK
+                             predictor and order-1 first-order correctors the method has order
+                             p0 + order - 1 (Theorem 2); corrector j then integrates with
+                             p0 + j quadrature nodes (the window of Section III-C, widened),
+                             and p0 + order - 1 <= 12 is required. Single integrators only (a
+                             batch requires RIDC_PRED_FBE).                                  */
 } ridc_problem;
 
 typedef struct {
@@ -114,8 +131,9 @@ typedef struct ridc_ctx* ridc_handle;   /* opaque; owned by the library         
 /* Create an integrator of order `order` (predictor + order-1 correctors, Theorem 1:
  * local error O(dt^{order+1})) with uniform step dt (Section III-C assumes uniform steps).
  *   nu      : diffusion coefficient per species (1 value, or 2 for Gray-Scott), > 0.
- *   order   : 1 <= order <= 12 (Section III-E: 8th and 12th order stay free of the Runge
- *             phenomenon in double precision).
+ *   order   : levels (predictor + order-1 correctors), 1 <= order <= 12 (Section III-E: 8th
+ *             and 12th order stay free of the Runge phenomenon in double precision); with an
+ *             ARK predictor of order p0 (problem->predictor), p0 + order - 1 <= 12.
  *   stream  : cudaStream_t used for all device work, or NULL for the legacy default stream.
  * Allocates the level-history rings and the solver tables on the current CUDA device.
  * The state is undefined until ridc_set_initial(). On error *out is untouched.            */
@@ -281,6 +299,13 @@ int ridc_schedule_plan(int order, long nsteps, unsigned* active, size_t cap, siz
  * reachable progress (negative, a level ahead of the one below, or the top past nsteps). */
 int ridc_schedule_plan_from(int order, const long* start, long nsteps, unsigned* active,
                             size_t cap, size_t* count);
+
+/* ridc_schedule_plan_from for a predictor of order p0 (ridc_predictor): level j may step from
+ * n once level j-1 holds index max(n+1, p0+j-1), the last node of its p0+j-node stencil, and
+ * lower levels keep p0+j+2 ring slots. start == NULL: a fresh run. With RIDC_PRED_FBE this is
+ * ridc_schedule_plan_from.                                                                    */
+int ridc_schedule_plan_predictor(int order, int predictor, const long* start, long nsteps,
+                                 unsigned* active, size_t cap, size_t* count);
 
 /* Quadrature weights w[j][m][i] of the corrector (Section III-C), FP64, computed exactly
  * in rational arithmetic and rounded: node i of the stencil t_b..t_{b+j}, interval

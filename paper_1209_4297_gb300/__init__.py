@@ -6,8 +6,10 @@ does not load the library; the first call does, and raises if the library is mis
 """
 from .binding import (Batch, Integrator, RidcError, debug_fail_alloc, error_string, lib,
                       quadrature_weights, set_allocator, use_torch_allocator,
-                      schedule_plan, schedule_plan_from, LIB_PATH, KERNELS)
+                      schedule_plan, schedule_plan_from, schedule_plan_predictor, LIB_PATH,
+                      KERNELS, PREDICTORS)
 
 __all__ = ["Batch", "Integrator", "RidcError", "debug_fail_alloc", "error_string", "lib",
            "quadrature_weights", "set_allocator", "use_torch_allocator",
-           "schedule_plan", "schedule_plan_from", "LIB_PATH", "KERNELS"]
+           "schedule_plan", "schedule_plan_from", "schedule_plan_predictor", "LIB_PATH",
+           "KERNELS", "PREDICTORS"]

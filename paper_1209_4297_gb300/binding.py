@@ -20,6 +20,7 @@ KINDS = {"adv_diff_1d_periodic": 0, "gray_scott_2d_neumann": 1, "adv_diff_2d_dir
          "adv_diff_1d_upwind_periodic": 3, "burgers_1d_dirichlet": 4}
 KINDS_1D = ("adv_diff_1d_periodic", "adv_diff_1d_upwind_periodic", "burgers_1d_dirichlet")
 PRECISIONS = {"fp64": 0, "mixed_bf16x3": 1, "fp32_solve": 2, "mixed_fp16x3": 3}
+PREDICTORS = {"fbe": 0, "ark3": 1, "ark4": 2}
 KERNELS = {"rhs": 0, "gemm_tc": 1, "gemm_f64": 2, "residual": 3, "finalize": 4, "ridc1d": 5,
            "split_f16": 6}
 
@@ -33,7 +34,7 @@ class RidcError(RuntimeError):
 class Problem(ctypes.Structure):
     _fields_ = [("kind", c_int), ("a", c_double), ("b", c_double), ("F", c_double),
                 ("k", c_double), ("precision", c_int), ("n_refine", c_int),
-                ("restart_every", c_int)]
+                ("restart_every", c_int), ("predictor", c_int)]
 
 
 class Grid(ctypes.Structure):
@@ -76,6 +77,8 @@ def lib() -> ctypes.CDLL:
         "ridc_load_state": (i, [vp, vp, sz]),
         "ridc_schedule_plan": (i, [i, lg, POINTER(c_uint), sz, POINTER(sz)]),
         "ridc_schedule_plan_from": (i, [i, POINTER(lg), lg, POINTER(c_uint), sz, POINTER(sz)]),
+        "ridc_schedule_plan_predictor": (i, [i, i, POINTER(lg), lg, POINTER(c_uint), sz,
+                                             POINTER(sz)]),
         "ridc_quadrature_weights": (i, [i, POINTER(c_double), sz]),
         "ridc_set_profiling": (i, [vp, i]),
         "ridc_get_kernel_stats": (i, [vp, i, POINTER(lg), POINTER(d)]),
@@ -152,6 +155,19 @@ def schedule_plan_from(order: int, start, nsteps: int) -> np.ndarray:
     return np.array(out[:cnt.value], dtype=np.uint32)
 
 
+def schedule_plan_predictor(order: int, predictor: str, nsteps: int, start=None) -> np.ndarray:
+    """Masks of the lock-step schedule with predictor 'fbe', 'ark3' or 'ark4' (corrector j
+    reads a p0 + j node stencil), from progress `start` (None: a fresh run)."""
+    st = None if start is None else (c_long * order)(*[int(v) for v in start])
+    cnt = c_size_t(0)
+    L = lib()
+    L.ridc_schedule_plan_predictor(order, PREDICTORS[predictor], st, nsteps, None, 0, byref(cnt))
+    out = (c_uint * max(cnt.value, 1))()
+    _check(L.ridc_schedule_plan_predictor(order, PREDICTORS[predictor], st, nsteps, out,
+                                          cnt.value, byref(cnt)), "ridc_schedule_plan_predictor")
+    return np.array(out[:cnt.value], dtype=np.uint32)
+
+
 def debug_fail_alloc(k: int) -> None:
     """Test hook: the k-th device allocation from now on fails (0 disarms)."""
     _check(lib().ridc_debug_fail_alloc(k), "ridc_debug_fail_alloc")
@@ -218,11 +234,13 @@ class Integrator:
 
     def __init__(self, kind: str, n: int, nu, dt: float, order: int, *, a: float = 0.0,
                  b: float = 0.0, F: float = 0.0, k: float = 0.0, precision: str = "fp64",
-                 n_refine: int = 2, restart_every: int = 0, stream=None):
+                 n_refine: int = 2, restart_every: int = 0, predictor: str = "fbe",
+                 stream=None):
         L = lib()
         self._h = c_void_p(None)
         nu = np.atleast_1d(np.asarray(nu, dtype=np.float64))
-        pr = Problem(KINDS[kind], a, b, F, k, PRECISIONS[precision], n_refine, restart_every)
+        pr = Problem(KINDS[kind], a, b, F, k, PRECISIONS[precision], n_refine, restart_every,
+                     PREDICTORS[predictor])
         gr = Grid(1 if kind in KINDS_1D else 2, n)
         if stream is None:
             stream = _current_stream()
@@ -235,12 +253,13 @@ class Integrator:
 
     @classmethod
     def from_workload(cls, w, precision: str = "fp64", n_refine: int = 2, stream=None,
-                      order: int | None = None, restart_every: int | None = None):
+                      order: int | None = None, restart_every: int | None = None,
+                      predictor: str = "fbe"):
         """Integrator for an inputs.Workload; restart_every defaults to the workload's."""
         return cls(w.kind, w.n, w.nu, w.dt, order or w.order, a=w.a, b=w.b, F=w.F, k=w.k,
                    precision=precision, n_refine=n_refine,
                    restart_every=(getattr(w, "restart_every", 0) if restart_every is None
-                                  else restart_every), stream=stream)
+                                  else restart_every), predictor=predictor, stream=stream)
 
     def close(self) -> None:
         if self._h:
@@ -348,7 +367,7 @@ class Batch:
         self._h = c_void_p(None)
         n = len(workloads)
         probs = (Problem * n)(*[Problem(KINDS[w.kind], w.a, w.b, 0.0, 0.0, PRECISIONS["fp32_solve"],
-                                        n_refine, 0) for w in workloads])
+                                        n_refine, 0, 0) for w in workloads])
         grids = (Grid * n)(*[Grid(2, w.n) for w in workloads])
         nu = (c_double * n)(*[w.nu[0] for w in workloads])
         dt = (c_double * n)(*[w.dt for w in workloads])

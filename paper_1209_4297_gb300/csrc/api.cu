@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <new>
 #include <unordered_map>
@@ -118,33 +119,146 @@ int cuda_status(cudaError_t e) {
 // ------------------------------------------------------------------------------------------
 // lock-step schedule (Section III-E)
 // ------------------------------------------------------------------------------------------
+// Corrector j reads a K_j = p0 + j node stencil of level j-1 (Section III-C with p0 = 1 for
+// the FBE predictor; a p0-th order predictor needs one node per order gained, Theorem 2).
 // Level j may take its step n -> n+1 (n = p[j]) when
 //   (a) it has not reached its target: the top level stops at target_top, the lower levels
-//       at max(target_top, P-1), the last index a start-up stencil of the top level reads;
-//   (b) its inputs exist: level j-1 holds index max(n+1, j) (the quadrature stencil of
-//       Section III-C ends at t_{n+1}, or at t_j while n < j-1);
-//   (c) (lower levels only) writing index n+1 into its ring of j+3 slots does not evict a
-//       value level j+1 still reads: level j+1's next stencil starts at max(0, p[j+1]-j),
-//       so n - max(0, p[j+1]-j) <= j+1.
+//       at max(target_top, K_{P-1} - 1), the last index a start-up stencil of the top level
+//       reads;
+//   (b) its inputs exist: level j-1 holds index max(n+1, K_j - 1) (the stencil ends at
+//       t_{n+1}, or at t_{K_j - 1} during start-up);
+//   (c) (lower levels only) writing index n+1 into its ring of K_{j+1} + 1 slots does not
+//       evict a value level j+1 still reads: level j+1's next stencil starts at
+//       b = max(0, p[j+1] + 2 - K_{j+1}), so n - b <= K_{j+1} - 1.
 // All tests use the values from before the step, so the levels of one step are independent.
-// Rule (b) alone gives the paper's start-up waits j(j+1)/2; rule (c) holds lower levels
-// back so that memory stays at j+3 fields per level, after which every level lags the one
-// below by exactly one step.
-unsigned plan_step(int P, const long* p, long target_top) {
+// Rule (b) alone gives the paper's start-up waits j(j+1)/2 (p0 = 1); rule (c) holds lower
+// levels back so that memory stays at K_{j+1} + 1 fields per level, after which every level
+// lags the one below by exactly one step.
+unsigned plan_step(int P, const long* p, long target_top, int p0) {
   if (p[P - 1] >= target_top) return 0;   // the run is complete once the top level arrives
-  const long target_low = std::max(target_top, (long)(P - 1));
+  const long target_low = std::max(target_top, (long)(p0 + P - 2));
   unsigned mask = 0;
   for (int j = 0; j < P; ++j) {
     const long tgt = (j == P - 1) ? target_top : target_low;
     bool ok = p[j] < tgt;
-    if (ok && j > 0) ok = p[j - 1] >= std::max(p[j] + 1, (long)j);
-    if (ok && j < P - 1) ok = p[j] - std::max(0L, p[j + 1] - j) <= j + 1;
+    if (ok && j > 0) ok = p[j - 1] >= std::max(p[j] + 1, (long)(p0 + j - 1));
+    if (ok && j < P - 1) ok = p[j] - std::max(0L, p[j + 1] + 1 - p0 - j) <= p0 + j;
     if (ok) mask |= 1u << j;
   }
   return mask;
 }
 
-static int ring_cap(int P, int j) { return j < P - 1 ? j + 3 : 2; }
+static int ring_cap(int P, int j, int p0) { return j < P - 1 ? p0 + j + 2 : 2; }
+
+// ------------------------------------------------------------------------------------------
+// ARK predictors (Section II): the third- and fourth-order IMEX additive Runge-Kutta methods,
+// as exact rationals. Row i of A^S holds a^S_i0..a^S_ii, row i of A^N a^N_i0..a^N_i,i-1. The
+// third-order tableau is garbled in the paper's source; it is read stage by stage (five
+// stages, diagonals 0, 1/2, 2/3, 2, 1), which satisfies every additive-RK order condition to
+// order 3. Both methods are stiffly accurate: the last stage is the new solution.
+// ------------------------------------------------------------------------------------------
+struct Rat {
+  long long p, q;   // p / q, q > 0
+};
+static long long gcdll(long long a, long long b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b) { const long long t = a % b; a = b; b = t; }
+  return a ? a : 1;
+}
+static Rat rat(long long p, long long q) {
+  if (q < 0) { p = -p; q = -q; }
+  const long long g = gcdll(p, q);
+  return {p / g, q / g};
+}
+static Rat radd(Rat a, Rat b) { return rat(a.p * b.q + b.p * a.q, a.q * b.q); }
+static Rat rneg(Rat a) { return {-a.p, a.q}; }
+static double rdbl(Rat a) { return (double)a.p / (double)a.q; }   // both exact: one rounding
+
+struct Tableau {
+  int s;
+  Rat AS[kMaxStages][kMaxStages];
+  Rat AN[kMaxStages][kMaxStages];
+};
+
+static void tab_row(Rat* row, std::initializer_list<Rat> v) {
+  int k = 0;
+  for (const Rat& x : v) row[k++] = x;
+}
+
+static bool get_tableau(int pred, Tableau* t) {
+  *t = Tableau{};
+  for (auto& r : t->AS) for (auto& x : r) x = {0, 1};
+  for (auto& r : t->AN) for (auto& x : r) x = {0, 1};
+  const Rat z = {0, 1};
+  if (pred == RIDC_PRED_ARK3) {
+    t->s = 5;
+    tab_row(t->AS[1], {z, rat(1, 2)});
+    tab_row(t->AS[2], {rat(1, 4), rat(-5, 12), rat(2, 3)});
+    tab_row(t->AS[3], {rat(2, 1), rat(-7, 2), rat(1, 2), rat(2, 1)});
+    tab_row(t->AS[4], {rat(1, 6), z, rat(2, 3), rat(-5, 6), rat(1, 1)});
+    tab_row(t->AN[1], {rat(1, 2)});
+    tab_row(t->AN[2], {rat(1, 4), rat(1, 4)});
+    tab_row(t->AN[3], {z, rat(1, 1), z});
+    tab_row(t->AN[4], {rat(1, 6), z, rat(2, 3), rat(1, 6)});
+    return true;
+  }
+  if (pred == RIDC_PRED_ARK4) {
+    t->s = 7;
+    tab_row(t->AS[1], {rat(-1, 6), rat(1, 2)});
+    tab_row(t->AS[2], {rat(1, 6), rat(-1, 3), rat(1, 2)});
+    tab_row(t->AS[3], {rat(3, 8), rat(-3, 8), z, rat(1, 2)});
+    tab_row(t->AS[4], {rat(1, 8), z, rat(3, 8), rat(-1, 2), rat(1, 2)});
+    tab_row(t->AS[5], {rat(-1, 2), z, rat(3, 1), rat(-3, 1), rat(1, 1), rat(1, 2)});
+    tab_row(t->AS[6], {rat(1, 6), z, z, z, rat(2, 3), rat(-1, 2), rat(2, 3)});
+    tab_row(t->AN[1], {rat(1, 3)});
+    tab_row(t->AN[2], {rat(1, 6), rat(1, 6)});
+    tab_row(t->AN[3], {rat(1, 8), z, rat(3, 8)});
+    tab_row(t->AN[4], {rat(1, 8), z, rat(3, 8), z});
+    tab_row(t->AN[5], {rat(1, 2), z, rat(-3, 2), z, rat(2, 1)});
+    tab_row(t->AN[6], {rat(1, 6), z, z, z, rat(2, 3), rat(1, 6)});
+    return true;
+  }
+  return false;
+}
+
+int predictor_order(int pred) {
+  switch (pred) {
+    case RIDC_PRED_FBE: return 1;
+    case RIDC_PRED_ARK3: return 3;
+    case RIDC_PRED_ARK4: return 4;
+    default: return 0;
+  }
+}
+
+int ark_plan(int pred, ArkStage* st, double* coef, int* ncoef) {
+  Tableau t;
+  if (!get_tableau(pred, &t)) return 0;
+  for (int i = 1; i < t.s; ++i) {
+    const Rat aii = t.AS[i][i];
+    // operator of this stage: an existing coefficient or a new one
+    int k = 0;
+    while (k < *ncoef && coef[k] != rdbl(aii)) ++k;
+    if (k == *ncoef) {
+      if (*ncoef >= kMaxCoefs) return 0;
+      coef[(*ncoef)++] = rdbl(aii);
+    }
+    ArkStage& S = st[i];
+    S = ArkStage{};
+    S.coef = k;
+    for (int j = 0; j < i; ++j) {
+      // F_j carries a^S_ij, KN_j carries a^N_ij - a^S_ij; stage 0 adds a_ii K^S_0
+      Rat cF = t.AS[i][j], cN = radd(t.AN[i][j], rneg(t.AS[i][j]));
+      if (j == 0) {
+        cF = radd(cF, aii);
+        cN = radd(cN, rneg(aii));
+      }
+      if (cF.p != 0) { S.src[S.nterms] = 2 * j; S.w[S.nterms++] = rdbl(cF); }
+      if (cN.p != 0) { S.src[S.nterms] = 2 * j + 1; S.w[S.nterms++] = rdbl(cN); }
+    }
+  }
+  return t.s;
+}
 
 // ------------------------------------------------------------------------------------------
 // quadrature weights: exact rationals (Section III-C), rounded once
@@ -312,11 +426,17 @@ static int build_tables_2d(Ctx* c) {
     }
     RIDC_TRY(upload(c, &c->Q, Qa));
     RIDC_TRY(upload(c, &c->Qt, Qb));
-    std::vector<double> inv((size_t)c->S * n * n);
-    for (int s = 0; s < c->S; ++s)
-      for (int ky = 0; ky < n; ++ky)
-        for (int kx = 0; kx < n; ++kx)
-          inv[((size_t)s * n + ky) * n + kx] = 1.0 / (1.0 - c->dt * c->nu[s] * (ls[ky] + ls[kx]));
+    // one table per solve operator (I - a dt nu_s L): a = 1, then the ARK diagonals;
+    // (a dt) nu_s with a = 1 is exactly dt nu_s
+    std::vector<double> inv((size_t)c->ncoef * c->S * n * n);
+    for (int k = 0; k < c->ncoef; ++k)
+      for (int s = 0; s < c->S; ++s) {
+        const double adtnu = (c->coef[k] * c->dt) * c->nu[s];
+        double* t = inv.data() + ((size_t)k * c->S + s) * n * n;
+        for (int ky = 0; ky < n; ++ky)
+          for (int kx = 0; kx < n; ++kx)
+            t[(size_t)ky * n + kx] = 1.0 / (1.0 - adtnu * (ls[ky] + ls[kx]));
+      }
     RIDC_TRY(upload(c, &c->inv_den, inv));
   } else {
     // parity split: Q[n-1-x][k] = (-1)^k Q[x][k]; Qe[x'][k'] = Q[x'][2k'], Qo[x'][k'] = Q[x'][2k'+1]
@@ -368,7 +488,7 @@ static int build_tables_1d(Ctx* c) {
   const double mu = c->nu[0] * c->dt / (c->h * c->h);
   const double rho = 2.0 * mu / (1.0 + 2.0 * mu + std::sqrt(1.0 + 4.0 * mu));
   const double s = rho / mu;
-  std::vector<double> tri((size_t)npad + 3 + (size_t)n + (size_t)c->P * c->P * c->P, 0.0);
+  std::vector<double> tri((size_t)npad + 3 + (size_t)n + (size_t)c->W * c->W * c->W, 0.0);
   for (int k = 0; k <= npad; ++k) tri[k] = std::pow(rho, (double)k);
   tri[npad + 2] = s;
   if (is_1d_dirichlet(c->kind)) {
@@ -383,7 +503,7 @@ static int build_tables_1d(Ctx* c) {
   } else {
     tri[npad + 1] = 1.0 / (1.0 - std::pow(rho, (double)n));
   }
-  fill_weights(c->P, tri.data() + npad + 3 + n);
+  fill_weights(c->W, tri.data() + npad + 3 + n);
   return upload(c, &c->tri, tri);
 }
 
@@ -397,6 +517,8 @@ static void free_all(Ctx* c) {
   f(c->Q); f(c->Qt); f(c->inv_den); f(c->lam_f); f(c->Bfh); f(c->Bfl); f(c->Bbh); f(c->Bbl);
   f(c->xs); f(c->pmax);
   f(c->tri); f(c->sched_dev); f(c->p_dev); f(c->err_dev);
+  for (int i = 0; i < kMaxStages; ++i) { f(c->stF[i]); f(c->stKN[i]); }
+  f(c->stY);
   if (c->pinned) cudaFreeHost(c->pinned);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
 }
@@ -421,13 +543,30 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
 
   const long n = c->n;
   c->plane = (c->dim == 1) ? n : (long)c->S * n * n;
-  std::vector<double> w((size_t)order * order * order);
-  fill_weights(order, w.data());
+  c->pred = pr->predictor;
+  c->p0 = predictor_order(pr->predictor);
+  c->W = c->p0 + order - 1;
+  c->ncoef = 1;
+  c->coef[0] = 1.0;
+  c->nstages = 1;
+  if (c->pred != RIDC_PRED_FBE) {
+    c->nstages = ark_plan(c->pred, c->stage, c->coef, &c->ncoef);
+    if (c->nstages < 2) return RIDC_ERR_ARG;
+  }
+  std::vector<double> w((size_t)c->W * c->W * c->W);
+  fill_weights(c->W, w.data());
   c->wq = w;
 
   const size_t pb = (size_t)c->plane * sizeof(double);
+  // ARK stages 1..s-2 keep F and f^N of their stage value for the later stages; the stage
+  // value itself is written to one scratch field
+  for (int i = 1; i + 1 < c->nstages; ++i) {
+    RIDC_CUDA(dev_malloc((void**)&c->stF[i], pb));
+    RIDC_CUDA(dev_malloc((void**)&c->stKN[i], pb));
+  }
+  if (c->nstages > 1) RIDC_CUDA(dev_malloc((void**)&c->stY, pb));
   for (int j = 0; j < order; ++j) {
-    c->cap[j] = ring_cap(order, j);
+    c->cap[j] = ring_cap(order, j, c->p0);
     RIDC_CUDA(dev_malloc((void**)&c->eta[j], c->cap[j] * pb));
     RIDC_CUDA(dev_malloc((void**)&c->fN[j], c->cap[j] * pb));
     if (j < order - 1 || j == 0) RIDC_CUDA(dev_malloc((void**)&c->Fq[j], c->cap[j] * pb));
@@ -487,6 +626,9 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
   if (pr->kind < 0 || pr->kind > 4) return RIDC_ERR_ARG;
   if (pr->precision != RIDC_FP64 && !is_mixed(pr->precision)) return RIDC_ERR_ARG;
   if (pr->n_refine < 0 || pr->n_refine > 4) return RIDC_ERR_ARG;
+  if (predictor_order(pr->predictor) == 0) return RIDC_ERR_ARG;
+  // the widest quadrature stencil has p0 + order - 1 nodes (at most 12)
+  if (predictor_order(pr->predictor) + order - 1 > kMaxOrder) return RIDC_ERR_UNSUPPORTED;
   const int S = (pr->kind == RIDC_GRAY_SCOTT_2D_NEUMANN) ? 2 : 1;
   for (int s = 0; s < S; ++s)
     if (!(nu[s] > 0.0) || !std::isfinite(nu[s])) return RIDC_ERR_ARG;
@@ -494,6 +636,7 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
       pr->kind == RIDC_BURGERS_1D_DIRICHLET) {
     if (g->dim != 1 || g->n < 8) return RIDC_ERR_ARG;
     if (pr->precision != RIDC_FP64) return RIDC_ERR_UNSUPPORTED;
+    if (pr->predictor != RIDC_PRED_FBE) return RIDC_ERR_UNSUPPORTED;
     // shared-memory rows of the levels one CTA carries
     if (oned_smem_doubles(order, g->n, oned_npad(g->n)) > kOneDMaxSmemDoubles)
       return RIDC_ERR_UNSUPPORTED;
@@ -716,7 +859,83 @@ static int step_2d(Ctx* c, unsigned mask) {
   return rc;
 }
 
+// Level 0's step n -> n+1 with an ARK predictor (Section II), stage by stage: each implicit
+// stage forms its right-hand side from the earlier stages' F and f^N (ArkStage), solves with
+// (I - a_ii dt D) on the same batched solver (per-plane operators), and evaluates F and f^N of
+// its stage value; the last stage is the new solution and goes into level 0's ring. It runs
+// ahead of the correctors' batched step: the levels of one pipeline step are independent.
+static int ark_predictor_step(Ctx* c) {
+  const long n = c->p[0];
+  const double* y = slot_ptr(c, c->eta[0], 0, n);
+  const double* X[2 * kMaxStages] = {nullptr};
+  X[0] = slot_ptr(c, c->Fq[0], 0, n);
+  X[1] = slot_ptr(c, c->fN[0], 0, n);
+  for (int i = 1; i + 1 < c->nstages; ++i) {
+    X[2 * i] = c->stF[i];
+    X[2 * i + 1] = c->stKN[i];
+  }
+  const bool f16 = c->prec == RIDC_MIXED_FP16X3;
+  for (int i = 1; i < c->nstages; ++i) {
+    const ArkStage& st = c->stage[i];
+    RhsArgs ra{};
+    RhsLevel& L = ra.lv[0];
+    L.eta_j = nullptr;
+    for (int t = 0; t < st.nterms; ++t) {
+      L.Fn[t] = X[st.src[t]];
+      L.w[t] = c->dt * st.w[t];
+    }
+    L.nnodes = st.nterms;
+    ra.nlev = 1;
+    ra.combo = 1;
+    ra.plane = c->plane;
+    ra.dt = c->dt;
+    ra.r = c->r;
+    ra.r_hi = (c->prec == RIDC_MIXED_BF16X3) ? c->xh : nullptr;
+    ra.r_lo = (c->prec == RIDC_MIXED_BF16X3) ? c->xl : nullptr;
+    ra.r_stage = f16 ? c->xs : nullptr;
+    ra.pmax = f16 ? c->pmax : nullptr;
+    ra.n = c->n;
+    if (f16) RIDC_TRY(reset_plane_max(c));
+    RIDC_TRY(launch_rhs(c, ra));
+    if (f16) RIDC_TRY(launch_split_f16(c, 0, c->S, 0));
+    for (int q = 0; q < c->S; ++q) c->plane_coef[q] = st.coef;
+    DeltaParts parts;
+    const int rc = solve_planes_dev(c, c->S, true, &parts);
+    for (int q = 0; q < c->S; ++q) c->plane_coef[q] = 0;
+    RIDC_TRY(rc);
+    FinArgs fa{};
+    fa.n = c->n;
+    fa.kind = c->kind;
+    fill_fin_consts(c, &fa);
+    fa.nlev = 1;
+    const bool last = i == c->nstages - 1;
+    FinLevel& Fl = fa.lv[0];
+    Fl.base = y;
+    Fl.d64 = parts.d64;
+    Fl.d32 = parts.d32;
+    Fl.eta = last ? slot_ptr(c, c->eta[0], 0, n + 1) : c->stY;
+    Fl.fN = last ? slot_ptr(c, c->fN[0], 0, n + 1) : c->stKN[i];
+    Fl.F = last ? (c->Fq[0] ? slot_ptr(c, c->Fq[0], 0, n + 1) : nullptr) : c->stF[i];
+    RIDC_TRY(launch_finalize(c, fa));
+  }
+  return RIDC_OK;
+}
+
+static int levels_step_2d(Ctx* c, unsigned mask);
+
 static int step_2d_launch(Ctx* c, unsigned mask) {
+  const bool ark = c->nstages > 1;
+  if (ark && (mask & 1u)) RIDC_TRY(ark_predictor_step(c));
+  const unsigned rest = ark ? (mask & ~1u) : mask;
+  if (rest) RIDC_TRY(levels_step_2d(c, rest));
+  for (int j = 0; j < c->P; ++j)
+    if (mask & (1u << j)) c->p[j]++;
+  return RIDC_OK;
+}
+
+// The FBE predictor (if in the mask) and the correctors of one pipeline step: one fused
+// right-hand-side launch, one batched solve, one finalize launch. Does not advance c->p.
+static int levels_step_2d(Ctx* c, unsigned mask) {
   RhsArgs ra{};
   FinArgs fa{};
   fa.n = c->n;
@@ -740,13 +959,15 @@ static int step_2d_launch(Ctx* c, unsigned mask) {
       L.fN_j = slot_ptr(c, c->fN[j], j, n);
       L.eta_pn = slot_ptr(c, c->eta[j - 1], j - 1, n + 1);
       L.fN_p = slot_ptr(c, c->fN[j - 1], j - 1, n);
-      const long b = std::max(0L, n + 1 - j);
+      // K-node stencil of level j-1 (K = p0 + j): t_b..t_{b+K-1}, interval m = n - b
+      const int K = c->p0 + j, d = K - 1, W = c->W;
+      const long b = std::max(0L, n + 2 - K);
       const long m = n - b;
-      for (int i = 0; i <= j; ++i) {
+      for (int i = 0; i < K; ++i) {
         L.Fn[i] = slot_ptr(c, c->Fq[j - 1], j - 1, b + i);
-        L.w[i] = c->dt * c->wq[((size_t)j * P + m) * P + i];
+        L.w[i] = c->dt * c->wq[((size_t)d * W + m) * W + i];
       }
-      L.nnodes = j + 1;
+      L.nnodes = K;
       base = L.eta_pn;
     }
     FinLevel& Fl = fa.lv[na];
@@ -780,8 +1001,6 @@ static int step_2d_launch(Ctx* c, unsigned mask) {
     fa.lv[q].d32 = parts.d32 ? parts.d32 + (size_t)q * c->plane : nullptr;
   }
   RIDC_TRY(launch_finalize(c, fa));
-  for (int j = 0; j < P; ++j)
-    if (mask & (1u << j)) c->p[j]++;
   return RIDC_OK;
 }
 
@@ -794,7 +1013,7 @@ static int advance_run(Ctx* c, long nsteps) {
     long p[kMaxOrder];
     for (int j = 0; j < kMaxOrder; ++j) p[j] = c->p[j];
     for (;;) {
-      const unsigned m = plan_step(c->P, p, target);
+      const unsigned m = plan_step(c->P, p, target, c->p0);
       if (!m) break;
       masks.push_back(m);
       for (int j = 0; j < c->P; ++j)
@@ -818,7 +1037,7 @@ static int advance_run(Ctx* c, long nsteps) {
     return RIDC_OK;
   }
   for (;;) {
-    const unsigned m = plan_step(c->P, c->p, target);
+    const unsigned m = plan_step(c->P, c->p, target, c->p0);
     if (!m) break;
     RIDC_TRY(step_2d(c, m));
   }
@@ -931,7 +1150,7 @@ extern "C" int ridc_get_progress(ridc_handle h, long* steps, int nlevels) {
 // the level keeps it) f, every slot in slot order: cap[j] * plane FP64 values per field.
 struct StateHeader {
   char magic[8];
-  int32_t version, kind, dim, n, S, P;
+  int32_t version, kind, dim, n, S, P, predictor, reserved;
   double dt, nu[kMaxSpecies], a, b, F, k;
   int64_t restart_every, seg_base, p[kMaxOrder];
   int32_t cap[kMaxOrder];
@@ -939,7 +1158,7 @@ struct StateHeader {
   uint64_t payload;
 };
 static const char kStateMagic[8] = {'R', 'I', 'D', 'C', 'S', 'T', 'A', 'T'};
-constexpr int32_t kStateVersion = 1;
+constexpr int32_t kStateVersion = 2;
 
 static uint64_t state_payload(const Ctx* c) {
   uint64_t vals = 0;
@@ -953,6 +1172,7 @@ static void fill_header(const Ctx* c, StateHeader* hd) {
   memcpy(hd->magic, kStateMagic, sizeof(kStateMagic));
   hd->version = kStateVersion;
   hd->kind = c->kind; hd->dim = c->dim; hd->n = c->n; hd->S = c->S; hd->P = c->P;
+  hd->predictor = c->pred;
   hd->dt = c->dt;
   for (int s = 0; s < kMaxSpecies; ++s) hd->nu[s] = (s < c->S) ? c->nu[s] : 0.0;
   hd->a = c->a; hd->b = c->b; hd->F = c->gsF; hd->k = c->gsk;
@@ -1011,7 +1231,7 @@ extern "C" int ridc_load_state(ridc_handle h, const void* buf, size_t len) {
     return RIDC_ERR_ARG;
   // same problem: every parameter the stored f^N and f depend on, bit for bit
   if (hd.kind != mine.kind || hd.dim != mine.dim || hd.n != mine.n || hd.S != mine.S ||
-      hd.P != mine.P || memcmp(&hd.dt, &mine.dt, sizeof(double)) != 0 ||
+      hd.P != mine.P || hd.predictor != mine.predictor || memcmp(&hd.dt, &mine.dt, sizeof(double)) != 0 ||
       memcmp(hd.nu, mine.nu, sizeof(hd.nu)) != 0 || memcmp(&hd.a, &mine.a, sizeof(double)) != 0 ||
       memcmp(&hd.b, &mine.b, sizeof(double)) != 0 || memcmp(&hd.F, &mine.F, sizeof(double)) != 0 ||
       memcmp(&hd.k, &mine.k, sizeof(double)) != 0 || hd.restart_every != mine.restart_every ||
@@ -1054,8 +1274,19 @@ extern "C" int ridc_schedule_plan(int order, long nsteps, unsigned* active, size
 
 extern "C" int ridc_schedule_plan_from(int order, const long* start, long nsteps,
                                        unsigned* active, size_t cap, size_t* count) {
-  if (order < 1 || order > kMaxOrder || nsteps < 0 || !start || !count || (cap && !active))
+  if (!start) return RIDC_ERR_ARG;
+  return ridc_schedule_plan_predictor(order, RIDC_PRED_FBE, start, nsteps, active, cap, count);
+}
+
+extern "C" int ridc_schedule_plan_predictor(int order, int predictor, const long* start,
+                                            long nsteps, unsigned* active, size_t cap,
+                                            size_t* count) {
+  const int p0 = predictor_order(predictor);
+  if (p0 == 0 || order < 1 || order > kMaxOrder || p0 + order - 1 > kMaxOrder || nsteps < 0 ||
+      !count || (cap && !active))
     return RIDC_ERR_ARG;
+  const long zero[kMaxOrder] = {0};
+  if (!start) start = zero;
   long p[kMaxOrder] = {0};
   for (int j = 0; j < order; ++j) {
     p[j] = start[j];
@@ -1064,7 +1295,7 @@ extern "C" int ridc_schedule_plan_from(int order, const long* start, long nsteps
   if (p[order - 1] > nsteps) return RIDC_ERR_ARG;
   size_t s = 0;
   for (;;) {
-    const unsigned m = plan_step(order, p, nsteps);
+    const unsigned m = plan_step(order, p, nsteps, p0);
     if (!m) break;
     if (s < cap) active[s] = m;
     ++s;

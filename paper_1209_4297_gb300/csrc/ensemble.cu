@@ -613,7 +613,7 @@ static int batch_run(BatchCtx* b, long nsteps, int cl, int per_sm, const int* or
     const long target = p[I.P - 1] + nsteps;
     std::vector<unsigned> masks;
     for (;;) {
-      const unsigned m = plan_step(I.P, p, target);
+      const unsigned m = plan_step(I.P, p, target, 1);
       if (!m) break;
       masks.push_back(m);
       for (int j = 0; j < I.P; ++j)
@@ -691,6 +691,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     if (pr.kind != RIDC_ADV_DIFF_2D_DIRICHLET) return RIDC_ERR_UNSUPPORTED;
     if (pr.precision != RIDC_FP32_SOLVE) return RIDC_ERR_UNSUPPORTED;
     if (pr.restart_every != 0) return RIDC_ERR_UNSUPPORTED;
+    if (pr.predictor != RIDC_PRED_FBE) return RIDC_ERR_UNSUPPORTED;
     if (pr.n_refine < 0 || pr.n_refine > 4) return RIDC_ERR_ARG;
     if (nref >= 0 && pr.n_refine != nref) return RIDC_ERR_ARG;   // one setting per batch
     nref = pr.n_refine;

@@ -182,7 +182,7 @@ struct SymArgs {
   __nv_bfloat16* oh;
   __nv_bfloat16* ol;
   const float* lam;   // eigenvalues in split order
-  float dtnu[kMaxSpecies];
+  float dtnu[kMaxPlanes];   // a_p dt nu_s of plane p (a_p: its operator's diagonal)
   int* err;
   int stall;            // test hook: CTA 0 leaves its first stage unloaded
   int f16;              // FP16 form: FP16 operands and the power-of-two scales below
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
       const uint32_t acc = tmem + (uint32_t)(b * SY_ACC_COLS) + ((uint32_t)(q * 32) << 16);
       if (fwd) {
         const int cbase = T.g * a.H + T.c0;   // output column position (split order)
-        const float dtnu = a.dtnu[plane % a.S];
+        const float dtnu = a.dtnu[plane];
         const float den_r = (a.mode == SYM_FWD_DEN) ? 1.0f - dtnu * lam_s[rl] : 0.f;
         // first transform: row rl = gy N/2 + y' goes to row block gy of the next operand
         const int gy = rl >= a.H ? 1 : 0, yp = rl - gy * a.H;
@@ -482,7 +482,10 @@ int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const 
   a.oh = oh;
   a.ol = ol;
   a.lam = c->lam_f;
-  for (int s = 0; s < c->S; ++s) a.dtnu[s] = (float)(c->dt * c->nu[s]);
+  if (plane0 < 0 || nplanes < 1 || plane0 + nplanes > kMaxPlanes) return RIDC_ERR_ARG;
+  // (a dt) nu: with a = 1 exactly the correctors' dt nu
+  for (int p = plane0; p < plane0 + nplanes; ++p)
+    a.dtnu[p] = (float)((c->coef[c->plane_coef[p]] * c->dt) * c->nu[p % c->S]);
   a.err = c->err_dev;
   a.stall = c->stall_next_gemm;
   c->stall_next_gemm = 0;

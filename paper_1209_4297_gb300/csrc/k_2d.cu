@@ -53,12 +53,24 @@ __device__ __forceinline__ double flip_sign(double v, bool neg) {
 // GB300 a predicated-off FP64 instruction still occupies the FP64 pipe, so no FP64 work may
 // be issued for absent nodes.
 // ---------------------------------------------------------------------------------------------
-template <int NODES>
+// COMBO: the right-hand side of an ARK stage, sum_k w_k Fn_k (a separate instantiation, so
+// that the corrector kernels keep their registers)
+template <int NODES, bool COMBO>
 __device__ __forceinline__ double2 rhs_at(const RhsArgs& a, const RhsLevel& L,
                                           const double2* const (&Fn)[NODES],
                                           const double (&w)[NODES], long i) {
   double2 acc;
-  if (L.eta_j) {
+  if (COMBO) {
+    const double2 F = __ldg(Fn[0] + i);
+    acc.x = w[0] * F.x;
+    acc.y = w[0] * F.y;
+#pragma unroll
+    for (int k = 1; k < NODES; ++k) {
+      const double2 G = __ldg(Fn[k] + i);
+      acc.x = fma(w[k], G.x, acc.x);
+      acc.y = fma(w[k], G.y, acc.y);
+    }
+  } else if (L.eta_j) {
     const double2 e = ((const double2*)L.eta_j)[i], ep = ((const double2*)L.eta_pn)[i];
     const double2 f = ((const double2*)L.fN_j)[i], fp = ((const double2*)L.fN_p)[i];
     acc.x = fma(a.dt, f.x - fp.x, e.x - ep.x);
@@ -90,8 +102,14 @@ __device__ __forceinline__ void store_split2(__nv_bfloat16* hi, __nv_bfloat16* l
 
 // one value, in the same operation order as rhs_at (the FP64 path of odd planes: one species
 // and odd n make n^2 odd, so ring slots are only 8-byte aligned and double2 cannot be used)
-template <int NODES>
+template <int NODES, bool COMBO>
 __device__ __forceinline__ double rhs_at1(const RhsArgs& a, const RhsLevel& L, long i) {
+  if (COMBO) {
+    double acc = L.w[0] * __ldg(L.Fn[0] + i);
+#pragma unroll
+    for (int k = 1; k < NODES; ++k) acc = fma(L.w[k], __ldg(L.Fn[k] + i), acc);
+    return acc;
+  }
   if (L.eta_j) {
     double acc = fma(a.dt, L.fN_j[i] - L.fN_p[i], L.eta_j[i] - L.eta_pn[i]);
 #pragma unroll
@@ -121,7 +139,7 @@ __device__ __forceinline__ void flush_plane_max(unsigned* pmax, unsigned m) {
 
 // STAGE: the FP16 form (FP32 staging and plane maxima); a separate instantiation keeps the
 // FP64 and BF16 code free of its branches and registers
-template <int NODES, bool STAGE>
+template <int NODES, bool STAGE, bool COMBO>
 __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, long out_off) {
   const double2* Fn[NODES];
   double w[NODES];
@@ -135,7 +153,7 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
     const long half = a.plane >> 1;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < half;
          i += (long)gridDim.x * blockDim.x)
-      r2[i] = rhs_at<NODES>(a, L, Fn, w, i);
+      r2[i] = rhs_at<NODES, COMBO>(a, L, Fn, w, i);
     return;
   }
   // mixed form: each thread takes cells (2q, 2q+1) of rows y and n-1-y (y < n/2) and their
@@ -158,8 +176,8 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
     for (int side = 0; side < 2; ++side) {
       const long rowoff = sp * nn + (long)(side ? n - 1 - y : y) * n;
       const long iL = (rowoff + 2 * q) >> 1, iR = (rowoff + n - 2 - 2 * q) >> 1;
-      const double2 vL = rhs_at<NODES>(a, L, Fn, w, iL);
-      const double2 vR = rhs_at<NODES>(a, L, Fn, w, iR);
+      const double2 vL = rhs_at<NODES, COMBO>(a, L, Fn, w, iL);
+      const double2 vR = rhs_at<NODES, COMBO>(a, L, Fn, w, iR);
       r2[iL] = vL;
       r2[iR] = vR;
       v[side][0] = f64_to_f32(vL.x);
@@ -195,51 +213,64 @@ __device__ __forceinline__ void rhs_level(const RhsArgs& a, const RhsLevel& L, l
 }
 
 // FP64 right-hand side of odd planes (one species, odd n), one value per thread and step
-template <int NODES>
+template <int NODES, bool COMBO>
 __device__ __forceinline__ void rhs_level_scalar(const RhsArgs& a, const RhsLevel& L,
                                                  long out_off) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < a.plane;
        i += (long)gridDim.x * blockDim.x)
-    a.r[out_off + i] = rhs_at1<NODES>(a, L, i);
+    a.r[out_off + i] = rhs_at1<NODES, COMBO>(a, L, i);
 }
 
+template <bool COMBO>
 __global__ void __launch_bounds__(256) rhs_scalar_kernel(const __grid_constant__ RhsArgs a) {
   const RhsLevel& L = a.lv[blockIdx.y];
   const long out_off = (long)blockIdx.y * a.plane;
   switch (L.nnodes) {
-    case 1: rhs_level_scalar<1>(a, L, out_off); break;
-    case 2: rhs_level_scalar<2>(a, L, out_off); break;
-    case 3: rhs_level_scalar<3>(a, L, out_off); break;
-    case 4: rhs_level_scalar<4>(a, L, out_off); break;
-    case 5: rhs_level_scalar<5>(a, L, out_off); break;
-    case 6: rhs_level_scalar<6>(a, L, out_off); break;
-    case 7: rhs_level_scalar<7>(a, L, out_off); break;
-    case 8: rhs_level_scalar<8>(a, L, out_off); break;
-    case 9: rhs_level_scalar<9>(a, L, out_off); break;
-    case 10: rhs_level_scalar<10>(a, L, out_off); break;
-    case 11: rhs_level_scalar<11>(a, L, out_off); break;
-    default: rhs_level_scalar<12>(a, L, out_off); break;
+    case 1: rhs_level_scalar<1, COMBO>(a, L, out_off); break;
+    case 2: rhs_level_scalar<2, COMBO>(a, L, out_off); break;
+    case 3: rhs_level_scalar<3, COMBO>(a, L, out_off); break;
+    case 4: rhs_level_scalar<4, COMBO>(a, L, out_off); break;
+    case 5: rhs_level_scalar<5, COMBO>(a, L, out_off); break;
+    case 6: rhs_level_scalar<6, COMBO>(a, L, out_off); break;
+    case 7: rhs_level_scalar<7, COMBO>(a, L, out_off); break;
+    case 8: rhs_level_scalar<8, COMBO>(a, L, out_off); break;
+    case 9: rhs_level_scalar<9, COMBO>(a, L, out_off); break;
+    case 10: rhs_level_scalar<10, COMBO>(a, L, out_off); break;
+    case 11: rhs_level_scalar<11, COMBO>(a, L, out_off); break;
+    default: rhs_level_scalar<12, COMBO>(a, L, out_off); break;
   }
 }
 
-template <bool STAGE>
-__global__ void __launch_bounds__(256, 4) rhs_kernel(const __grid_constant__ RhsArgs a) {
+// the corrector kernels are capped at 64 registers (32 warps per SM); the ARK-stage sums,
+// with up to 12 terms held for two cells of four rows, keep 128
+template <bool STAGE, bool COMBO>
+__global__ void __launch_bounds__(256, COMBO ? 2 : 4) rhs_kernel(const __grid_constant__ RhsArgs a) {
   const RhsLevel& L = a.lv[blockIdx.y];
   const long out_off = (long)blockIdx.y * a.plane;
   switch (L.nnodes) {
-    case 1: rhs_level<1, STAGE>(a, L, out_off); break;
-    case 2: rhs_level<2, STAGE>(a, L, out_off); break;
-    case 3: rhs_level<3, STAGE>(a, L, out_off); break;
-    case 4: rhs_level<4, STAGE>(a, L, out_off); break;
-    case 5: rhs_level<5, STAGE>(a, L, out_off); break;
-    case 6: rhs_level<6, STAGE>(a, L, out_off); break;
-    case 7: rhs_level<7, STAGE>(a, L, out_off); break;
-    case 8: rhs_level<8, STAGE>(a, L, out_off); break;
-    case 9: rhs_level<9, STAGE>(a, L, out_off); break;
-    case 10: rhs_level<10, STAGE>(a, L, out_off); break;
-    case 11: rhs_level<11, STAGE>(a, L, out_off); break;
-    default: rhs_level<12, STAGE>(a, L, out_off); break;
+    case 1: rhs_level<1, STAGE, COMBO>(a, L, out_off); break;
+    case 2: rhs_level<2, STAGE, COMBO>(a, L, out_off); break;
+    case 3: rhs_level<3, STAGE, COMBO>(a, L, out_off); break;
+    case 4: rhs_level<4, STAGE, COMBO>(a, L, out_off); break;
+    case 5: rhs_level<5, STAGE, COMBO>(a, L, out_off); break;
+    case 6: rhs_level<6, STAGE, COMBO>(a, L, out_off); break;
+    case 7: rhs_level<7, STAGE, COMBO>(a, L, out_off); break;
+    case 8: rhs_level<8, STAGE, COMBO>(a, L, out_off); break;
+    case 9: rhs_level<9, STAGE, COMBO>(a, L, out_off); break;
+    case 10: rhs_level<10, STAGE, COMBO>(a, L, out_off); break;
+    case 11: rhs_level<11, STAGE, COMBO>(a, L, out_off); break;
+    default: rhs_level<12, STAGE, COMBO>(a, L, out_off); break;
   }
+}
+
+template <bool COMBO>
+static void launch_rhs_kind(Ctx* c, const RhsArgs& a, dim3 grid) {
+  if (a.r_stage)
+    rhs_kernel<true, COMBO><<<grid, 256, 0, c->stream>>>(a);
+  else if (!a.r_hi && (a.plane & 1))   // FP64, odd plane: fields only 8-byte aligned
+    rhs_scalar_kernel<COMBO><<<grid, 256, 0, c->stream>>>(a);
+  else
+    rhs_kernel<false, COMBO><<<grid, 256, 0, c->stream>>>(a);
 }
 
 int launch_rhs(Ctx* c, const RhsArgs& a) {
@@ -250,12 +281,8 @@ int launch_rhs(Ctx* c, const RhsArgs& a) {
   dim3 grid((unsigned)bx, a.nlev);
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_RHS, &e0);
-  if (a.r_stage)
-    rhs_kernel<true><<<grid, 256, 0, c->stream>>>(a);
-  else if (!a.r_hi && (a.plane & 1))   // FP64, odd plane: fields only 8-byte aligned
-    rhs_scalar_kernel<<<grid, 256, 0, c->stream>>>(a);
-  else
-    rhs_kernel<false><<<grid, 256, 0, c->stream>>>(a);
+  if (a.combo) launch_rhs_kind<true>(c, a, grid);
+  else launch_rhs_kind<false>(c, a, grid);
   prof_end(c, RIDC_KERNEL_RHS, e0);
   return cuda_status(cudaGetLastError());
 }
@@ -369,8 +396,8 @@ struct ResArgs {
   float* stage;             // FP16 form: the same values in FP32 (else nullptr)
   unsigned* pmax;           // FP16 form: per-plane maxima of this solve pass
   int n, S, plane0;
-  double c[kMaxSpecies];    // c_s
-  double c1[kMaxSpecies];   // -(1 + 4 c_s)
+  double c[kMaxPlanes];     // c_p = a_p dt nu_s / h^2 of plane p (a_p: its operator's diagonal)
+  double c1[kMaxPlanes];    // -(1 + 4 c_p)
 };
 
 // One block covers a 32 x 32 tile at (x0, y0), x0, y0 < n/2, and its three mirror tiles
@@ -386,8 +413,7 @@ __global__ void __launch_bounds__(TX * BY) residual_kernel(const __grid_constant
   const int p = a.plane0 + blockIdx.z;
   const long off = (long)p * nn;
   const bool has_d = a.dprev || a.inc;
-  const int sp = p % a.S;
-  const double cs = a.c[sp], c1 = a.c1[sp];
+  const double cs = a.c[p], c1 = a.c1[p];
   for (int side = 0; side < 4; ++side) {
     const int sx = side & 1, sy = side >> 1;
     const int x0 = sx == 0 ? blockIdx.x * TX : n - TX - blockIdx.x * TX;
@@ -465,9 +491,11 @@ int launch_residual(Ctx* c, int plane0, int nplanes, const double* dprev, const 
   }
   a.n = c->n;
   a.S = c->S;
-  for (int s = 0; s < c->S; ++s) {
-    a.c[s] = c->dt * c->nu[s] / (c->h * c->h);
-    a.c1[s] = -(1.0 + 4.0 * a.c[s]);
+  if (plane0 < 0 || nplanes < 0 || plane0 + nplanes > kMaxPlanes) return RIDC_ERR_ARG;
+  for (int p = plane0; p < plane0 + nplanes; ++p) {
+    // (a dt) nu / h^2: with a = 1 exactly the correctors' dt nu / h^2
+    a.c[p] = (c->coef[c->plane_coef[p]] * c->dt) * c->nu[p % c->S] / (c->h * c->h);
+    a.c1[p] = -(1.0 + 4.0 * a.c[p]);
   }
   if (c->n % (2 * TX) != 0 || c->n % (2 * TY) != 0) return RIDC_ERR_UNSUPPORTED;
   dim3 grid(c->n / (2 * TX), c->n / (2 * TY), nplanes);
@@ -585,12 +613,17 @@ int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev) {
 // ---------------------------------------------------------------------------------------------
 constexpr int GB = 64, GK = 16;
 
+// 1/den table of each plane of a solve: the table [t][N][N] of inv_den, t = coef * S + species
+struct PlaneTabs {
+  int t[kMaxPlanes];
+};
+
 template <int EPI>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict__ A,
                                                        const double* __restrict__ B,
                                                        double* __restrict__ out,
                                                        const double* __restrict__ inv_den, int n,
-                                                       int rows, int S) {
+                                                       int rows, const PlaneTabs pt) {
   __shared__ __align__(16) double As[GK][GB + 2];
   __shared__ __align__(16) double Bs[GK][GB + 2];
   const int t = threadIdx.x;
@@ -633,7 +666,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const double* __restrict_
       const int m = col0 + tc * 4 + j;
       if (m >= n) continue;
       double v = acc[i][j];
-      if (EPI == EPI_SCALE_DEN) v *= inv_den[((long)(plane % S) * n + m) * n + rl];
+      if (EPI == EPI_SCALE_DEN) v *= inv_den[((long)pt.t[plane] * n + m) * n + rl];
       out[((long)plane * n + m) * n + rl] = v;
     }
   }
@@ -652,7 +685,7 @@ __global__ void __launch_bounds__(256) gemm_f64_split_kernel(const double* __res
                                                              const double* __restrict__ B,
                                                              double* __restrict__ out,
                                                              const double* __restrict__ inv_den,
-                                                             int n, int rows, int S) {
+                                                             int n, int rows, const PlaneTabs pt) {
   constexpr int GH = GB / 2;
   __shared__ __align__(16) double As[2][GK][GB + 2];
   __shared__ __align__(16) double Bs[2][GK][GH + 2];
@@ -728,7 +761,7 @@ __global__ void __launch_bounds__(256) gemm_f64_split_kernel(const double* __res
       if (FWD) {
         double v0 = acc[0][i][j], v1 = acc[1][i][j];
         if (EPI == EPI_SCALE_DEN) {
-          const double* id = inv_den + (long)(plane % S) * n * n;
+          const double* id = inv_den + (long)pt.t[plane] * n * n;
           v0 *= id[(long)cc * n + rl];
           v1 *= id[(long)(H + cc) * n + rl];
         }
@@ -746,25 +779,28 @@ __global__ void __launch_bounds__(256) gemm_f64_split_kernel(const double* __res
 int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int nplanes, int epi,
                     bool forward) {
   const int n = c->n, rows = nplanes * n;
+  if (nplanes < 1 || nplanes > kMaxPlanes) return RIDC_ERR_ARG;
+  PlaneTabs pt{};
+  for (int p = 0; p < nplanes; ++p) pt.t[p] = c->plane_coef[p] * c->S + p % c->S;
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_GEMM_F64, &e0);
   if (n % 2 == 0) {
     dim3 grid((rows + GB - 1) / GB, (n / 2 + GB / 2 - 1) / (GB / 2));
     if (forward && epi == EPI_SCALE_DEN)
       gemm_f64_split_kernel<true, EPI_SCALE_DEN><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n,
-                                                                           rows, c->S);
+                                                                           rows, pt);
     else if (forward)
       gemm_f64_split_kernel<true, EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n,
-                                                                       rows, c->S);
+                                                                       rows, pt);
     else
       gemm_f64_split_kernel<false, EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n,
-                                                                        rows, c->S);
+                                                                        rows, pt);
   } else {
     dim3 grid((rows + GB - 1) / GB, (n + GB - 1) / GB);
     if (epi == EPI_SCALE_DEN)
-      gemm_f64_kernel<EPI_SCALE_DEN><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, c->S);
+      gemm_f64_kernel<EPI_SCALE_DEN><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, pt);
     else
-      gemm_f64_kernel<EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, c->S);
+      gemm_f64_kernel<EPI_STORE><<<grid, 256, 0, c->stream>>>(A, B, out, c->inv_den, n, rows, pt);
   }
   prof_end(c, RIDC_KERNEL_GEMM_F64, e0);
   return cuda_status(cudaGetLastError());

@@ -18,6 +18,28 @@ constexpr int kMaxOrder = 12;
 constexpr int kMaxSpecies = 2;
 constexpr int kMaxPasses = 5;       // solve passes of the mixed forms: 1 + up to 4 refinements
 constexpr int kMaxPlanes = kMaxOrder * kMaxSpecies;
+constexpr int kMaxStages = 8;       // stages of an ARK predictor (the fourth-order one has 7)
+constexpr int kMaxCoefs = 4;        // distinct solve operators (I - a dt D): a = 1 and the
+                                    // ARK diagonals (the third-order one adds 1/2, 2/3, 2)
+constexpr int kMaxTerms = kMaxOrder;   // terms of an ARK stage right-hand side
+
+// One implicit stage i >= 1 of an ARK predictor (Section II) in delta form. With K^S_j = F_j -
+// KN_j (F = f^N + D Y and KN = f^N(Y) of stage j; stage 0 is y_n itself):
+//   (I - dt a_ii D) delta_i = dt sum_t w[t] X[src[t]],   Y_i = y_n + delta_i,
+// X[2j] = F_j, X[2j+1] = KN_j, and w from a^S_ij (+ a_ii for j = 0) on F_j and
+// a^N_ij - a^S_ij (- a_ii for j = 0) on KN_j, in exact rationals (zero terms dropped).
+struct ArkStage {
+  int coef;                  // index of a_ii in Ctx::coef
+  int nterms;
+  int src[kMaxTerms];
+  double w[kMaxTerms];       // units of dt
+};
+// Fill the stages of predictor `pred` (RIDC_PRED_ARK3/4): returns the stage count s (the
+// last stage is the new solution: both tableaux are stiffly accurate), or 0 for FBE / an
+// unknown value. coef[0] = 1 is the correctors' operator; new diagonals are appended.
+int ark_plan(int pred, ArkStage* st, double* coef, int* ncoef);
+// order p0 of a predictor (0 for an unknown value)
+int predictor_order(int pred);
 // FP16 form: an operand plane is scaled by 2^k with max|v| 2^k in [2^(K0-1), 2^K0),
 // K0 = 15 - ceil(log2 N), so every intermediate of the transform, at most N 2^K0 <= 2^15,
 // stays finite in FP16 while small values keep clear of its subnormals
@@ -51,11 +73,14 @@ __host__ __device__ inline float pow2f(int k) {
 // ---- launch descriptors ---------------------------------------------------------------
 
 // Right-hand side of one advancing level in delta form (the Dy of the base cancels):
-//   predictor: r = dt * F^0_n                                          (eq. (pred))
-//   corrector: r = (eta^j_n - eta^{j-1}_{n+1}) + dt (f^N(eta^j_n) - f^N(eta^{j-1}_n))
-//                  + dt sum_i w_i F^{j-1}_{b+i}                         (eq. (corr))
+//   FBE predictor: r = dt * F^0_n                                      (eq. (pred))
+//   ARK stage i:   r = sum_t w_t X_t  (w_t in units of dt already; see ArkStage)
+//   corrector:     r = (eta^j_n - eta^{j-1}_{n+1}) + dt (f^N(eta^j_n) - f^N(eta^{j-1}_n))
+//                      + dt sum_i w_i F^{j-1}_{b+i}                     (eq. (corr))
+// ARK stages (RhsArgs::combo) take the sum of the nnodes terms w_i Fn_i as the whole
+// right-hand side; the FBE predictor (eta_j == nullptr) takes w_0 Fn_0.
 struct RhsLevel {
-  const double* eta_j;    // eta^j_n          [S][N][N]  (nullptr for the predictor)
+  const double* eta_j;    // eta^j_n          [S][N][N]  (nullptr: predictor / ARK stage)
   const double* fN_j;     // f^N(eta^j_n)
   const double* eta_pn;   // eta^{j-1}_{n+1}
   const double* fN_p;     // f^N(eta^{j-1}_n)
@@ -75,6 +100,7 @@ struct RhsArgs {
   float* r_stage;         // FP16 form: the split values in FP32, same layout (else nullptr)
   unsigned* pmax;         // FP16 form: per-plane max |staged value| (FP32 bits), pass 0
   int n;
+  int combo;              // every level is an ARK stage: r = sum_k w_k Fn_k (own kernel)
 };
 
 // New state of one advancing level: eta = base + d64 + d32, then f^N(eta) and
@@ -124,8 +150,20 @@ struct Ctx {
   long restart_every = 0;    // restart interval in top-level steps (0: none), Section III-E
   long seg_base = 0;
 
-  // quadrature weights w[j][m][i] (units of dt), exact rationals rounded to FP64
-  std::vector<double> wq;   // [P][P][P]
+  // quadrature weights w[d][m][i] (units of dt) of the (d+1)-node stencils, exact rationals
+  // rounded to FP64; corrector j uses d = p0 + j - 1
+  std::vector<double> wq;   // [W][W][W]
+  int W = 1;                // p0 + P - 1: the widest stencil's node count
+
+  // predictor (Section II / Theorem 2): FBE or an ARK method of order p0 with nstages stages
+  int pred = RIDC_PRED_FBE, p0 = 1, nstages = 1;
+  ArkStage stage[kMaxStages];        // stages 1..nstages-1
+  double coef[kMaxCoefs] = {1.0};    // diagonal coefficients a of the solve operators
+  int ncoef = 1;
+  int plane_coef[kMaxPlanes] = {0};  // operator of each plane of the next solve (index in coef)
+  double* stF[kMaxStages] = {nullptr};    // stage fields F_i, KN_i (stages 1..nstages-2), and
+  double* stKN[kMaxStages] = {nullptr};   // the stage value Y_i that the finalize kernel writes
+  double* stY = nullptr;
 
   // level rings: ring j has cap[j] slots of [S][N][N] values; slot of index t is t % cap[j]
   int cap[kMaxOrder] = {0};
@@ -158,8 +196,8 @@ struct Ctx {
   // fast-diagonalisation tables (2D): Q[x][k] orthonormal eigenvectors of the 1D Laplacian
   double* Q = nullptr;       // [N][N]   Q, its columns in split order when N is even
   double* Qt = nullptr;      // [N][N]   Q^T, its rows in split order when N is even
-  double* inv_den = nullptr; // [S][N][N] 1 / (1 - dt nu_s (lam_ky + lam_kx)), FP64 path (split
-                             //           order for ky and kx when N is even)
+  double* inv_den = nullptr; // [ncoef][S][N][N] 1 / (1 - a dt nu_s (lam_ky + lam_kx)), FP64 path
+                             //           (split order for ky and kx when N is even)
   float* lam_f = nullptr;    // [N] eigenvalues in split order (even modes, then odd), FP32
   // parity-split eigenvector tables, BF16 (or scaled FP16) hi/lo, each [N][N/2]:
   //   Bf = [Qe^T; Qo^T] (forward products), Bb = [Qe; Qo] (inverse products)
@@ -266,8 +304,9 @@ inline int current_sm_count() {
 void prof_begin(Ctx* c, int kind, cudaEvent_t* e0);
 void prof_end(Ctx* c, int kind, cudaEvent_t e0);
 
-// lock-step rule (Section III-E): which levels advance in one pipeline step
-unsigned plan_step(int P, const long* p, long target_top);
+// lock-step rule (Section III-E): which levels advance in one pipeline step, for a predictor
+// of order p0 (corrector j reads a p0+j-node stencil)
+unsigned plan_step(int P, const long* p, long target_top, int p0);
 
 // ---- kernel launchers (each returns RIDC_OK or an error code) -------------------------------------
 int launch_rhs(Ctx* c, const RhsArgs& a);

@@ -19,7 +19,8 @@ int main(int argc, char** argv) {
     FILE* f = fopen(argv[1], "rb");
     if (!f || fread(u0, sizeof(double), COUNT, f) != COUNT) return 4;
     fclose(f);
-    ridc_problem pr = {RIDC_GRAY_SCOTT_2D_NEUMANN, 0.0, 0.0, 0.04, 0.06, RIDC_MIXED_BF16X3, 2, 0};
+    ridc_problem pr = {RIDC_GRAY_SCOTT_2D_NEUMANN, 0.0, 0.0, 0.04, 0.06, RIDC_MIXED_BF16X3, 2, 0,
+                       RIDC_PRED_FBE};
     ridc_grid g = {2, N};
     const double nu[2] = {2e-5, 1e-5};
     ridc_handle h = NULL;

@@ -192,3 +192,95 @@ def test_binding_tables_match_the_header():
     for name, val in B.KERNELS.items():
         assert defines["RIDC_KERNEL_" + ids[name]] == val, name
     assert len(B.KERNELS) == defines["RIDC_KERNEL_COUNT"]
+
+
+# ---------------------------------------------------------------- schedules with an ARK predictor
+P0 = {"fbe": 1, "ark3": 3, "ark4": 4}
+
+
+def _simulate_p0(order, masks, p0):
+    """Replay a schedule for a p0-th order predictor: corrector j reads the K = p0 + j node
+    stencil t_b..t_{b+K-1}, b = max(0, n + 2 - K), of ring j-1 (p0 + j + 1 slots below the top
+    level) plus eta^{j-1}_{n+1} and f^N(eta^{j-1}_n); every read must hit a live value."""
+    P = order
+    p = [0] * P
+    cap = [p0 + j + 2 if j < P - 1 else 2 for j in range(P)]
+    rings = [{0: 0} for _ in range(P)]
+    first = [None] * P
+    for s, m in enumerate(masks):
+        reads = [set() for _ in range(P)]
+        for j in range(P):
+            if not (m >> j) & 1:
+                continue
+            n = p[j]
+            if first[j] is None:
+                first[j] = s + 1
+            if j > 0:
+                K = p0 + j
+                b = max(0, n + 2 - K)
+                need = set(range(b, b + K)) | {n + 1, n}
+                for t in need:
+                    assert rings[j - 1].get(t % cap[j - 1]) == t, (s, j, t)
+                    reads[j - 1].add(t % cap[j - 1])
+            assert rings[j].get(n % cap[j]) == n
+            reads[j].add(n % cap[j])
+        for j in range(P):
+            if (m >> j) & 1:
+                assert (p[j] + 1) % cap[j] not in reads[j], (s, j)   # no write over a read
+        for j in range(P):
+            if (m >> j) & 1:
+                p[j] += 1
+                rings[j][p[j] % cap[j]] = p[j]
+    return p, first
+
+
+@pytest.mark.parametrize("predictor", ["fbe", "ark3", "ark4"])
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 5, 30])
+def test_predictor_schedule_reads_live_slots_and_waits(predictor, order, nsteps):
+    p0 = P0[predictor]
+    if p0 + order - 1 > 12:
+        pytest.skip("beyond the widest stencil")
+    masks = R.schedule_plan_predictor(order, predictor, nsteps)
+    p, first = _simulate_p0(order, masks, p0)
+    assert p[order - 1] == nsteps
+    low = max(nsteps, p0 + order - 2) if order > 1 else nsteps
+    for j in range(order - 1):
+        assert p[j] == (low if nsteps > 0 else 0)
+    if nsteps >= 5:
+        for j in range(order):
+            assert first[j] == 1 + j * (p0 - 1) + j * (j + 1) // 2, (j, first)
+
+
+def test_predictor_schedule_fbe_is_the_paper_schedule():
+    for order in (1, 2, 4, 8, 12):
+        for nsteps in (0, 3, 17):
+            np.testing.assert_array_equal(R.schedule_plan_predictor(order, "fbe", nsteps),
+                                          R.schedule_plan(order, nsteps))
+
+
+@pytest.mark.parametrize("predictor", ["ark3", "ark4"])
+def test_predictor_schedule_split_and_limits(predictor):
+    p0 = P0[predictor]
+    order = 4
+    p = [0] * order
+    top = 0
+    for k in (1, 2, 9, 20):
+        top += k
+        for m in R.schedule_plan_predictor(order, predictor, top, start=p):
+            for j in range(order):
+                if (int(m) >> j) & 1:
+                    p[j] += 1
+        assert p[order - 1] == top
+    from paper_1209_4297_gb300 import RidcError
+    with pytest.raises(RidcError):        # p0 + order - 1 > 12: no stencil that wide
+        R.schedule_plan_predictor(13 - p0 + 1, predictor, 5)
+    assert len(R.schedule_plan_predictor(13 - p0, predictor, 5)) > 0
+
+
+def test_binding_predictors_match_the_header():
+    from paper_1209_4297_gb300 import binding as B
+    txt = open(os.path.join(ROOT, "include", "ridc.h")).read()
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(RIDC_[A-Z0-9_]+)\s*=\s*(\d+)", txt))
+    for name, val in B.PREDICTORS.items():
+        assert enums["RIDC_PRED_" + name.upper()] == val, name

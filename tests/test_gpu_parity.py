@@ -163,12 +163,31 @@ def test_gray_scott_mixed_matches_oracle_256():
         assert rel_l2(levels[j][0], ref[j]) <= MIXED_TIGHT, j
 
 
+def _ulp_envelope(w, order, ref):
+    """How far the oracle's own result moves when every initial value moves by one ulp
+    (seeded directions): the rounding level the problem itself allows (reading G9)."""
+    g = np.random.default_rng(1)
+    u1 = np.nextafter(w.u0, w.u0 + g.choice([-1.0, 1.0], size=w.u0.shape))
+    moved = oracle.ridc_sequential(oracle.from_workload(w), u1, w.dt, w.nsteps, order)
+    return rel_l2(moved, ref)
+
+
 def test_dirichlet_mixed_matches_oracle_256():
+    """Central advection at cell Peclet ~4 makes the operator non-normal: one ulp on the
+    initial data moves the oracle's result by 1.2e-11 after 24 steps, more than 1e-12. The
+    FP64 GPU path (8e-12 from the oracle) and the mixed path (4e-12 from the FP64 path) are
+    held to that envelope; the mixed path also to the contract bar."""
     w = inputs.adv_diff_2d(n=256, nsteps=24, kmax=8, nu=1e-3)
     got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
+    fp64, _, _ = _run(w)
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 4)
+    env = _ulp_envelope(w, 4, ref)
+    print("dirichlet 256 mixed: vs oracle %.3e, vs FP64 GPU %.3e, FP64 GPU vs oracle %.3e, "
+          "one-ulp envelope %.3e" % (rel_l2(got, ref), rel_l2(got, fp64), rel_l2(fp64, ref), env))
     assert rel_l2(got, ref) <= 1e-8
-    assert rel_l2(got, ref) <= MIXED_TIGHT
+    assert rel_l2(got, fp64) <= env
+    assert rel_l2(fp64, ref) <= 2 * env
+    assert rel_l2(got, ref) <= 2 * env
 
 
 # ---------------------------------------------------------------- errors
@@ -259,13 +278,20 @@ def test_gray_scott_order8_mixed_512_through_startup():
 
 
 def test_dirichlet_order12_mixed_512_through_startup():
-    """RIDC-12 on 512^2 Dirichlet advection-diffusion in the mixed form (78 start-up steps)."""
+    """RIDC-12 on 512^2 Dirichlet advection-diffusion in the mixed form (78 start-up steps).
+    Order 12's start-up weights (sum |w| up to 30) and the growing, non-normal problem make it
+    sensitive to rounding: one ulp on the initial data moves the oracle by 4.8e-10."""
     w = inputs.adv_diff_2d(n=512, nsteps=90, order=12, kmax=8, nu=1e-3)
     got, _, _ = _run(w, precision="mixed_bf16x3", n_refine=2)
     ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, w.nsteps, 12)
+    fp64, _, _ = _run(w)
+    env = _ulp_envelope(w, 12, ref)
+    print("dirichlet 512 order 12 mixed: vs oracle %.3e, vs FP64 GPU %.3e, FP64 GPU vs oracle "
+          "%.3e, one-ulp envelope %.3e" % (rel_l2(got, ref), rel_l2(got, fp64),
+                                           rel_l2(fp64, ref), env))
     assert rel_l2(got, ref) <= 1e-8
-    # order 12's start-up weights (sum |w| up to 30) amplify rounding on both sides
-    assert rel_l2(got, ref) <= 1e-11
+    assert rel_l2(got, fp64) <= env
+    assert rel_l2(got, ref) <= 2 * env
 
 
 def test_profiling_samples_every_kth_step():
