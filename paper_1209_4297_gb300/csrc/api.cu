@@ -485,25 +485,30 @@ static bool is_1d_dirichlet(int kind) { return kind == RIDC_BURGERS_1D_DIRICHLET
 //   x = y - kappa y_{n-1} g,  y = M^-1 r,  kappa = mu rho / (1 + mu rho g_{n-1}).
 static int build_tables_1d(Ctx* c) {
   const int n = c->n, npad = c->npad;
-  const double mu = c->nu[0] * c->dt / (c->h * c->h);
-  const double rho = 2.0 * mu / (1.0 + 2.0 * mu + std::sqrt(1.0 + 4.0 * mu));
-  const double s = rho / mu;
-  std::vector<double> tri((size_t)npad + 3 + (size_t)n + (size_t)c->W * c->W * c->W, 0.0);
-  for (int k = 0; k <= npad; ++k) tri[k] = std::pow(rho, (double)k);
-  tri[npad + 2] = s;
-  if (is_1d_dirichlet(c->kind)) {
-    // g = M^-1 e_{n-1}: z_j = rho^(n-1-j), then g_j = s z_j + rho g_{j-1}
-    double* gv = tri.data() + npad + 3;
-    double prev = 0.0;
-    for (int j = 0; j < n; ++j) {
-      prev = s * std::pow(rho, (double)(n - 1 - j)) + rho * prev;
-      gv[j] = prev;
+  const long T = oned_table_doubles(n, npad);
+  std::vector<double> tri((size_t)c->ncoef * T + (size_t)c->W * c->W * c->W, 0.0);
+  for (int k = 0; k < c->ncoef; ++k) {
+    // operator (I - a dt nu L): mu = nu (a dt) / h^2, with a = 1 exactly nu dt / h^2
+    double* t = tri.data() + (size_t)k * T;
+    const double mu = c->nu[0] * (c->coef[k] * c->dt) / (c->h * c->h);
+    const double rho = 2.0 * mu / (1.0 + 2.0 * mu + std::sqrt(1.0 + 4.0 * mu));
+    const double s = rho / mu;
+    for (int q = 0; q <= npad; ++q) t[q] = std::pow(rho, (double)q);
+    t[npad + 2] = s;
+    if (is_1d_dirichlet(c->kind)) {
+      // g = M^-1 e_{n-1}: z_j = rho^(n-1-j), then g_j = s z_j + rho g_{j-1}
+      double* gv = t + npad + 3;
+      double prev = 0.0;
+      for (int j = 0; j < n; ++j) {
+        prev = s * std::pow(rho, (double)(n - 1 - j)) + rho * prev;
+        gv[j] = prev;
+      }
+      t[npad + 1] = mu * rho / (1.0 + mu * rho * gv[n - 1]);
+    } else {
+      t[npad + 1] = 1.0 / (1.0 - std::pow(rho, (double)n));
     }
-    tri[npad + 1] = mu * rho / (1.0 + mu * rho * gv[n - 1]);
-  } else {
-    tri[npad + 1] = 1.0 / (1.0 - std::pow(rho, (double)n));
   }
-  fill_weights(c->W, tri.data() + npad + 3 + n);
+  fill_weights(c->W, tri.data() + (size_t)c->ncoef * T);
   return upload(c, &c->tri, tri);
 }
 
@@ -518,7 +523,7 @@ static void free_all(Ctx* c) {
   f(c->xs); f(c->pmax);
   f(c->tri); f(c->sched_dev); f(c->p_dev); f(c->err_dev);
   for (int i = 0; i < kMaxStages; ++i) { f(c->stF[i]); f(c->stKN[i]); }
-  f(c->stY);
+  f(c->stY); f(c->st1d);
   if (c->pinned) cudaFreeHost(c->pinned);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
 }
@@ -560,11 +565,15 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
   const size_t pb = (size_t)c->plane * sizeof(double);
   // ARK stages 1..s-2 keep F and f^N of their stage value for the later stages; the stage
   // value itself is written to one scratch field
-  for (int i = 1; i + 1 < c->nstages; ++i) {
-    RIDC_CUDA(dev_malloc((void**)&c->stF[i], pb));
-    RIDC_CUDA(dev_malloc((void**)&c->stKN[i], pb));
+  if (c->dim == 2) {
+    for (int i = 1; i + 1 < c->nstages; ++i) {
+      RIDC_CUDA(dev_malloc((void**)&c->stF[i], pb));
+      RIDC_CUDA(dev_malloc((void**)&c->stKN[i], pb));
+    }
+    if (c->nstages > 1) RIDC_CUDA(dev_malloc((void**)&c->stY, pb));
+  } else if (c->nstages > 1) {
+    RIDC_CUDA(dev_malloc((void**)&c->st1d, (size_t)(2 * c->nstages + 1) * pb));
   }
-  if (c->nstages > 1) RIDC_CUDA(dev_malloc((void**)&c->stY, pb));
   for (int j = 0; j < order; ++j) {
     c->cap[j] = ring_cap(order, j, c->p0);
     RIDC_CUDA(dev_malloc((void**)&c->eta[j], c->cap[j] * pb));
@@ -636,9 +645,9 @@ extern "C" int ridc_create(const ridc_problem* pr, const ridc_grid* g, const dou
       pr->kind == RIDC_BURGERS_1D_DIRICHLET) {
     if (g->dim != 1 || g->n < 8) return RIDC_ERR_ARG;
     if (pr->precision != RIDC_FP64) return RIDC_ERR_UNSUPPORTED;
-    if (pr->predictor != RIDC_PRED_FBE) return RIDC_ERR_UNSUPPORTED;
     // shared-memory rows of the levels one CTA carries
-    if (oned_smem_doubles(order, g->n, oned_npad(g->n)) > kOneDMaxSmemDoubles)
+    if (oned_smem_doubles(order, g->n, oned_npad(g->n), pr->predictor != RIDC_PRED_FBE) >
+        kOneDMaxSmemDoubles)
       return RIDC_ERR_UNSUPPORTED;
   } else {
     if (g->dim != 2 || g->n < 4) return RIDC_ERR_ARG;

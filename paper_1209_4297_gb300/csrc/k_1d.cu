@@ -14,24 +14,42 @@
 //   eta^j_{n+1} = base + delta, base = eta^0_n (j = 0) or eta^{j-1}_{n+1}
 //   f^N(eta) (Section IV's operators) and F = f^N + nu (eta_{i+1} - 2 eta_i + eta_{i-1}) / h^2
 // The step masks come from the host's plan of the same lock-step rule.
+// With an ARK predictor (Section II, Theorem 2) level 0 takes its step stage by stage on its
+// CTA: each implicit stage sums dt w X over the earlier stages' F and f^N (ArkStage), solves
+// with its own operator (I - a_ii dt D: its rho powers are loaded into a second shared table)
+// and evaluates F and f^N of the stage value into global scratch, which only this CTA reads;
+// the last stage is the new solution. Correctors read p0 + j-node stencils.
 #include "ridc_internal.h"
 
 namespace ridc {
+
+struct OneDStage {
+  int coef;                  // operator table index
+  int nterms;
+  int src[kMaxTerms];        // 2 j: F_j, 2 j + 1: f^N_j (stage 0: level 0's ring slot n)
+  double w[kMaxTerms];       // dt * weight
+};
 
 struct OneDArgs {
   double* eta[kMaxOrder];
   double* fN[kMaxOrder];
   double* F[kMaxOrder];
   int cap[kMaxOrder];
-  const double* wq;        // [P][P][P]
-  const double* tri;       // rho^k (k = 0..npad), wrap or kappa, rho/mu, g, weights
+  const double* wq;        // [W][W][W]
+  const double* tri;       // per operator: rho^k (k = 0..npad), wrap or kappa, rho/mu, g
   const unsigned* sched;   // step masks
   long nsteps_pipe;
   long* p_dev;             // steps taken per level (read at start, written at the end)
   int P, n, npad, init_only, kind;
+  int p0, W;               // predictor order, weight-table side p0 + P - 1
   double dt, c_lap;
   double cadv;             // central: a/(2h); upwind: a/h; Burgers: 1/(4h)
   bool upwind_left;        // upwind with a >= 0: backward difference
+  // ARK predictor (nstages > 1): stages 1..nstages-1; scratch [2 nstages + 1][n]: F_i at
+  // row 2 i, f^N_i at row 2 i + 1, the stage value Y at row 2 nstages
+  int nstages;
+  OneDStage st[kMaxStages];
+  double* scratch;
 };
 
 // f^N and F of one state; periodic wrap or zero Dirichlet ghosts
@@ -172,6 +190,8 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// ARK: level 0 is an ARK predictor (a separate instantiation keeps the FBE kernel's code)
+template <bool ARK>
 __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_constant__ OneDArgs a) {
   extern __shared__ double sm[];
   const int n = a.n, P = a.P, npad = a.npad;
@@ -180,6 +200,7 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
   double* R = sm;                       // [L][npad] right-hand sides, then solutions
   double* E = sm + (size_t)L * npad;    // [L][n] new states
   double* rp = E + (size_t)L * n;       // [npad+1] powers rho^k
+  double* rq = rp + npad + 1;           // ARK: [npad+1] powers of the stage operator's rho
   __shared__ long p[kMaxOrder];
   __shared__ int lev[kMaxOrder];
   __shared__ int na;
@@ -194,6 +215,9 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
   const double corr = a.tri[npad + 1], sfac = a.tri[npad + 2];
   const double* gvec = a.tri + npad + 3;
   const bool cyclic = a.kind != RIDC_BURGERS_1D_DIRICHLET;
+  const long T = (long)npad + 3 + n;    // one operator's table
+  constexpr bool ark = ARK;
+  int rq_coef = -1;                     // operator whose powers rq holds
   __syncthreads();
 
   for (long s = 0; s < a.nsteps_pipe; ++s) {
@@ -213,7 +237,42 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
       double* r = R + (size_t)q * npad;
       double* e = E + (size_t)q * n;
       // ring reads bypass L1 (__ldcg): other SMs of the cluster wrote them
-      if (j == 0) {
+      if (j == 0 && ark) {
+        // ARK predictor: stages 1..s-1; the last one leaves its solved delta in r and y_n
+        // in e, and the shared solve below skips it
+        const double* F0 = a.F[0] + (nj % a.cap[0]) * n;
+        const double* f0 = a.fN[0] + (nj % a.cap[0]) * n;
+        const double* e0 = a.eta[0] + (nj % a.cap[0]) * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) e[i] = __ldcg(e0 + i);
+        double* Y = a.scratch + (size_t)2 * a.nstages * n;
+        for (int si = 1; si < a.nstages; ++si) {
+          const OneDStage& S = a.st[si];
+          for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double acc = 0.0;
+            for (int t = 0; t < S.nterms; ++t) {
+              const int src = S.src[t];
+              const double* X = src == 0 ? F0 : src == 1 ? f0 : a.scratch + (size_t)src * n;
+              const double x = src < 2 ? __ldcg(X + i) : X[i];
+              acc = t == 0 ? S.w[0] * x : fma(S.w[t], x, acc);
+            }
+            r[i] = acc;
+          }
+          if (S.coef != rq_coef) {      // powers of this stage's rho into shared memory
+            for (int i = threadIdx.x; i <= npad; i += blockDim.x) rq[i] = a.tri[S.coef * T + i];
+            rq_coef = S.coef;
+          }
+          __syncthreads();
+          tri_solve_block(r, n, npad, rq, a.tri[S.coef * T + npad + 1],
+                          a.tri[S.coef * T + npad + 2], a.tri + S.coef * T + npad + 3, cyclic,
+                          scratch);
+          if (si == a.nstages - 1) break;
+          // stage value Y = y_n + delta, then F and f^N of it (read back by this CTA only)
+          for (int i = threadIdx.x; i < n; i += blockDim.x) Y[i] = e[i] + r[i];
+          __syncthreads();
+          eval_state(a, Y, a.scratch + (size_t)(2 * si + 1) * n, a.scratch + (size_t)2 * si * n);
+          __syncthreads();
+        }
+      } else if (j == 0) {
         const double* F0 = a.F[0] + (nj % a.cap[0]) * n;
         const double* e0 = a.eta[0] + (nj % a.cap[0]) * n;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -225,13 +284,15 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
         const double* fj = a.fN[j] + (nj % a.cap[j]) * n;
         const double* ep = a.eta[j - 1] + ((nj + 1) % a.cap[j - 1]) * n;
         const double* fp = a.fN[j - 1] + (nj % a.cap[j - 1]) * n;
-        const long b = nj + 1 - j > 0 ? nj + 1 - j : 0;
+        // K-node stencil of level j-1 (K = p0 + j): t_b..t_{b+K-1}, interval m = nj - b
+        const int K = a.p0 + j;
+        const long b = nj + 2 - K > 0 ? nj + 2 - K : 0;
         const int m = (int)(nj - b);
-        const double* w = a.wq + ((size_t)j * P + m) * P;
+        const double* w = a.wq + ((size_t)(K - 1) * a.W + m) * a.W;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
           const double base = __ldcg(ep + i);
           double acc = fma(a.dt, __ldcg(fj + i) - __ldcg(fp + i), __ldcg(ej + i) - base);
-          for (int k = 0; k <= j; ++k)
+          for (int k = 0; k < K; ++k)
             acc = fma(a.dt * w[k], __ldcg(a.F[j - 1] + ((b + k) % a.cap[j - 1]) * n + i), acc);
           r[i] = acc;
           e[i] = base;
@@ -240,7 +301,8 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
     }
     __syncthreads();
     for (int q = 0; q < na; ++q)
-      tri_solve_block(R + (size_t)q * npad, n, npad, rp, corr, sfac, gvec, cyclic, scratch);
+      if (!(ark && lev[q] == 0))   // an ARK predictor's last stage is solved already
+        tri_solve_block(R + (size_t)q * npad, n, npad, rp, corr, sfac, gvec, cyclic, scratch);
     // new states: base + delta (each thread updates the entries it stored the base of)
     for (int q = 0; q < na; ++q)
       for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -270,8 +332,20 @@ int launch_1d(Ctx* c, long nsteps_pipe, int init_only) {
     a.F[j] = c->Fq[j];
     a.cap[j] = c->cap[j];
   }
-  a.wq = nullptr;
   a.tri = c->tri;
+  a.p0 = c->p0;
+  a.W = c->W;
+  a.nstages = c->nstages;
+  a.scratch = c->st1d;
+  for (int i = 1; i < c->nstages; ++i) {
+    const ArkStage& S = c->stage[i];
+    a.st[i].coef = S.coef;
+    a.st[i].nterms = S.nterms;
+    for (int t = 0; t < S.nterms; ++t) {
+      a.st[i].src[t] = S.src[t];
+      a.st[i].w[t] = c->dt * S.w[t];
+    }
+  }
   a.sched = c->sched_dev;
   a.nsteps_pipe = nsteps_pipe;
   a.p_dev = c->p_dev;
@@ -286,13 +360,18 @@ int launch_1d(Ctx* c, long nsteps_pipe, int init_only) {
   else if (c->kind == RIDC_ADV_DIFF_1D_UPWIND_PERIODIC) a.cadv = c->a / c->h;
   else a.cadv = 1.0 / (4.0 * c->h);
   a.upwind_left = c->a >= 0.0;
-  // the quadrature weights follow the solver constants: uploaded once per handle
-  a.wq = c->tri + c->npad + 3 + c->n;
+  // the quadrature weights follow the solver tables: uploaded once per handle
+  a.wq = c->tri + (size_t)c->ncoef * oned_table_doubles(c->n, c->npad);
   const int CL = init_only ? 1 : oned_cluster(c->P);
-  const size_t smem = oned_smem_doubles(c->P, c->n, c->npad) * sizeof(double);
-  static std::atomic<unsigned long long> attr_done{0};
-  RIDC_TRY(raise_smem_limit_once(ridc1d_kernel, (int)(kOneDMaxSmemDoubles * sizeof(double)),
-                                 &attr_done));
+  const size_t smem = oned_smem_doubles(c->P, c->n, c->npad, c->nstages > 1) * sizeof(double);
+  static std::atomic<unsigned long long> attr_done{0}, attr_done_ark{0};
+  const bool ark = c->nstages > 1;
+  if (ark)
+    RIDC_TRY(raise_smem_limit_once(ridc1d_kernel<true>,
+                                   (int)(kOneDMaxSmemDoubles * sizeof(double)), &attr_done_ark));
+  else
+    RIDC_TRY(raise_smem_limit_once(ridc1d_kernel<false>,
+                                   (int)(kOneDMaxSmemDoubles * sizeof(double)), &attr_done));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(ONED_THREADS);
@@ -307,7 +386,8 @@ int launch_1d(Ctx* c, long nsteps_pipe, int init_only) {
   cfg.numAttrs = 1;
   cudaEvent_t e0;
   prof_begin(c, RIDC_KERNEL_1D, &e0);
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, ridc1d_kernel, a);
+  const cudaError_t e = ark ? cudaLaunchKernelEx(&cfg, ridc1d_kernel<true>, a)
+                            : cudaLaunchKernelEx(&cfg, ridc1d_kernel<false>, a);
   prof_end(c, RIDC_KERNEL_1D, e0);
   return cuda_status(e);
 }

@@ -208,13 +208,15 @@ struct Ctx {
   // X/W share xh/xl and Y/Z share yh/yl, each plane at the same addresses in every layout
   CUtensorMap tm_Xh, tm_Xl, tm_Yh, tm_Yl, tm_Wh, tm_Wl, tm_Zh, tm_Zl, tm_Bfh, tm_Bfl, tm_Bbh, tm_Bbl;
 
-  // 1D: constants of the tridiagonal solve and the quadrature weights, one table:
+  // 1D: constants of the tridiagonal solves and the quadrature weights, one table: for each
+  // operator (I - coef[k] dt D), k < ncoef, a block of oned_table_doubles(n, npad) values
   //   [0, npad]            rho^k
   //   npad+1               periodic: 1 / (1 - rho^n);  Dirichlet: kappa (Sherman-Morrison)
   //   npad+2               rho / mu
   //   [npad+3, npad+3+n)   Dirichlet: g = M^-1 e_{n-1}  (zeros when periodic)
-  //   then                 quadrature weights [P][P][P]
+  // then the quadrature weights [W][W][W]
   double* tri = nullptr;
+  double* st1d = nullptr;    // 1D ARK stages: F_i and f^N_i of stages 1..s-2, and Y ([2s+1][n])
   int npad = 0;              // n rounded up to a multiple of the 1D block size
   unsigned* sched_dev = nullptr;   // step masks of one 1D advance
   size_t sched_cap = 0;
@@ -342,10 +344,13 @@ constexpr int ONED_THREADS = 256;
 constexpr long kOneDMaxSmemDoubles = 28000;   // 224 KB of the 227 KB a CTA may use
 inline int oned_cluster(int P) { return P < 8 ? P : 8; }
 inline int oned_npad(int n) { return (n + ONED_THREADS - 1) / ONED_THREADS * ONED_THREADS; }
-inline long oned_smem_doubles(int P, int n, int npad) {
+// ark: an ARK predictor also keeps the powers of its stage operator's rho (npad + 1 more)
+inline long oned_smem_doubles(int P, int n, int npad, bool ark = false) {
   const long L = (P + oned_cluster(P) - 1) / oned_cluster(P);
-  return L * npad + L * n + npad + 1;
+  return L * npad + L * n + (ark ? 2L : 1L) * (npad + 1);
 }
+// 1D solver table of one operator (I - a dt D): rho^k (k <= npad), wrap or kappa, rho/mu, g[n]
+inline long oned_table_doubles(int n, int npad) { return (long)npad + 3 + n; }
 int launch_check_finite(Ctx* c, const double* x, long count, int* flag_dev);
 
 // epilogue kinds of the FP64 fast-diagonalisation GEMM

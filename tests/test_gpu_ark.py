@@ -11,7 +11,7 @@ import pytest
 
 import inputs
 import oracle
-from paper_1209_4297_gb300 import Batch, Integrator, RidcError
+from paper_1209_4297_gb300 import Integrator, RidcError
 from tests.gpu_util import need_cuda, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -170,5 +170,59 @@ def test_unsupported_requests():
         Integrator.from_workload(w, order=10, predictor="ark4")
     assert e.value.code == RIDC_ERR_UNSUPPORTED
     w1 = inputs.adv_diff_1d(n=64, nsteps=1)
-    with pytest.raises(RidcError):
-        Integrator.from_workload(w1, predictor="ark3").close()
+    with pytest.raises(RidcError):                   # 1D: the same width limit
+        Integrator.from_workload(w1, order=11, predictor="ark3").close()
+
+
+# ---------------------------------------------------------------- 1D (one SM per level)
+@pytest.mark.parametrize("predictor", ["ark3", "ark4"])
+def test_1d_periodic_workload_every_level(predictor):
+    """The 1D periodic advection-diffusion workload (N = 256, dt = 1/512) with an ARK
+    predictor and three correctors: order 6 (ARK3) or 7 (ARK4)."""
+    w = inputs.adv_diff_1d(nsteps=96)
+    _, levels, prog = _gpu(w, predictor, 4)
+    ref = _oracle(w, predictor, 4, all_levels=True)
+    assert prog == [96] * 4
+    for j in range(4):
+        assert rel_l2(levels[j], ref[j]) <= 1e-12, (j, rel_l2(levels[j], ref[j]))
+
+
+@pytest.mark.parametrize("predictor,order", [("ark3", 1), ("ark4", 2), ("ark3", 6), ("ark4", 9)])
+def test_1d_burgers_orders(predictor, order):
+    """Burgers' Dirichlet walls (Sherman-Morrison with each stage's own operator); order 9
+    with ARK4 puts two levels on CTA 0 of the 8-CTA cluster and the widest stencil (12)."""
+    w = inputs.burgers_1d(n=200, nsteps=37, T=0.037, order=order)
+    got, _, _ = _gpu(w, predictor, order)
+    assert rel_l2(got, _oracle(w, predictor, order)) <= 1e-12
+
+
+def test_1d_upwind_with_restarts_and_split_advance():
+    w = inputs.adv_diff_upwind_1d(n=300, nsteps=60, T=0.6, restarts=0)
+    a, _, _ = _gpu(w, "ark4", 3, restart_every=20)
+    b, _, _ = _gpu(w, "ark4", 3, restart_every=20, splits=[7, 13, 40])
+    np.testing.assert_array_equal(a, b)
+    ref = oracle.ridc_restarted(oracle.from_workload(w), w.u0, w.dt, 60, 3, 20, predictor="ark4")
+    assert rel_l2(a, ref) <= 1e-12
+
+
+def test_theorem2_order_6_on_the_1d_workload():
+    """ARK3 predictor + three first-order correctors on the 1D periodic workload's problem:
+    observed order 3 + 3 = 6 against its semi-discrete exact solution, on the GPU."""
+    def exact(w, t):
+        n, h = w.n, 1.0 / w.n
+        x = np.arange(n) / n
+        u = np.zeros(n)
+        for kk, (A, ph) in enumerate(zip(w.meta["amp"], w.meta["phase"])):
+            k = kk + 1
+            sig = 4 * np.sin(np.pi * k * h) ** 2 / h ** 2
+            om = np.sin(2 * np.pi * k * h) / h
+            u += A * np.exp(-w.nu[0] * sig * t) * np.sin(2 * np.pi * k * x + ph - w.a * om * t)
+        return u
+
+    errs = []
+    for N in (128, 256, 512):
+        w = inputs.adv_diff_1d(n=32, nsteps=N, dt=1.0 / N)
+        got, _, _ = _gpu(w, "ark3", 4)
+        errs.append(rel_l2(got, exact(w, 1.0)))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert slopes[-1] >= 5.85, (errs, slopes)
