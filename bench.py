@@ -253,8 +253,10 @@ def run_reference(args):
 
 
 def run_ensemble(args):
-    """The 512-instance ensemble (uneven Dirichlet advection-diffusion, FP32 solves with two
-    FP64-residual refinement passes: with one, the worst instance misses the 1e-8 bar) advanced 256 steps by one persistent launch; the autotuner
+    """The 512-instance ensemble (uneven Dirichlet advection-diffusion, solves at FP32 accuracy
+    on the tensor cores (TF32 hi/lo, three products) with two FP64-residual refinement passes:
+    with one, the worst instance misses the 1e-8 bar) advanced 256 steps by one persistent
+    launch; the autotuner
     picks the launch configuration first. Not the default line: a per-config measurement.
     --ens-count / --ens-steps shrink it (for profiling a small case)."""
     import torch
@@ -276,62 +278,172 @@ def run_ensemble(args):
         b.advance(nst)
     torch.cuda.synchronize()
     times = []
-    for _ in range(args.steps):
-        b.set_initial(u0s)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.advance(nst)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    b.close()
+    g0 = b.graph_launches()
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            b.set_initial(u0s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.advance(nst)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    graphs = b.graph_launches() - g0
     ms = statistics.median(times)
-    # algorithmic FP32 work of the solves: per advancing level and pass, four transforms,
-    # each two parity-split (side x side/2) x (side/2 x side/2) products = side^3 flop
+    # the oracle on a bounded sample: four instances (smallest work, a middle one, the
+    # largest, and the one with the strongest growth) over the first k steps; its time is
+    # the CPU baseline and its results the reference of the relative L2
+    import oracle
+    k_or = min(nst, args.oracle_steps or 16)
+    b.set_initial(u0s)
+    b.advance(k_or)
+    work = [w.order * w.n ** 3 for w in ws]
+    picks = sorted({int(np.argmin(work)), int(np.argsort(work)[len(ws) // 2]),
+                    int(np.argmax(work)), min(303, len(ws) - 1)})
+    rels, s_or, cells_or = [], 0.0, 0
+    for i in picks:
+        w = ws[i]
+        t0 = time.perf_counter()
+        ref = oracle.ridc_sequential(oracle.from_workload(w), w.u0, w.dt, k_or, w.order)[0]
+        s_or += time.perf_counter() - t0
+        cells_or += w.n * w.n * k_or
+        got = b.solution(i)
+        rels.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    b.close()
+    cpu = {"value": cells_or / s_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"instances {picks}, {k_or} steps each ({s_or:.1f} s, numpy/scipy FP64, "
+                     "single thread)"}
+    # algorithmic work of the launch. Solves: per advancing level and pass, four transforms,
+    # each two parity-split (side x side/2) x (side/2 x side/2) products = side^3 flop, run as
+    # three TF32 split products. FP64 phases, per cell of an advancing level (ens_step_ops):
+    # right-hand side 1 (predictor) or j+4, per refinement pass the residual stencil (5) and
+    # the running total (1 from the second pass), new state 2, f^N 4 and f 5 (levels that
+    # keep f).
     from paper_1209_4297_gb300 import schedule_plan
     passes = 1 + args.ens_refine
-    gemm_flops = 0.0
+    gemm_flops, fp64_ops = 0.0, 0.0
     for w in ws:
-        levels = sum(bin(int(m)).count("1") for m in schedule_plan(w.order, nst))
-        gemm_flops += levels * 4 * 1.0 * w.n ** 3 * passes
+        for m in schedule_plan(w.order, nst):
+            for j in range(w.order):
+                if not (int(m) >> j) & 1:
+                    continue
+                gemm_flops += 4 * 1.0 * w.n ** 3 * passes
+                keeps_f = j < w.order - 1 or j == 0
+                ops = ((1 if j == 0 else j + 4) + 5 * args.ens_refine + max(0, args.ens_refine - 1)
+                       + 2 + 4 + (5 if keeps_f else 0))
+                fp64_ops += ops * w.n * w.n
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    fp32_peak = sms * 128 * 2 * 2070e6   # FP32 lanes per SM x FMA x max SM clock
-    gemm_tf = gemm_flops / (ms * 1e-3) / 1e12
+    peaks, peak_src = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = FP64_OPS_PER_CLK_SM * sms * mhz * 1e6
+    tf32_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) / 2   # TF32 = BF16 / 2
+    secs = ms * 1e-3
+    gemm_tf = gemm_flops / secs / 1e12
     line = {"metric": f"ensemble cell-updates/s (sum over instances of side^2 x {nst} steps)",
             "value": cells * nst / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "dtype": "f64+fp32 solves", "data": "synthetic",
+            "dtype": "f64+tf32x3(fp32 acc) solves", "data": "synthetic", "gpu_launches": int(graphs),
+            "gpu_launches_note": "CUDA graphs of one persistent cluster kernel each",
+            "scaling": "weak", "vs_baseline": None,
+            "rel_l2_vs_oracle": {"value": max(rels), "instances": picks,
+                                 "per_instance": rels, "top_level_steps": k_or},
+            "cpu_baseline": None if args.no_cpu else cpu, "clocks": clk.summary(),
             "config": {"workload": f"ensemble_{count}_dirichlet_adv_diff", "instances": count,
                        "steps": nst, "n_refine": args.ens_refine, "autotune_choice": choice,
                        "launch": "one CUDA graph per advance (counter reset + persistent "
                                  "cluster launch)",
                        "cells_per_step": cells},
-            "roofline": {"bound": "alu", "kernel": "ensemble_kernel (FP32 SIMT solves)",
-                         "achieved": gemm_tf, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                         "frac": gemm_tf * 1e12 / fp32_peak,
-                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz "
-                                        "(nominal)",
-                         "dense_equivalent_tflops": 2 * gemm_tf,
-                         "note": "algorithmic FP32 flops of the parity-split solves (4 "
-                                 "transforms of side^3 flop per level and pass) over the whole "
-                                 "launch, which also runs the FP64 right-hand sides, residuals "
-                                 "and finalize"}}
+            "roofline": {"bound": "alu", "kernel": "ensemble_kernel (one persistent cluster "
+                         "launch: FP64 phases and TF32x3 tcgen05 solves)",
+                         "achieved": fp64_ops / secs, "peak": fp64_peak, "unit": "FP64 op/s",
+                         "frac": fp64_ops / secs / fp64_peak,
+                         "peak_source": f"{FP64_OPS_PER_CLK_SM} FP64 ops/clk/SM x {sms} SMs x "
+                                        f"{mhz:.0f} MHz (nominal FP64 pipe)",
+                         "work": "FP64 operations per cell of an advancing level: right-hand "
+                                 "side 1 or j+4, 5 per refinement residual (+1 running total "
+                                 "from the second pass), new state 2, f^N 4, f 5",
+                         "tensor": {"achieved_useful_tflops": gemm_tf,
+                                    "issued_tflops": 3 * gemm_tf, "peak": tf32_peak,
+                                    "frac_issued": 3 * gemm_tf / tf32_peak,
+                                    "peak_source": f"{peak_src} bf16_tflops_sustained / 2 "
+                                                   "(dense TF32 is half of BF16)"},
+                         "traffic": None,
+                         "note": "the whole launch, FP64 phases and solves together; neither "
+                                 "pipe is saturated: per-instance phases are separated by "
+                                 "cluster barriers"}}
     print(json.dumps(line), flush=True)
+
+
+# ---- per-config lines -----------------------------------------------------------------------
+# Algorithmic FP64 operations per cell of one level-step of the 1D kernel (an approximate count
+# of the operations the algorithm needs, stated so the FP64-pipe fraction can be checked):
+# right-hand side 1 (predictor, dt F) or j+4 (corrector j: two differences, one dt fma, j+1
+# quadrature fmas); solve 8 (backward recurrence and its carry, cyclic wrap, forward recurrence
+# with its rho/mu scaling, carry and wrap); new state 1; f^N 2 and F 4.
+ONED_SOLVE_OPS, ONED_STATE_OPS = 8, 7
+
+
+def planes_solved(mask: int, order: int, species: int, stages: int) -> int:
+    """Plane-solves of one pipeline step: every advancing level solves its species once, an
+    ARK predictor's level solves once per implicit stage (stages - 1)."""
+    act = [j for j in range(order) if (mask >> j) & 1]
+    n = 0
+    for j in act:
+        n += species * ((stages - 1) if (j == 0 and stages > 1) else 1)
+    return n
+
+
+def oned_ops(masks, order, n):
+    """Algorithmic FP64 operations of a 1D integration (counts above)."""
+    ops = 0.0
+    for m in masks:
+        for j in range(order):
+            if (int(m) >> j) & 1:
+                ops += ((1 if j == 0 else j + 4) + ONED_SOLVE_OPS + ONED_STATE_OPS) * n
+    return ops
+
+
+def _timed_integrations(it, u0, nt, runs, stream, prof):
+    """CUDA-event time (ms) of `runs` whole integrations from u0 (inputs resident), with
+    nvidia-smi clocks sampled meanwhile and kernel timing at period `prof`."""
+    import torch
+    it.set_profiling(prof)
+    launches0 = it.launch_count()
+    times = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(runs):
+            it.set_initial(u0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it.advance(nt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    kinds = ("rhs", "gemm_tc", "gemm_f64", "residual", "finalize", "ridc1d", "split_f16")
+    stats = {k: it.kernel_stats(k) for k in kinds}
+    it.set_profiling(False)
+    return times, it.launch_count() - launches0, stats, clk.summary()
 
 
 def run_single(args):
     """One of the other single-instance workloads, timed like the default line (whole
-    integrations, CUDA events, inputs resident): the 1D periodic workload (512 steps, FP64),
-    the paper's 1D runs (upwind advection-diffusion to T = 40 with 10 restart intervals;
-    viscous Burgers to T = 1),
-    1024^2 Gray-Scott in FP64 (a truncated run: its 2000 steps take minutes), the 4096^2
-    Dirichlet workload (512 steps, mixed, by default BF16x3 with 2 refinement passes) or the
-    2048^2 Gray-Scott workload in a chosen split form and refinement count
-    (--mixed-precision, --n-refine)."""
+    integrations, CUDA events, inputs resident, clocks sampled), with its dominant kernel's
+    roofline, the oracle on a bounded sample of the same workload (its time is the CPU
+    baseline, its result the reference of the line's relative L2), and for the 1D workloads
+    the same pipeline with one level (FBE) for the paper's wall-time comparison:
+      adv_diff_1d          the 1D periodic workload (N = 256, 512 steps, FP64)
+      adv_diff_upwind_1d   the paper's upwind advection-diffusion run (T = 40, 10 restarts)
+      burgers_1d           the paper's viscous Burgers run (T = 1)
+      gray_scott_1024_fp64 1024^2 Gray-Scott in FP64, all 2000 steps
+      gray_scott_2048_mixed the headline grid in a chosen form (--mixed-precision, --n-refine,
+                           --order, --predictor)
+      adv_diff_4096        the 4096^2 Dirichlet workload (512 steps, mixed)
+    --predictor ark3 / ark4 runs any of them with an ARK predictor (Theorem 2)."""
     import torch
 
     import inputs
-    from paper_1209_4297_gb300 import Integrator
+    import oracle
+    from paper_1209_4297_gb300 import Integrator, schedule_plan_predictor
 
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
@@ -342,61 +454,139 @@ def run_single(args):
     elif args.workload == "burgers_1d":
         w, prec, nt = inputs.burgers_1d(), "fp64", 2000
     elif args.workload == "gray_scott_1024_fp64":
-        w, prec, nt = inputs.gray_scott_2d(n=1024, nsteps=2000), "fp64", args.nt_truncate
+        w, prec, nt = inputs.gray_scott_2d(n=1024, nsteps=2000), "fp64", 2000
     elif args.workload == "gray_scott_2048_mixed":
         w, prec, nt = inputs.gray_scott_2d(n=2048, nsteps=1000), args.mixed_precision, args.nt
     else:
         w, prec, nt = inputs.adv_diff_2d(n=4096, nsteps=512), args.mixed_precision, 512
-    u0 = torch.from_numpy(w.u0).cuda()
-
-    def timed(order):
-        it = Integrator.from_workload(w, precision=prec, n_refine=args.n_refine,
-                                      stream=stream.cuda_stream, order=order)
-        for _ in range(args.warmup):
-            it.set_initial(u0)
-            it.advance(nt)
-        torch.cuda.synchronize()
-        times = []
-        launches0 = it.launch_count()
-        for _ in range(args.steps):
-            it.set_initial(u0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            it.advance(nt)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        launches = it.launch_count() - launches0
-        it.close()
-        return statistics.median(times), launches
-
     order = args.order or w.order
-    ms, launches = timed(order)
-    # the paper's claim in one-GPU form: the whole RIDC-4 pipeline against plain FBE (one
-    # level) on the same workload and step count
-    fbe_ms = timed(1)[0] if w.dim == 1 else None
-    cells = (w.n if w.dim == 1 else w.n * w.n) * nt
-    cpu = None
-    if w.dim == 1 and not args.no_cpu:
-        # the oracle on the whole workload (restarted where the workload restarts)
-        import oracle
-        t0 = time.perf_counter()
-        oracle.ridc_restarted(oracle.from_workload(w), w.u0, w.dt, nt, order, w.restart_every)
-        s = time.perf_counter() - t0
-        cpu = {"value": cells / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the whole workload ({s:.1f} s, numpy/scipy FP64, dense LU solves)"}
-    line = {"metric": f"RIDC-{order} cell-updates/s", "value": cells / (ms * 1e-3), "unit": UNIT,
+    pred = args.predictor
+    stages = {"fbe": 1, "ark3": 5, "ark4": 7}[pred]
+    S = w.species
+    u0 = torch.from_numpy(w.u0).cuda()
+    kw = dict(precision=prec, n_refine=args.n_refine, stream=stream.cuda_stream)
+
+    # warm-up: W integrations, at most 40 steps each for the long lines (tables, caches and
+    # clocks are warm after the first); then K whole integrations are timed
+    warm_nt = nt if nt <= 600 else 40
+    it = Integrator.from_workload(w, order=order, predictor=pred, **kw)
+    for _ in range(args.warmup):
+        it.set_initial(u0)
+        it.advance(warm_nt)
+    torch.cuda.synchronize()
+    prof = 1 if w.dim == 1 else PROF_EVERY
+    times, launches, stats, clocks = _timed_integrations(it, u0, nt, args.steps, stream, prof)
+    ms = statistics.median(times)
+    cells_side = w.n if w.dim == 1 else w.n * w.n
+    cells = cells_side * nt
+    masks = schedule_plan_predictor(order, pred, nt)
+    peaks, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = FP64_OPS_PER_CLK_SM * sms * mhz * 1e6
+
+    # ---- roofline of the dominant kernel (work of the sampled steps over their launch time)
+    sampled = masks[::prof]
+    passes = 1 if prec == "fp64" else 1 + args.n_refine
+    roof = None
+    if w.dim == 1:
+        n_l, ms_l = stats["ridc1d"]
+        cl = min(order, 8)
+        ops = oned_ops(masks, order, w.n) * args.steps
+        peak = FP64_OPS_PER_CLK_SM * cl * mhz * 1e6
+        if ms_l > 0:
+            roof = {"bound": "alu", "kernel": "ridc1d_kernel (one SM per level, cluster of "
+                    f"{cl})", "achieved": ops / (ms_l * 1e-3), "peak": peak,
+                    "unit": "FP64 op/s", "frac": ops / (ms_l * 1e-3) / peak,
+                    "peak_source": f"{FP64_OPS_PER_CLK_SM} FP64 ops/clk/SM x {cl} SMs x "
+                                   f"{mhz:.0f} MHz (the SMs the launch uses)",
+                    "work": "about (rhs + 8 solve + 7 state) FP64 ops per cell per level-step",
+                    "traffic": None,
+                    "note": "latency-bound: a step is a chain of block-wide scans and one "
+                            "cluster barrier"}
+    elif prec == "fp64":
+        n_g, ms_g = stats["gemm_f64"]
+        per = 4.0 * w.n ** 3 if w.n % 2 == 0 else 8.0 * w.n ** 3   # per plane-solve
+        flops = sum(planes_solved(int(m), order, S, stages) for m in sampled) * per * args.steps
+        if ms_g > 0:
+            ach = flops / (ms_g * 1e-3)
+            roof = {"bound": "alu", "kernel": "gemm_f64_split_kernel (parity-split DFMA fast "
+                    "diagonalisation)", "achieved": ach / 1e12, "peak": 2 * fp64_peak / 1e12,
+                    "unit": "TFLOP/s", "frac": ach / (2 * fp64_peak),
+                    "peak_source": f"{FP64_OPS_PER_CLK_SM} DFMA/clk/SM x {sms} SMs x "
+                                   f"{mhz:.0f} MHz x 2 flop (nominal FP64 pipe)",
+                    "work": "N^3 flop per plane per transform (parity split), 4 transforms "
+                            "per solve", "traffic": None,
+                    "avg_launch_ms": ms_g / n_g if n_g else None}
+    else:
+        n_t, ms_t = stats["gemm_tc"]
+        flops = (sum(planes_solved(int(m), order, S, stages) for m in sampled)
+                 * 4 * passes * 3.0 * w.n ** 3 * args.steps)
+        peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        if ms_t > 0:
+            ach = flops / (ms_t * 1e-3) / 1e12
+            roof = {"bound": "tensor", "kernel": "gemm_sym_kernel (parity-split "
+                    f"{prec[6:].upper()} tcgen05)", "achieved": ach, "peak": peak_tf,
+                    "unit": "TFLOP/s", "frac": ach / peak_tf,
+                    "peak_source": f"{peak_src} bf16_tflops_sustained",
+                    "useful_tflops": ach / 3, "work": "3 N^3 flop per plane per transform "
+                    "(three split products), 4 transforms per pass", "traffic": None,
+                    "avg_launch_ms": ms_t / n_t if n_t else None}
+    share = {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items() if v[0]}
+
+    # ---- FBE on the same path (1D: the paper's wall-time comparison)
+    fbe_ms = None
+    if w.dim == 1 and order > 1:
+        it1 = Integrator.from_workload(w, order=1, **kw)
+        t1, _, _, _ = _timed_integrations(it1, u0, nt, args.steps, stream, 0)
+        it1.close()
+        fbe_ms = statistics.median(t1)
+
+    # ---- the oracle on a bounded sample: CPU baseline and the reference of the rel. L2
+    if w.dim == 1:
+        k_or = nt                                  # the whole workload
+    elif w.n <= 1024:
+        k_or = args.oracle_steps or 12
+    else:
+        k_or = args.oracle_steps or 2
+    it.set_initial(u0)
+    it.advance(k_or)
+    got = it.solution()
+    it.close()
+    t0 = time.perf_counter()
+    ref = oracle.ridc_restarted(oracle.from_workload(w), w.u0, w.dt, k_or, order,
+                                w.restart_every, predictor=pred)
+    s_or = time.perf_counter() - t0
+    # the oracle runs its lower levels ahead to the top level's start-up nodes, so its rate
+    # counts the top level's steps only, as the GPU line does
+    cpu = {"value": cells_side * k_or / s_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{k_or} top-level steps of this workload ({s_or:.1f} s, numpy/scipy "
+                     "FP64, single thread)"}
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    line = {"metric": f"RIDC-{order} cell-updates/s" + ("" if pred == "fbe" else
+                                                         f", {pred.upper()} predictor"),
+            "value": cells / (ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "us_per_pipeline_step": 1e3 * ms / (nt + order * (order - 1) // 2),
-            "higher_is_better": True,
+            "us_per_pipeline_step": 1e3 * ms / len(masks),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else f"f64+{prec[6:]}(fp32 acc)",
             "data": "synthetic", "gpu_launches": int(launches),
             "fbe_ms": fbe_ms, "ridc_over_fbe_time": (ms / fbe_ms) if fbe_ms else None,
             "config": {"workload": args.workload, "grid": w.n, "order": order,
-                       "top_level_steps": nt, "full_steps": w.nsteps, "dt": w.dt,
-                       "restart_every": w.restart_every,
-                       "n_refine": None if prec == "fp64" else args.n_refine},
-            "cpu_baseline": cpu}
+                       "predictor": pred, "formal_order": order - 1 +
+                       {"fbe": 1, "ark3": 3, "ark4": 4}[pred],
+                       "top_level_steps": nt, "pipeline_steps": int(len(masks)),
+                       "dt": w.dt, "restart_every": w.restart_every,
+                       "n_refine": None if prec == "fp64" else args.n_refine,
+                       "warmup_integrations": f"{args.warmup} of {warm_nt} steps",
+                       "l2": "inputs larger than L2" if w.dim == 2 and S * w.n * w.n * 8 *
+                             order * 4 > 129e6 else "working set fits in L2"},
+            "roofline": roof,
+            "kernel_ms": share,
+            "rel_l2_vs_oracle": {"value": rel, "top_level_steps": k_or},
+            "cpu_baseline": None if args.no_cpu else cpu,
+            "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -478,7 +668,11 @@ def main():
                     help="instances of the ensemble line (the configuration has 512)")
     ap.add_argument("--ens-steps", type=int, default=256,
                     help="steps of the ensemble line (the configuration has 256)")
-    ap.add_argument("--nt-truncate", type=int, default=60)
+    ap.add_argument("--oracle-steps", type=int, default=0,
+                    help="top-level steps of the oracle sample of a 2D single-workload line "
+                         "(0: 12 up to 1024^2, 2 above)")
+    ap.add_argument("--predictor", default="fbe", choices=["fbe", "ark3", "ark4"],
+                    help="level-0 predictor of the single-workload lines (Theorem 2)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

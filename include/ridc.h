@@ -237,8 +237,10 @@ int ridc_solve_planes_fixed(int kind, int n, const double* nu, double dt, const 
 /* Many independent instances of RIDC_ADV_DIFF_2D_DIRICHLET (uneven grid sides 32..512, each a
  * multiple of 32 for the parity-split solves; orders 1..4; own a, b, nu and dt) advanced
  * together by one persistent kernel launch: a cluster of CTAs integrates each instance,
- * largest instances first. Solves run in FP32 (problem.precision must be RIDC_FP32_SOLVE);
- * everything else is FP64, as in ridc_create.
+ * largest instances first. Solves run at FP32 accuracy on the tensor cores (problem.precision
+ * must be RIDC_FP32_SOLVE): FP32 operands split into TF32 hi + lo, three products per
+ * transform (about 22 significant bits) with FP32 accumulation; everything else is FP64, as in
+ * ridc_create.
  * The paper integrates one instance at a time; batching many is this library's addition.
  *   count      : number of instances; problems, grids, nu, dt, order are arrays of `count`.
  *   n_refine   : must be the same for all instances (0..4 refinement passes).
@@ -256,26 +258,24 @@ int ridc_batch_set_initial(ridc_batch b, const double* const* u0, int on_device)
  * (one kernel launch). Stream-ordered; returns after launching.                            */
 int ridc_batch_advance(ridc_batch b, long nsteps);
 
-/* Copy instance i's most corrected level (n_i*n_i values). Synchronises the stream.       */
+/* Copy instance i's most corrected level (n_i*n_i values). Synchronises the stream.
+ * RIDC_ERR_TIMEOUT (once) if a bounded device-side wait of an earlier advance gave up.      */
 int ridc_batch_get_solution(ridc_batch b, int i, double* out, size_t count, int out_on_device);
 
 /* Sum over instances of n_i^2: the cell-updates one top-level step performs.               */
 long ridc_batch_cells(ridc_batch b);
 
-/* Autotuner: picks, per grid side, the GEMM tile (64 x 32 or 128 x 64 rows x half-columns of
- * the parity-split products) that integrates that
- * side's instances fastest, then the cluster size (1, 2 or 4 CTAs cooperating on each
- * instance) and the CTAs per SM (1 or 2) that run the whole batch fastest; each trial
+/* Autotuner: picks the cluster size (1, 2 or 4 CTAs cooperating on each instance) and the
+ * CTAs per SM (1 or 2) that run the whole batch fastest (the tensor-core tile, 128 rows by the
+ * widest multiple of 16 up to 64 that divides side/2, follows from each grid side); each trial
  * advances `nsteps` steps of the real batch. The choice is kept for later advances. Requires
  * an initial state and leaves the state undefined: call ridc_batch_set_initial afterwards.
- * *choice = CTAs per SM * 16 + cluster size (the launch shape; the tile per side stays in
- * the batch); *best_ms = the fastest whole-batch trial.                                    */
+ * *choice = CTAs per SM * 16 + cluster size; *best_ms = the fastest whole-batch trial.     */
 int ridc_batch_autotune(ridc_batch b, long nsteps, int* choice, float* best_ms);
 
 /* Use launch shape `choice` (CTAs per SM * 16 + cluster size, as ridc_batch_autotune reports
  * it: 1 or 2 CTAs per SM, clusters of 1, 2 or 4 CTAs) for later advances, e.g. one tuned
- * earlier on the same batch. Tiles keep the autotuner's choice, or before any autotuning
- * the larger tile for sides >= 128. RIDC_ERR_ARG for another value.                        */
+ * earlier on the same batch. RIDC_ERR_ARG for another value.                                */
 int ridc_batch_set_launch(ridc_batch b, int choice);
 
 /* CUDA-graph launches so far: every advance (and every autotuner trial) is one graph of a

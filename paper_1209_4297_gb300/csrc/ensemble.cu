@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "ridc_internal.h"
+#include "tc_util.cuh"
 
 namespace ridc {
 
@@ -86,8 +87,6 @@ struct EnsClass {
   const float* Qs;   // [s][s]  Qs[x][c] = Q[x][k]: Q with its columns in split order
   const float* lam;  // [s]     eigenvalues in split order
   int s;
-  int variant;       // GEMM tile: 0 = 64 rows x 32 half-columns (4 x 2+2 per thread),
-                     //            1 = 128 rows x 64 half-columns (8 x 4+4 per thread)
 };
 
 struct EnsArgs {
@@ -102,169 +101,209 @@ struct EnsArgs {
   const double* wq;   // [kMaxOrder][kMaxOrder][kMaxOrder]
   double* r_ws;       // per cluster: [EMaxP][s_max^2] FP64
   double* d_ws;       // per cluster: [EMaxP][s_max^2] FP64 (refinement total)
+  int* err;           // set when a bounded device wait gives up
   float* f_ws;        // per cluster: 3 x [EMaxP][s_max^2] FP32 (operand, two intermediates)
   long ws_plane;
   int nref;
 };
 
-// ---- cluster-level FP32 GEMMs of the fast diagonalisation, parity-split ----------------------
+// ---- cluster-level GEMMs of the fast diagonalisation on the tensor cores, parity-split -------
 // The sine eigenvectors obey Q[s-1-x][k] = (-1)^k Q[x][k]. With H = s/2 and spectral indices
 // in split order (even k, then odd k: c = g H + k', k = 2k' + g) every transform is two
 // (rows x H) x (H x H) products instead of one (rows x s) x (s x s): half the flops.
 //   forward (FWD): out[.][g H + k'] = sum_{x'<H} (A[x'] +- A[s-1-x']) Q[x'][2k'+g]; A is
-//                  butterflied as it is loaded, B rows are rows of Qts (Q^T in split order);
+//                  butterflied as it is staged, B rows are rows of Qts (Q^T in split order);
 //   inverse:       out[.][x'] = E + O, out[.][s-1-x'] = E - O with E = sum_{k'} A[k'] Q[x'][2k'],
 //                  O = sum_{k'} A[H+k'] Q[x'][2k'+1]; B rows are rows of Qs (Q, columns in
 //                  split order).
-// Every thread accumulates both halves (TM rows x TN/2 columns each), so a block tile covers
-// 16 TM rows x 8 TN half-columns. Results are stored transposed per plane, out[plane][m][row %
-// s], optionally times 1/(1 - dtnu (lam[row % s] + lam[m])) (forward, split order). Tiles are
-// dealt round-robin to the CL CTAs of the cluster. 16-deep K slices: the next slice is fetched
-// into registers (float4) while the current one is multiplied out of shared memory.
-template <int TM, int TN>
-struct DualSmem {
-  float A[2][2][16][16 * TM + 4];   // [half][buffer][k][row]
-  float B[2][2][16][8 * TN + 4];    // [half][buffer][k][column]
+// Results are stored transposed per plane, out[plane][m][row % s], optionally times
+// 1/(1 - dtnu (lam[row % s] + lam[m])) (forward, split order).
+//
+// Each product runs on the 5th-generation tensor cores as kind::tf32 with split operands:
+// v = hi + lo, hi = v rounded to TF32 (10 fraction bits), lo = v - hi (exact in FP32) rounded
+// to TF32 too, and C ~= Ah Bh + Ah Bl + Al Bh, about 22 significant bits per product with FP32
+// accumulation in tensor memory: the accuracy of the FP32 solves it replaces. A tile is 128
+// rows (M) by BN half-columns (N, a multiple of 16 up to 64 that divides H) per parity half,
+// both halves accumulated side by side in 2 BN TMEM columns. K advances in slices of 32 values
+// (128-byte rows, 128B swizzle): all 256 threads load a slice from global memory (float4),
+// butterfly, split and write it to shared memory, one thread issues its 24 MMAs (2 halves x 3
+// products x 4 steps of K = 8) and commits them to an mbarrier, and every thread waits on that
+// barrier (bounded) before the slice buffer is reused. The epilogue reads the accumulators
+// with tcgen05.ld: warp w covers TMEM lanes (= tile rows) 32 (w % 4).. and every other group
+// of 16 columns. Tiles are dealt round-robin to the CL CTAs of the cluster.
+constexpr int UM_BM = 128, UM_BK = 32, UM_MAXBN = 64;
+constexpr int UM_TILE_A = UM_BM * UM_BK * 4;       // 16 KB: 128 rows x 32 FP32
+constexpr int UM_TILE_B = UM_MAXBN * UM_BK * 4;    // 8 KB
+constexpr uint32_t UM_TMEM_COLS = 2 * UM_MAXBN;    // two halves of BN <= 64 FP32 columns
+struct UmmaSmem {                                  // 1 KB aligned
+  unsigned char a[2][2][UM_TILE_A];                // [half][hi, lo]
+  unsigned char b[2][2][UM_TILE_B];                // [half][hi, lo]
 };
-constexpr size_t ENS_SMEM_BYTES =
-    sizeof(DualSmem<8, 8>) > sizeof(DualSmem<4, 4>) ? sizeof(DualSmem<8, 8>) : sizeof(DualSmem<4, 4>);
+constexpr size_t ENS_SMEM_BYTES = sizeof(UmmaSmem) + 1024;   // + alignment slack
+
+// per-CTA state of the tensor-core GEMMs: tensor-memory base, the MMA-completion mbarrier and
+// the number of commits so far (every thread counts them alike, so the parity is known)
+struct UmmaState {
+  uint32_t tmem;
+  uint32_t bar;
+  uint32_t commits;
+  int* err;
+};
+
+// tile column width: the largest multiple of 16 up to 64 that divides H (H = s/2, s a
+// multiple of 32)
+__device__ __forceinline__ int um_bn(int H) {
+  for (int bn = UM_MAXBN; bn >= 16; bn -= 16)
+    if (H % bn == 0) return bn;
+  return 16;
+}
+
+// v ~= hi + lo, both TF32 values in FP32 words
+__device__ __forceinline__ void um_split(float v, float& hi, float& lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+  const float r = v - __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+  hi = __uint_as_float(h);
+  lo = __uint_as_float(l);
+}
+
+// write the split of 4 consecutive K values (chunk c of row r) into hi and lo tiles with the
+// 128B swizzle: the 16-byte chunk index is XORed with r % 8
+__device__ __forceinline__ void um_put(unsigned char* hi, unsigned char* lo, int r, int c, float4 v) {
+  float4 h, l;
+  um_split(v.x, h.x, l.x);
+  um_split(v.y, h.y, l.y);
+  um_split(v.z, h.z, l.z);
+  um_split(v.w, h.w, l.w);
+  const int off = r * 128 + ((c ^ (r & 7)) << 4);
+  *reinterpret_cast<float4*>(hi + off) = h;
+  *reinterpret_cast<float4*>(lo + off) = l;
+}
 
 __device__ __forceinline__ float4 f4_add(float4 a, float4 b, float sg) {
   return make_float4(a.x + sg * b.x, a.y + sg * b.y, a.z + sg * b.z, a.w + sg * b.w);
 }
 
-template <int TM, int TN, bool FWD>
-__device__ void dual_sgemm(const float* __restrict__ A, const float* __restrict__ B,
-                           float* __restrict__ out, int s, int rows, const float* lam,
-                           float dtnu, bool scale, DualSmem<TM, TN>& sm, int rank, int CL) {
-  constexpr int BM = 16 * TM, BH = 8 * TN, TH = TN / 2;
-  constexpr int AV = BM * 4 / ENS_THREADS;            // float4 of A per thread and half
-  constexpr int BV = (BH * 4 + ENS_THREADS - 1) / ENS_THREADS;
-  const int t = threadIdx.x;
-  const int tr = t & 15, tc = t >> 4;
-  const int H = s / 2;
-  const int nrt = (rows + BM - 1) / BM, nct = (H + BH - 1) / BH;
-  const int KT = H / 16;
+// bounded wait for the latest commit; false (and the error flagged) if it never completes
+// or an earlier wait already gave up
+__device__ __forceinline__ bool um_wait(UmmaState& st) {
+  if (*(volatile int*)st.err) return false;
+  return tc::s_wait(st.bar, (st.commits - 1) & 1u, st.err);
+}
+
+template <bool FWD>
+__device__ void dual_umma(const float* __restrict__ A, const float* __restrict__ B,
+                          float* __restrict__ out, int s, int rows, const float* lam,
+                          float dtnu, bool scale, UmmaSmem& sm, UmmaState& st, int rank, int CL) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int H = s / 2, BN = um_bn(H);
+  const int nrt = (rows + UM_BM - 1) / UM_BM, nct = H / BN;
+  const int KS = (H + UM_BK - 1) / UM_BK;
+  // instruction descriptor, kind::tf32: FP32 accumulator (bits 4-5 = 1), A and B TF32 (bits
+  // 7-9 and 10-12 = 2), both K-major, N / 8 (bits 17-22), M / 16 (bits 24-28)
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(UM_BM >> 4) << 24);
   for (int tile = rank; tile < nrt * nct; tile += CL) {
-    const int row0 = (tile / nct) * BM, col0 = (tile % nct) * BH;
-    float acc[2][TM][TH];
+    const int row0 = (tile / nct) * UM_BM, col0 = (tile % nct) * BN;
+    for (int kb = 0; kb < KS; ++kb) {
+      const int k0 = kb * UM_BK;
+      // the previous MMAs still read the slice buffers; the decision to give up is made by
+      // the whole CTA together, so every thread leaves at the same point
+      const bool ok = st.commits == 0 || um_wait(st);
+      if (__syncthreads_or(!ok)) return;
+      // A: 128 rows x 8 chunks of 4 K values per half; 4 chunks per thread
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TH; ++j) acc[h][i][j] = 0.f;
-    float4 ra[2][AV], rb[2][BV];
-    auto fetch = [&](int kt) {
-#pragma unroll
-      for (int v = 0; v < AV; ++v) {
-        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3, gr = row0 + lr;
-        const int k0 = kt * 16 + q * 4;
-        if (gr < rows) {
+      for (int v = 0; v < UM_BM * 8 / ENS_THREADS; ++v) {
+        const int e = t + v * ENS_THREADS, r = e >> 3, c = e & 7, gr = row0 + r;
+        const int k = k0 + c * 4;
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+        if (gr < rows && k < H) {
           const float* ar = A + (long)gr * s;
           if (FWD) {
-            // x' = k0..k0+3 and their mirrors s-1-x' (a reversed float4)
-            const float4 x = *reinterpret_cast<const float4*>(ar + k0);
-            const float4 m4 = *reinterpret_cast<const float4*>(ar + s - 4 - k0);
+            // x' = k..k+3 and their mirrors s-1-x' (a reversed float4)
+            const float4 x = *reinterpret_cast<const float4*>(ar + k);
+            const float4 m4 = *reinterpret_cast<const float4*>(ar + s - 4 - k);
             const float4 m = make_float4(m4.w, m4.z, m4.y, m4.x);
-            ra[0][v] = f4_add(x, m, 1.f);
-            ra[1][v] = f4_add(x, m, -1.f);
+            a0 = f4_add(x, m, 1.f);
+            a1 = f4_add(x, m, -1.f);
           } else {
-            ra[0][v] = *reinterpret_cast<const float4*>(ar + k0);
-            ra[1][v] = *reinterpret_cast<const float4*>(ar + H + k0);
+            a0 = *reinterpret_cast<const float4*>(ar + k);
+            a1 = *reinterpret_cast<const float4*>(ar + H + k);
           }
-        } else {
-          ra[0][v] = ra[1][v] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        um_put(sm.a[0][0], sm.a[0][1], r, c, a0);
+        um_put(sm.a[1][0], sm.a[1][1], r, c, a1);
       }
-#pragma unroll
-      for (int v = 0; v < BV; ++v) {
-        const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3, gc = col0 + lr;
-        const int k0 = kt * 16 + q * 4;
-        if (e < BH * 4 && gc < H) {
+      // B: BN rows x 8 chunks per half
+      for (int e = t; e < BN * 8; e += ENS_THREADS) {
+        const int r = e >> 3, c = e & 7, gc = col0 + r;
+        const int k = k0 + c * 4;
+        float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+        if (k < H) {
           // forward: rows k' and H + k' of Qts; inverse: row x' of Qs, columns k' and H + k'
-          const float* b0 = FWD ? B + (long)gc * s + k0 : B + (long)gc * s + k0;
-          const float* b1 = FWD ? B + (long)(H + gc) * s + k0 : B + (long)gc * s + H + k0;
-          rb[0][v] = *reinterpret_cast<const float4*>(b0);
-          rb[1][v] = *reinterpret_cast<const float4*>(b1);
-        } else {
-          rb[0][v] = rb[1][v] = make_float4(0.f, 0.f, 0.f, 0.f);
+          b0 = *reinterpret_cast<const float4*>(B + (long)gc * s + k);
+          b1 = FWD ? *reinterpret_cast<const float4*>(B + (long)(H + gc) * s + k)
+                   : *reinterpret_cast<const float4*>(B + (long)gc * s + H + k);
         }
+        um_put(sm.b[0][0], sm.b[0][1], r, c, b0);
+        um_put(sm.b[1][0], sm.b[1][1], r, c, b1);
       }
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-#pragma unroll
-        for (int v = 0; v < AV; ++v) {
-          const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
-          sm.A[h][buf][q * 4 + 0][lr] = ra[h][v].x;
-          sm.A[h][buf][q * 4 + 1][lr] = ra[h][v].y;
-          sm.A[h][buf][q * 4 + 2][lr] = ra[h][v].z;
-          sm.A[h][buf][q * 4 + 3][lr] = ra[h][v].w;
-        }
-#pragma unroll
-        for (int v = 0; v < BV; ++v) {
-          const int e = t + v * ENS_THREADS, lr = e >> 2, q = e & 3;
-          if (e < BH * 4) {
-            sm.B[h][buf][q * 4 + 0][lr] = rb[h][v].x;
-            sm.B[h][buf][q * 4 + 1][lr] = rb[h][v].y;
-            sm.B[h][buf][q * 4 + 2][lr] = rb[h][v].z;
-            sm.B[h][buf][q * 4 + 3][lr] = rb[h][v].w;
-          }
-        }
-      }
-    };
-    __syncthreads();
-    fetch(0);
-    stash(0);
-    __syncthreads();
-    for (int kt = 0; kt < KT; ++kt) {
-      const int buf = kt & 1;
-      if (kt + 1 < KT) fetch(kt + 1);
-#pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
+      tc::s_fence_async_smem();
+      __syncthreads();
+      if (t == 0) {
+        tc::s_fence_after();
+        const int kst = min(4, (H - k0) / 8);   // H is a multiple of 16: 2 or 4 steps
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          float av[TM], bv[TH];
-#pragma unroll
-          for (int i = 0; i < TM; ++i) av[i] = sm.A[h][buf][kk][tr * TM + i];
-#pragma unroll
-          for (int j = 0; j < TH; ++j) bv[j] = sm.B[h][buf][kk][tc * TH + j];
-#pragma unroll
-          for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TH; ++j) acc[h][i][j] = fmaf(av[i], bv[j], acc[h][i][j]);
-        }
-      }
-      if (kt + 1 < KT) stash(buf ^ 1);
-      __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int gr = row0 + tr * TM + i;
-      if (gr >= rows) continue;
-      const int plane = gr / s, rl = gr - plane * s;
-      float* op = out + (long)plane * s * s;
-#pragma unroll
-      for (int j = 0; j < TH; ++j) {
-        const int c = col0 + tc * TH + j;   // k' (forward) or x' (inverse), < H
-        if (c >= H) continue;
-        if (FWD) {
-          float v0 = acc[0][i][j], v1 = acc[1][i][j];
-          if (scale) {
-            v0 = __fdividef(v0, 1.0f - dtnu * (lam[rl] + lam[c]));
-            v1 = __fdividef(v1, 1.0f - dtnu * (lam[rl] + lam[H + c]));
+          const uint64_t ah = tc::s_desc(tc::s_u32(sm.a[h][0])), al = tc::s_desc(tc::s_u32(sm.a[h][1]));
+          const uint64_t bh = tc::s_desc(tc::s_u32(sm.b[h][0])), bl = tc::s_desc(tc::s_u32(sm.b[h][1]));
+          const uint32_t acc = st.tmem + (uint32_t)(h * BN);
+          for (int ks = 0; ks < kst; ++ks) {
+            const uint64_t adv = (uint64_t)(ks * 32 >> 4);   // 8 FP32 = 32 bytes along K
+            tc::s_mma_tf32(acc, ah + adv, bh + adv, idesc, (kb | ks) != 0);
+            tc::s_mma_tf32(acc, ah + adv, bl + adv, idesc, 1);
+            tc::s_mma_tf32(acc, al + adv, bh + adv, idesc, 1);
           }
-          op[(long)c * s + rl] = v0;
-          op[(long)(H + c) * s + rl] = v1;
+        }
+        tc::s_commit(st.bar);
+      }
+      ++st.commits;
+    }
+    if (__syncthreads_or(!um_wait(st))) return;
+    tc::s_fence_after();
+    // epilogue: TMEM lane = tile row; warp w reads lanes 32 (w % 4).. and column groups of 16
+    const int rl0 = row0 + 32 * (warp & 3) + lane;
+    const bool live = rl0 < rows;
+    const int plane = live ? rl0 / s : 0, rl = rl0 - plane * s;
+    float* op = out + (long)plane * s * s;
+    const uint32_t tl = st.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int ch = warp >> 2; ch < BN / 16; ch += 2) {
+      uint32_t v0[16], v1[16];
+      tc::s_ld16(tl + (uint32_t)(ch * 16), v0);
+      tc::s_ld16(tl + (uint32_t)(BN + ch * 16), v1);
+      tc::s_ld_wait();
+      if (!live) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = col0 + ch * 16 + j;   // k' (forward) or x' (inverse), < H
+        float x0 = __uint_as_float(v0[j]), x1 = __uint_as_float(v1[j]);
+        if (FWD) {
+          if (scale) {
+            x0 = __fdividef(x0, 1.0f - dtnu * (lam[rl] + lam[c]));
+            x1 = __fdividef(x1, 1.0f - dtnu * (lam[rl] + lam[H + c]));
+          }
+          op[(long)c * s + rl] = x0;
+          op[(long)(H + c) * s + rl] = x1;
         } else {
-          const float ev = acc[0][i][j], ov = acc[1][i][j];
-          op[(long)c * s + rl] = ev + ov;
-          op[(long)(s - 1 - c) * s + rl] = ev - ov;
+          op[(long)c * s + rl] = x0 + x1;
+          op[(long)(s - 1 - c) * s + rl] = x0 - x1;
         }
       }
     }
+    // the accumulators are free again once every thread has read them (the next tile's MMAs
+    // are issued after the barrier of its first slice)
+    tc::s_fence_before();
   }
 }
 
@@ -311,37 +350,43 @@ __device__ __forceinline__ void csync() {
   else __syncthreads();
 }
 
-// FP32 fast-diagonalisation solve of np planes: df = Q ((Q^T rf Q) ./ den) Q^T, each transform
-// as a parity-split pair of half-size products (spectral indices in split order throughout)
-template <int CL, int TM, int TN>
-__device__ void cl_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf, float* t1,
-                         float* t2, float* df, DualSmem<TM, TN>& sm, int rank) {
-  const int s = C.s, rows = np * s;
-  dual_sgemm<TM, TN, true>(rf, C.Qts, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
-  csync<CL>();
-  dual_sgemm<TM, TN, true>(t1, C.Qts, t2, s, rows, C.lam, I.dtnu, true, sm, rank, CL);
-  csync<CL>();
-  dual_sgemm<TM, TN, false>(t2, C.Qs, t1, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
-  csync<CL>();
-  dual_sgemm<TM, TN, false>(t1, C.Qs, df, s, rows, C.lam, I.dtnu, false, sm, rank, CL);
-  csync<CL>();
-}
-
+// Fast-diagonalisation solve of np planes on the tensor cores: df = Q ((Q^T rf Q) ./ den) Q^T,
+// each transform as a parity-split pair of half-size products (spectral indices in split
+// order throughout), FP32 in and out
 template <int CL>
-__device__ __forceinline__ void solve_any(const EnsClass& C, const EnsInst& I, int np,
-                                          const float* rf, float* t1, float* t2, float* df,
-                                          unsigned char* smem, int rank) {
-  if (C.variant == 1)
-    cl_solve<CL, 8, 8>(C, I, np, rf, t1, t2, df, *reinterpret_cast<DualSmem<8, 8>*>(smem), rank);
-  else
-    cl_solve<CL, 4, 4>(C, I, np, rf, t1, t2, df, *reinterpret_cast<DualSmem<4, 4>*>(smem), rank);
+__device__ void cl_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf, float* t1,
+                         float* t2, float* df, UmmaSmem& sm, UmmaState& st, int rank) {
+  const int s = C.s, rows = np * s;
+  dual_umma<true>(rf, C.Qts, t1, s, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
+  csync<CL>();
+  dual_umma<true>(t1, C.Qts, t2, s, rows, C.lam, I.dtnu, true, sm, st, rank, CL);
+  csync<CL>();
+  dual_umma<false>(t2, C.Qs, t1, s, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
+  csync<CL>();
+  dual_umma<false>(t1, C.Qs, df, s, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
+  csync<CL>();
 }
 
 template <int CL>
 __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_constant__ EnsArgs a) {
-  extern __shared__ __align__(16) unsigned char ens_smem[];   // ENS_SMEM_BYTES: GEMM tiles
+  extern __shared__ __align__(16) unsigned char ens_smem[];   // ENS_SMEM_BYTES: GEMM slices
   __shared__ int item;
+  __shared__ __align__(8) uint64_t um_bar;
+  __shared__ uint32_t um_tmem_slot;
   const int rank = (CL > 1) ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+  // tensor-core set-up: the slice buffers on a 1 KB boundary (128B swizzle), the MMA-completion
+  // barrier, and UM_TMEM_COLS columns of tensor memory for the accumulators
+  const uint32_t pad = (1024u - (tc::s_u32(ens_smem) & 1023u)) & 1023u;
+  UmmaSmem& usm = *reinterpret_cast<UmmaSmem*>(ens_smem + pad);
+  if (threadIdx.x == 0) {
+    tc::s_init(tc::s_u32(&um_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) tc::s_tmem_alloc(tc::s_u32(&um_tmem_slot), UM_TMEM_COLS);
+  tc::s_fence_before();
+  __syncthreads();
+  tc::s_fence_after();
+  UmmaState ust{um_tmem_slot, tc::s_u32(&um_bar), 0u, a.err};
   const long cid = blockIdx.x / CL;
   const long wp = a.ws_plane;
   double* r = a.r_ws + cid * EMaxP * wp;
@@ -416,7 +461,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
       // 2./3. FP32 solve (the increment overwrites rf, free after the first GEMM), then
       // refinement passes against the FP64 residual
       const float* df = rf;
-      solve_any<CL>(C, I, na, rf, t1, t2, rf, ens_smem, rank);
+      cl_solve<CL>(C, I, na, rf, t1, t2, rf, usm, ust, rank);
       for (int pass = 1; pass <= a.nref; ++pass) {
         for (long e = g0; e < na * ss; e += gs)
           dt_tot[e] = (pass == 1) ? e_f32_to_f64(df[e]) : dt_tot[e] + e_f32_to_f64(df[e]);
@@ -447,7 +492,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
           }
         }
         csync<CL>();
-        solve_any<CL>(C, I, na, rf, t1, t2, rf, ens_smem, rank);
+        cl_solve<CL>(C, I, na, rf, t1, t2, rf, usm, ust, rank);
       }
       // 4a. new states eta = base + delta (FP64)
       for (int q = 0; q < na; ++q) {
@@ -514,6 +559,14 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
     if (rank == 0 && threadIdx.x == 0)
       for (int j = 0; j < EMaxP; ++j) Ig.p[j] = p[j];
   }
+  // every MMA has been waited for (or a wait gave up and flagged the error): free the tensor
+  // memory
+  tc::s_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::s_fence_after();
+    tc::s_tmem_free(ust.tmem, UM_TMEM_COLS);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -542,6 +595,7 @@ struct BatchCtx {
   unsigned* masks_dev[EMaxP + 1] = {nullptr};
   size_t masks_cap[EMaxP + 1] = {0};
   double *r_ws = nullptr, *d_ws = nullptr;
+  int* err_dev = nullptr;              // device-side error flag (bounded waits that gave up)
   float* f_ws = nullptr;
   long ws_plane = 0;
   int cl = 1;                          // autotuned cluster size (CTAs per instance)
@@ -600,6 +654,7 @@ static int batch_run(BatchCtx* b, long nsteps, int cl, int per_sm, const int* or
   a.wq = b->wq_dev;
   a.r_ws = b->r_ws;
   a.d_ws = b->d_ws;
+  a.err = b->err_dev;
   a.f_ws = b->f_ws;
   a.ws_plane = b->ws_plane;
   a.nref = b->nref;
@@ -749,7 +804,6 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     }
     EnsClass C{};
     C.s = s;
-    C.variant = s >= 128 ? 1 : 0;   // until the autotuner decides
     void* p;
     if ((rc = b_alloc(b, &p, Qs.size() * 4)) != RIDC_OK) return fail(rc);
     cudaMemcpy(p, Qs.data(), Qs.size() * 4, cudaMemcpyHostToDevice);
@@ -837,6 +891,9 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   b->d_ws = (double*)p;
   if ((rc = b_alloc(b, &p, (size_t)ctas * 3 * EMaxP * b->ws_plane * sizeof(float))) != RIDC_OK) return fail(rc);
   b->f_ws = (float*)p;
+  if ((rc = b_alloc(b, &p, sizeof(int))) != RIDC_OK) return fail(rc);
+  b->err_dev = (int*)p;
+  cudaMemset(p, 0, sizeof(int));
   b->cl = 4;
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_status(e));
@@ -937,6 +994,13 @@ extern "C" int ridc_batch_get_solution(ridc_batch h, int i, double* out, size_t 
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_status(e);
+  int err = 0;
+  e = cudaMemcpy(&err, b->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (err) {   // reported once: the flag is cleared for the calls that follow
+    cudaMemset(b->err_dev, 0, sizeof(int));
+    return RIDC_ERR_TIMEOUT;
+  }
   if (!out_on_device)
     for (size_t k = 0; k < count; ++k)
       if (!std::isfinite(out[k])) return RIDC_ERR_NONFINITE;
@@ -948,11 +1012,10 @@ extern "C" long ridc_batch_cells(ridc_batch h) {
   return b ? b->cells_per_step : -1;
 }
 
-// Autotuner. First, per grid side, the GEMM tile (64 x 32 or 128 x 64) that integrates the
-// instances of that side fastest on their own (one-CTA clusters); then the cluster size (1, 2
-// or 4 CTAs per instance) and the CTAs per SM (1 or 2) that run the whole batch fastest with
-// those tiles. Each trial advances `nsteps` top-level steps from the current state. The
-// choice is kept for later advances; *choice = CTAs per SM * 16 + cluster size.
+// Autotuner: the cluster size (1, 2 or 4 CTAs per instance) and the CTAs per SM (1 or 2) that
+// run the whole batch fastest (the tensor-core tile follows from each grid side). Each trial
+// advances `nsteps` top-level steps from the current state. The choice is kept for later
+// advances; *choice = CTAs per SM * 16 + cluster size.
 // The state is scrambled: call ridc_batch_set_initial afterwards.
 extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float* best_ms) {
   BatchCtx* b = bctx(h);
@@ -982,29 +1045,6 @@ extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float
     return RIDC_OK;
   };
   int rc = RIDC_OK;
-  int mask = 0;
-  for (size_t c = 0; c < b->cls.size() && rc == RIDC_OK; ++c) {
-    std::vector<int> sub;
-    for (int i = 0; i < b->n; ++i)
-      if (b->inst[i].cls == (int)c) sub.push_back(i);
-    if (sub.empty()) continue;
-    cudaMemcpyAsync(b->sub_dev, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice,
-                    b->stream);
-    float best = 1e30f;
-    int bv = b->cls[c].variant;
-    for (int v = 0; v < 2 && rc == RIDC_OK; ++v) {
-      b->cls[c].variant = v;
-      cudaMemcpyAsync(b->cls_dev, b->cls.data(), b->cls.size() * sizeof(EnsClass),
-                      cudaMemcpyHostToDevice, b->stream);
-      float ms = 0.f;
-      rc = timed(1, 1, b->sub_dev, (int)sub.size(), &ms);
-      if (ms < best) { best = ms; bv = v; }
-    }
-    b->cls[c].variant = bv;
-    if (bv) mask |= 1 << c;
-  }
-  cudaMemcpyAsync(b->cls_dev, b->cls.data(), b->cls.size() * sizeof(EnsClass),
-                  cudaMemcpyHostToDevice, b->stream);
   float best = 1e30f;
   int bcl = b->cl, bps = b->per_sm;
   for (int per_sm = 1; per_sm <= 2 && rc == RIDC_OK; ++per_sm)
@@ -1021,7 +1061,6 @@ extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float
   b->cl = bcl;
   b->per_sm = bps;
   b->initialised = false;
-  (void)mask;
   if (choice) *choice = bps * 16 + bcl;
   if (best_ms) *best_ms = best;
   return RIDC_OK;

@@ -35,10 +35,13 @@
 #include <cudaTypedefs.h>
 
 #include "ridc_internal.h"
+#include "tc_util.cuh"
 
 namespace ridc {
 
 namespace {
+
+using namespace tc;
 
 constexpr int SY_BM = 128, SY_BK = 64;
 constexpr int SY_TILE = SY_BM * SY_BK * 2;   // 16 KB: 128 rows x 64 BF16 (A tiles)
@@ -67,47 +70,6 @@ constexpr int sy_smem_base() { return SyCfg<FWD, BN>::STAGES * SyCfg<FWD, BN>::S
 constexpr int SY_SMEM_MAX = 2 * (2 * SY_TILE + 2 * 256 * SY_BK * 2) + 2048 + SY_MAXN * 4;
 constexpr int SY_THREADS = 192;
 constexpr uint32_t SY_ACC_COLS = 256;        // per TMEM buffer: E (128) + O (128)
-constexpr unsigned long long SY_WAIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t s_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long s_gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool s_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool s_wait(uint32_t bar, uint32_t parity, int* err) {
-  unsigned long long t0 = 0;
-  for (uint32_t it = 0;; ++it) {
-    if (s_try(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
-      const unsigned long long t = s_gtimer();
-      if (t0 == 0) t0 = t;
-      else if (t - t0 > SY_WAIT_NS) {
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void s_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
 
 __device__ __forceinline__ void s_expect(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
@@ -123,43 +85,12 @@ __device__ __forceinline__ void s_tma(uint32_t dst, const CUtensorMap* tm, uint3
       : "memory");
 }
 
-// K-major operand tile of 128 rows x 64 BF16 (128 B rows), 128B swizzle, 8-row groups 1 KB apart
-__device__ __forceinline__ uint64_t s_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(16u >> 4) << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N from the instruction descriptor
 __device__ __forceinline__ void s_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                       uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void s_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void s_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-      " [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void s_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // v = hi + lo to about 16 (BF16) or 22 (FP16) significant bits; v - hi is exact in FP32
