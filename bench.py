@@ -130,8 +130,8 @@ class ClockSampler:
 # DRAM traffic of one full (8-plane) gemm_sym launch from one ncu capture
 # (profiles/gemm_sym_gray_scott_2048_mixed.md: dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the four modes), valid only for the kernel source it was taken on.
-GEMM_TRAFFIC = {"bytes": 2.320e8,
-                "source_sha256": "cc09b2e7b63fe3d683bbdd5b1caf128b58c202f37f04f65109dfeef5b1493a16"}
+GEMM_TRAFFIC = {"bytes": 2.319e8,
+                "source_sha256": "e1b7af6e50ca55e1a1f441125b63638a65ecfede4af675122ed6692b059a9632"}
 
 
 def gemm_traffic():
