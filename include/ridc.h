@@ -266,7 +266,7 @@ int ridc_batch_get_solution(ridc_batch b, int i, double* out, size_t count, int 
 long ridc_batch_cells(ridc_batch b);
 
 /* Autotuner: picks the cluster size (1, 2 or 4 CTAs cooperating on each instance) and the
- * CTAs per SM (1 or 2) that run the whole batch fastest (the tensor-core tile, 128 rows by the
+ * CTAs per SM (1 to 4) that run the whole batch fastest (the tensor-core tile, 128 rows by the
  * widest multiple of 16 up to 64 that divides side/2, follows from each grid side); each trial
  * advances `nsteps` steps of the real batch. The choice is kept for later advances. Requires
  * an initial state and leaves the state undefined: call ridc_batch_set_initial afterwards.
@@ -274,7 +274,7 @@ long ridc_batch_cells(ridc_batch b);
 int ridc_batch_autotune(ridc_batch b, long nsteps, int* choice, float* best_ms);
 
 /* Use launch shape `choice` (CTAs per SM * 16 + cluster size, as ridc_batch_autotune reports
- * it: 1 or 2 CTAs per SM, clusters of 1, 2 or 4 CTAs) for later advances, e.g. one tuned
+ * it: 1 to 4 CTAs per SM, clusters of 1, 2 or 4 CTAs) for later advances, e.g. one tuned
  * earlier on the same batch. RIDC_ERR_ARG for another value.                                */
 int ridc_batch_set_launch(ridc_batch b, int choice);
 

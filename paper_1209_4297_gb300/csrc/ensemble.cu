@@ -125,19 +125,20 @@ struct EnsArgs {
 // accumulation in tensor memory: the accuracy of the FP32 solves it replaces. A tile is 128
 // rows (M) by BN half-columns (N, a multiple of 16 up to 64 that divides H) per parity half,
 // both halves accumulated side by side in 2 BN TMEM columns. K advances in slices of 32 values
-// (128-byte rows, 128B swizzle): all 256 threads load a slice from global memory (float4),
-// butterfly, split and write it to shared memory, one thread issues its 24 MMAs (2 halves x 3
-// products x 4 steps of K = 8) and commits them to an mbarrier, and every thread waits on that
-// barrier (bounded) before the slice buffer is reused. The epilogue reads the accumulators
+// (128-byte rows, 128B swizzle), one parity half at a time through one set of buffers (48 KB,
+// so four CTAs fit per SM): all 256 threads load the half-slice from global memory (float4),
+// butterfly, split and write it to shared memory, one thread issues its 12 MMAs (3 products x
+// 4 steps of K = 8) and commits them to an mbarrier, and every thread waits on that barrier
+// (bounded) before the buffers are reused. The epilogue reads the accumulators
 // with tcgen05.ld: warp w covers TMEM lanes (= tile rows) 32 (w % 4).. and every other group
 // of 16 columns. Tiles are dealt round-robin to the CL CTAs of the cluster.
 constexpr int UM_BM = 128, UM_BK = 32, UM_MAXBN = 64;
 constexpr int UM_TILE_A = UM_BM * UM_BK * 4;       // 16 KB: 128 rows x 32 FP32
 constexpr int UM_TILE_B = UM_MAXBN * UM_BK * 4;    // 8 KB
 constexpr uint32_t UM_TMEM_COLS = 2 * UM_MAXBN;    // two halves of BN <= 64 FP32 columns
-struct UmmaSmem {                                  // 1 KB aligned
-  unsigned char a[2][2][UM_TILE_A];                // [half][hi, lo]
-  unsigned char b[2][2][UM_TILE_B];                // [half][hi, lo]
+struct UmmaSmem {                                  // 1 KB aligned; one parity half at a time
+  unsigned char a[2][UM_TILE_A];                   // [hi, lo]
+  unsigned char b[2][UM_TILE_B];                   // [hi, lo]
 };
 constexpr size_t ENS_SMEM_BYTES = sizeof(UmmaSmem) + 1024;   // + alignment slack
 
@@ -208,56 +209,50 @@ __device__ void dual_umma(const float* __restrict__ A, const float* __restrict__
     const int row0 = (tile / nct) * UM_BM, col0 = (tile % nct) * BN;
     for (int kb = 0; kb < KS; ++kb) {
       const int k0 = kb * UM_BK;
-      // the previous MMAs still read the slice buffers; the decision to give up is made by
-      // the whole CTA together, so every thread leaves at the same point
-      const bool ok = st.commits == 0 || um_wait(st);
-      if (__syncthreads_or(!ok)) return;
-      // A: 128 rows x 8 chunks of 4 K values per half; 4 chunks per thread
+      for (int h = 0; h < 2; ++h) {   // the parity halves in turn through one set of buffers
+        // the previous MMAs still read the slice buffers; the decision to give up is made by
+        // the whole CTA together, so every thread leaves at the same point
+        const bool ok = st.commits == 0 || um_wait(st);
+        if (__syncthreads_or(!ok)) return;
+        // A: 128 rows x 8 chunks of 4 K values; 4 chunks per thread
 #pragma unroll
-      for (int v = 0; v < UM_BM * 8 / ENS_THREADS; ++v) {
-        const int e = t + v * ENS_THREADS, r = e >> 3, c = e & 7, gr = row0 + r;
-        const int k = k0 + c * 4;
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-        if (gr < rows && k < H) {
-          const float* ar = A + (long)gr * s;
-          if (FWD) {
-            // x' = k..k+3 and their mirrors s-1-x' (a reversed float4)
-            const float4 x = *reinterpret_cast<const float4*>(ar + k);
-            const float4 m4 = *reinterpret_cast<const float4*>(ar + s - 4 - k);
-            const float4 m = make_float4(m4.w, m4.z, m4.y, m4.x);
-            a0 = f4_add(x, m, 1.f);
-            a1 = f4_add(x, m, -1.f);
-          } else {
-            a0 = *reinterpret_cast<const float4*>(ar + k);
-            a1 = *reinterpret_cast<const float4*>(ar + H + k);
+        for (int v = 0; v < UM_BM * 8 / ENS_THREADS; ++v) {
+          const int e = t + v * ENS_THREADS, r = e >> 3, c = e & 7, gr = row0 + r;
+          const int k = k0 + c * 4;
+          float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (gr < rows && k < H) {
+            const float* ar = A + (long)gr * s;
+            if (FWD) {
+              // x' = k..k+3 and their mirrors s-1-x' (a reversed float4)
+              const float4 x = *reinterpret_cast<const float4*>(ar + k);
+              const float4 m4 = *reinterpret_cast<const float4*>(ar + s - 4 - k);
+              const float4 m = make_float4(m4.w, m4.z, m4.y, m4.x);
+              av = f4_add(x, m, h ? -1.f : 1.f);
+            } else {
+              av = *reinterpret_cast<const float4*>(ar + h * H + k);
+            }
           }
+          um_put(sm.a[0], sm.a[1], r, c, av);
         }
-        um_put(sm.a[0][0], sm.a[0][1], r, c, a0);
-        um_put(sm.a[1][0], sm.a[1][1], r, c, a1);
-      }
-      // B: BN rows x 8 chunks per half
-      for (int e = t; e < BN * 8; e += ENS_THREADS) {
-        const int r = e >> 3, c = e & 7, gc = col0 + r;
-        const int k = k0 + c * 4;
-        float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
-        if (k < H) {
-          // forward: rows k' and H + k' of Qts; inverse: row x' of Qs, columns k' and H + k'
-          b0 = *reinterpret_cast<const float4*>(B + (long)gc * s + k);
-          b1 = FWD ? *reinterpret_cast<const float4*>(B + (long)(H + gc) * s + k)
-                   : *reinterpret_cast<const float4*>(B + (long)gc * s + H + k);
+        // B: BN rows x 8 chunks
+        for (int e = t; e < BN * 8; e += ENS_THREADS) {
+          const int r = e >> 3, c = e & 7, gc = col0 + r;
+          const int k = k0 + c * 4;
+          float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (k < H) {
+            // forward: rows k' and H + k' of Qts; inverse: row x' of Qs, columns k' and H + k'
+            bv = FWD ? *reinterpret_cast<const float4*>(B + (long)(h * H + gc) * s + k)
+                     : *reinterpret_cast<const float4*>(B + (long)gc * s + h * H + k);
+          }
+          um_put(sm.b[0], sm.b[1], r, c, bv);
         }
-        um_put(sm.b[0][0], sm.b[0][1], r, c, b0);
-        um_put(sm.b[1][0], sm.b[1][1], r, c, b1);
-      }
-      tc::s_fence_async_smem();
-      __syncthreads();
-      if (t == 0) {
-        tc::s_fence_after();
-        const int kst = min(4, (H - k0) / 8);   // H is a multiple of 16: 2 or 4 steps
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint64_t ah = tc::s_desc(tc::s_u32(sm.a[h][0])), al = tc::s_desc(tc::s_u32(sm.a[h][1]));
-          const uint64_t bh = tc::s_desc(tc::s_u32(sm.b[h][0])), bl = tc::s_desc(tc::s_u32(sm.b[h][1]));
+        tc::s_fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+          tc::s_fence_after();
+          const int kst = min(4, (H - k0) / 8);   // H is a multiple of 16: 2 or 4 steps
+          const uint64_t ah = tc::s_desc(tc::s_u32(sm.a[0])), al = tc::s_desc(tc::s_u32(sm.a[1]));
+          const uint64_t bh = tc::s_desc(tc::s_u32(sm.b[0])), bl = tc::s_desc(tc::s_u32(sm.b[1]));
           const uint32_t acc = st.tmem + (uint32_t)(h * BN);
           for (int ks = 0; ks < kst; ++ks) {
             const uint64_t adv = (uint64_t)(ks * 32 >> 4);   // 8 FP32 = 32 bytes along K
@@ -265,10 +260,10 @@ __device__ void dual_umma(const float* __restrict__ A, const float* __restrict__
             tc::s_mma_tf32(acc, ah + adv, bl + adv, idesc, 1);
             tc::s_mma_tf32(acc, al + adv, bh + adv, idesc, 1);
           }
+          tc::s_commit(st.bar);
         }
-        tc::s_commit(st.bar);
+        ++st.commits;
       }
-      ++st.commits;
     }
     if (__syncthreads_or(!um_wait(st))) return;
     tc::s_fence_after();
@@ -289,9 +284,9 @@ __device__ void dual_umma(const float* __restrict__ A, const float* __restrict__
         const int c = col0 + ch * 16 + j;   // k' (forward) or x' (inverse), < H
         float x0 = __uint_as_float(v0[j]), x1 = __uint_as_float(v1[j]);
         if (FWD) {
-          if (scale) {
-            x0 = __fdividef(x0, 1.0f - dtnu * (lam[rl] + lam[c]));
-            x1 = __fdividef(x1, 1.0f - dtnu * (lam[rl] + lam[H + c]));
+          if (scale) {   // den = 1 - dtnu (lam_y + lam_x) as one explicit fma
+            x0 = __fdividef(x0, __fmaf_rn(-dtnu, lam[rl] + lam[c], 1.0f));
+            x1 = __fdividef(x1, __fmaf_rn(-dtnu, lam[rl] + lam[H + c], 1.0f));
           }
           op[(long)c * s + rl] = x0;
           op[(long)(H + c) * s + rl] = x1;
@@ -367,8 +362,10 @@ __device__ void cl_solve(const EnsClass& C, const EnsInst& I, int np, const floa
   csync<CL>();
 }
 
+// 80 registers: three CTAs (24 warps) fit per SM, which the FP64 phases need to hide their
+// load latency; shared memory (49 KB) and tensor memory (128 columns) would allow four
 template <int CL>
-__global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_constant__ EnsArgs a) {
+__global__ void __launch_bounds__(ENS_THREADS, 3) ensemble_kernel(const __grid_constant__ EnsArgs a) {
   extern __shared__ __align__(16) unsigned char ens_smem[];   // ENS_SMEM_BYTES: GEMM slices
   __shared__ int item;
   __shared__ __align__(8) uint64_t um_bar;
@@ -547,7 +544,9 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ensemble_kernel(const __grid_c
           for (int u = 0; u < 2; ++u) {
             if (u == 1 && !two) break;
             const long ii = u ? i1 : i;
-            const double fn = -I.a2h * (xe[u] - xw[u]) - I.b2h * (yn[u] - ys[u]);
+            // explicit roundings: every instantiation (cluster size) computes the same bits
+            const double fn = __dsub_rn(__dmul_rn(-I.a2h, xe[u] - xw[u]),
+                                        __dmul_rn(I.b2h, yn[u] - ys[u]));
             fN[ii] = fn;
             if (F) F[ii] = fma(I.c_lap, (xe[u] + xw[u]) + (yn[u] + ys[u]), fma(I.c_lap4, ec[u], fn));
           }
@@ -636,7 +635,7 @@ static int launch_cl(cudaStream_t stream, const EnsArgs& a, int grid) {
   return cuda_status(cudaLaunchKernelEx(&cfg, ensemble_kernel<CL>, a));
 }
 
-// grid for cluster size cl and `per_sm` CTAs per SM (workspace holds 2 * sms clusters)
+// grid for cluster size cl and `per_sm` CTAs per SM (workspace holds 4 * sms clusters)
 static int grid_for(const BatchCtx* b, int cl, int per_sm, int count) {
   const int clusters = std::max(1, std::min(count, per_sm * b->sms / cl));
   return clusters * cl;
@@ -882,9 +881,9 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
   if ((rc = b_alloc(b, &p, wq.size() * sizeof(double))) != RIDC_OK) return fail(rc);
   b->wq_dev = (double*)p;
   cudaMemcpy(p, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice);
-  // per-cluster workspace, enough for one-CTA clusters, two per SM
+  // per-cluster workspace, enough for one-CTA clusters, four per SM
   b->ws_plane = (long)smax * smax;
-  const long ctas = 2L * b->sms;
+  const long ctas = 4L * b->sms;
   if ((rc = b_alloc(b, &p, (size_t)ctas * EMaxP * b->ws_plane * sizeof(double))) != RIDC_OK) return fail(rc);
   b->r_ws = (double*)p;
   if ((rc = b_alloc(b, &p, (size_t)ctas * EMaxP * b->ws_plane * sizeof(double))) != RIDC_OK) return fail(rc);
@@ -935,7 +934,7 @@ __global__ void ens_init_kernel(EnsInst* inst, int ninst) {
     const double* u = I.eta[0];
     const double xe = odd_at(u, s, gy, gx + 1), xw = odd_at(u, s, gy, gx - 1);
     const double yn = odd_at(u, s, gy + 1, gx), ys = odd_at(u, s, gy - 1, gx);
-    const double fn = -I.a2h * (xe - xw) - I.b2h * (yn - ys);
+    const double fn = __dsub_rn(__dmul_rn(-I.a2h, xe - xw), __dmul_rn(I.b2h, yn - ys));
     const double F = fma(I.c_lap, (xe + xw) + (yn + ys), fma(I.c_lap4, u[e], fn));
     for (int j = 0; j < I.P; ++j) {
       if (j > 0) I.eta[j][e] = u[e];
@@ -1012,7 +1011,7 @@ extern "C" long ridc_batch_cells(ridc_batch h) {
   return b ? b->cells_per_step : -1;
 }
 
-// Autotuner: the cluster size (1, 2 or 4 CTAs per instance) and the CTAs per SM (1 or 2) that
+// Autotuner: the cluster size (1, 2 or 4 CTAs per instance) and the CTAs per SM (1 to 4) that
 // run the whole batch fastest (the tensor-core tile follows from each grid side). Each trial
 // advances `nsteps` top-level steps from the current state. The choice is kept for later
 // advances; *choice = CTAs per SM * 16 + cluster size.
@@ -1047,7 +1046,7 @@ extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float
   int rc = RIDC_OK;
   float best = 1e30f;
   int bcl = b->cl, bps = b->per_sm;
-  for (int per_sm = 1; per_sm <= 2 && rc == RIDC_OK; ++per_sm)
+  for (int per_sm = 1; per_sm <= 4 && rc == RIDC_OK; ++per_sm)
     for (int cl = 1; cl <= 4 && rc == RIDC_OK; cl *= 2) {
       float ms = 0.f;
       rc = timed(cl, per_sm, b->order_dev, b->n, &ms);
@@ -1070,7 +1069,7 @@ extern "C" int ridc_batch_set_launch(ridc_batch h, int choice) {
   BatchCtx* b = bctx(h);
   if (!b) return RIDC_ERR_ARG;
   const int per_sm = choice / 16, cl = choice % 16;
-  if ((per_sm != 1 && per_sm != 2) || (cl != 1 && cl != 2 && cl != 4)) return RIDC_ERR_ARG;
+  if (per_sm < 1 || per_sm > 4 || (cl != 1 && cl != 2 && cl != 4)) return RIDC_ERR_ARG;
   b->per_sm = per_sm;
   b->cl = cl;
   return RIDC_OK;

@@ -109,7 +109,7 @@ def test_launch_shape_can_be_set_and_does_not_change_results():
     ws = inputs.ensemble(12, nsteps=6)
     ref = _run_batch(ws, 6, 1)
     need_cuda()
-    for choice in (1 * 16 + 1, 2 * 16 + 2, 1 * 16 + 4):
+    for choice in (1 * 16 + 1, 2 * 16 + 2, 1 * 16 + 4, 3 * 16 + 1, 4 * 16 + 4):
         with Batch(ws, n_refine=1) as b:
             b.set_launch(choice)
             b.set_initial([w.u0[0] for w in ws])
@@ -117,7 +117,7 @@ def test_launch_shape_can_be_set_and_does_not_change_results():
             for i in (0, 5, 11):
                 np.testing.assert_array_equal(b.solution(i), ref[i])
     with Batch(ws) as b:
-        for bad in (0, 16 + 3, 3 * 16 + 1):
+        for bad in (0, 16 + 3, 5 * 16 + 1):
             with pytest.raises(RidcError):
                 b.set_launch(bad)
 
