@@ -171,6 +171,52 @@ __device__ void tri_solve_block(double* r, int n, int npad, const double* rp, do
   __syncthreads();
 }
 
+// Corrector right-hand side of one level over this CTA's cells, with the K quadrature nodes
+// of the level below: every thread issues the loads of U of its cells (4 + K ring values each,
+// read past L1 because other SMs wrote them) before any arithmetic, so their L2 round trips
+// overlap instead of following one another; the arithmetic per cell is that of eq. (corr) in
+// delta form, in a fixed order.
+template <int K>
+__device__ __forceinline__ void rhs_corrector_1d(int n, double dt, const double* ej,
+                                                 const double* fj, const double* ep,
+                                                 const double* fp, const double* Fring, long b,
+                                                 int cap, const double* wq, double* r, double* e) {
+  constexpr int U = 2;
+  const double* F[K];
+  double w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    F[k] = Fring + ((b + k) % cap) * n;
+    w[k] = dt * wq[k];
+  }
+  for (int i0 = threadIdx.x; i0 < n; i0 += U * blockDim.x) {
+    double vb[U], vfj[U], vfp[U], vej[U], vF[K][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n) {
+        vb[u] = __ldcg(ep + i);
+        vfj[u] = __ldcg(fj + i);
+        vfp[u] = __ldcg(fp + i);
+        vej[u] = __ldcg(ej + i);
+#pragma unroll
+        for (int k = 0; k < K; ++k) vF[k][u] = __ldcg(F[k] + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n) {
+        double acc = fma(dt, vfj[u] - vfp[u], vej[u] - vb[u]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc = fma(w[k], vF[k][u], acc);
+        r[i] = acc;
+        e[i] = vb[u];
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -275,9 +321,30 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
       } else if (j == 0) {
         const double* F0 = a.F[0] + (nj % a.cap[0]) * n;
         const double* e0 = a.eta[0] + (nj % a.cap[0]) * n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          r[i] = a.dt * __ldcg(F0 + i);
-          e[i] = __ldcg(e0 + i);
+        // when a thread has several cells, the loads of up to four are issued together
+        if (n <= 2 * (int)blockDim.x) {
+          for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            r[i] = a.dt * __ldcg(F0 + i);
+            e[i] = __ldcg(e0 + i);
+          }
+        } else for (int i0 = threadIdx.x; i0 < n; i0 += 4 * blockDim.x) {
+          double vF[4], ve[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n) {
+              vF[u] = __ldcg(F0 + i);
+              ve[u] = __ldcg(e0 + i);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n) {
+              r[i] = a.dt * vF[u];
+              e[i] = ve[u];
+            }
+          }
         }
       } else {
         const double* ej = a.eta[j] + (nj % a.cap[j]) * n;
@@ -289,13 +356,22 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
         const long b = nj + 2 - K > 0 ? nj + 2 - K : 0;
         const int m = (int)(nj - b);
         const double* w = a.wq + ((size_t)(K - 1) * a.W + m) * a.W;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          const double base = __ldcg(ep + i);
-          double acc = fma(a.dt, __ldcg(fj + i) - __ldcg(fp + i), __ldcg(ej + i) - base);
-          for (int k = 0; k < K; ++k)
-            acc = fma(a.dt * w[k], __ldcg(a.F[j - 1] + ((b + k) % a.cap[j - 1]) * n + i), acc);
-          r[i] = acc;
-          e[i] = base;
+        const double* Fr = a.F[j - 1];
+        const int cp = a.cap[j - 1];
+        switch (K) {
+          case 2: rhs_corrector_1d<2>(n, a.dt, ej, fj, ep, fp, Fr, b, cp, w, r, e); break;
+          case 3: rhs_corrector_1d<3>(n, a.dt, ej, fj, ep, fp, Fr, b, cp, w, r, e); break;
+          case 4: rhs_corrector_1d<4>(n, a.dt, ej, fj, ep, fp, Fr, b, cp, w, r, e); break;
+          case 5: rhs_corrector_1d<5>(n, a.dt, ej, fj, ep, fp, Fr, b, cp, w, r, e); break;
+          default:   // wider stencils (orders above 6): one cell at a time
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+              const double base = __ldcg(ep + i);
+              double acc = fma(a.dt, __ldcg(fj + i) - __ldcg(fp + i), __ldcg(ej + i) - base);
+              for (int k = 0; k < K; ++k)
+                acc = fma(a.dt * w[k], __ldcg(Fr + ((b + k) % cp) * n + i), acc);
+              r[i] = acc;
+              e[i] = base;
+            }
         }
       }
     }

@@ -38,6 +38,21 @@ int main(void) {
         CHECK(f == first[j], "start-up wait j(j+1)/2");
     }
 
+    /* the same schedule with the ARK4 predictor: corrector j reads a 4 + j node stencil, so
+       level j first advances in step 3j + j(j+1)/2 (0-based) */
+    unsigned ark[32];
+    CHECK(ridc_schedule_plan_predictor(4, RIDC_PRED_ARK4, NULL, 10, ark, 32, &count) == RIDC_OK,
+          "plan with the ARK4 predictor");
+    const int first_ark[4] = {0, 4, 9, 15};
+    for (int j = 0; j < 4; ++j) {
+        int f = -1;
+        for (size_t s = 0; s < count && f < 0; ++s)
+            if (ark[s] & (1u << j)) f = (int)s;
+        CHECK(f == first_ark[j], "ARK4 start-up wait 3j + j(j+1)/2");
+    }
+    CHECK(ridc_schedule_plan_predictor(10, RIDC_PRED_ARK4, NULL, 5, ark, 32, &count) ==
+              RIDC_ERR_ARG, "ARK4 stencil wider than 12 nodes refused");
+
     /* error strings and argument checks */
     CHECK(strlen(ridc_error_string(RIDC_ERR_TIMEOUT)) > 0, "error_string");
     CHECK(ridc_set_allocator(NULL, NULL, NULL) == RIDC_OK, "default allocator");
