@@ -126,10 +126,11 @@ struct EnsArgs {
 // rows (M) by BN half-columns (N, a multiple of 16 up to 64 that divides H) per parity half,
 // both halves accumulated side by side in 2 BN TMEM columns. K advances in slices of 32 values
 // (128-byte rows, 128B swizzle), one parity half at a time through one set of buffers (48 KB,
-// so four CTAs fit per SM): all 256 threads load the half-slice from global memory (float4),
-// butterfly, split and write it to shared memory, one thread issues its 12 MMAs (3 products x
-// 4 steps of K = 8) and commits them to an mbarrier, and every thread waits on that barrier
-// (bounded) before the buffers are reused. The epilogue reads the accumulators
+// so four CTAs fit per SM): all 256 threads load the half-slice's A operand from global memory
+// (float4) into registers, then wait (bounded) on the mbarrier of the previous MMAs, which
+// still read the buffers, so that the loads and the MMAs overlap; then they butterfly, split
+// and write A and B to shared memory, and one thread issues the 12 MMAs (3 products x 4 steps
+// of K = 8) and commits them to the mbarrier. The epilogue reads the accumulators
 // with tcgen05.ld: warp w covers TMEM lanes (= tile rows) 32 (w % 4).. and every other group
 // of 16 columns. Tiles are dealt round-robin to the CL CTAs of the cluster.
 constexpr int UM_BM = 128, UM_BK = 32, UM_MAXBN = 64;
@@ -187,9 +188,7 @@ __device__ __forceinline__ float4 f4_add(float4 a, float4 b, float sg) {
 }
 
 // bounded wait for the latest commit; false (and the error flagged) if it never completes
-// or an earlier wait already gave up
 __device__ __forceinline__ bool um_wait(UmmaState& st) {
-  if (*(volatile int*)st.err) return false;
   return tc::s_wait(st.bar, (st.commits - 1) & 1u, st.err);
 }
 
@@ -205,21 +204,23 @@ __device__ void dual_umma(const float* __restrict__ A, const float* __restrict__
   // 7-9 and 10-12 = 2), both K-major, N / 8 (bits 17-22), M / 16 (bits 24-28)
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(UM_BM >> 4) << 24);
+  // an earlier wait of this launch gave up: leave at once (decided CTA-wide)
+  if (__syncthreads_or(*(volatile int*)st.err != 0)) return;
   for (int tile = rank; tile < nrt * nct; tile += CL) {
     const int row0 = (tile / nct) * UM_BM, col0 = (tile % nct) * BN;
     for (int kb = 0; kb < KS; ++kb) {
       const int k0 = kb * UM_BK;
       for (int h = 0; h < 2; ++h) {   // the parity halves in turn through one set of buffers
-        // the previous MMAs still read the slice buffers; the decision to give up is made by
-        // the whole CTA together, so every thread leaves at the same point
-        const bool ok = st.commits == 0 || um_wait(st);
-        if (__syncthreads_or(!ok)) return;
+        // the half-slice's A operand into registers first, so that its loads overlap the
+        // previous MMAs, which still read the slice buffers.
         // A: 128 rows x 8 chunks of 4 K values; 4 chunks per thread
+        constexpr int NA = UM_BM * 8 / ENS_THREADS;
+        float4 av[NA];
 #pragma unroll
-        for (int v = 0; v < UM_BM * 8 / ENS_THREADS; ++v) {
+        for (int v = 0; v < NA; ++v) {
           const int e = t + v * ENS_THREADS, r = e >> 3, c = e & 7, gr = row0 + r;
           const int k = k0 + c * 4;
-          float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
+          av[v] = make_float4(0.f, 0.f, 0.f, 0.f);
           if (gr < rows && k < H) {
             const float* ar = A + (long)gr * s;
             if (FWD) {
@@ -227,14 +228,22 @@ __device__ void dual_umma(const float* __restrict__ A, const float* __restrict__
               const float4 x = *reinterpret_cast<const float4*>(ar + k);
               const float4 m4 = *reinterpret_cast<const float4*>(ar + s - 4 - k);
               const float4 m = make_float4(m4.w, m4.z, m4.y, m4.x);
-              av = f4_add(x, m, h ? -1.f : 1.f);
+              av[v] = f4_add(x, m, h ? -1.f : 1.f);
             } else {
-              av = *reinterpret_cast<const float4*>(ar + h * H + k);
+              av[v] = *reinterpret_cast<const float4*>(ar + h * H + k);
             }
           }
-          um_put(sm.a[0], sm.a[1], r, c, av);
         }
-        // B: BN rows x 8 chunks
+        // the decision to give up is made by the whole CTA together, so every thread leaves
+        // at the same point
+        const bool ok = st.commits == 0 || um_wait(st);
+        if (__syncthreads_or(!ok)) return;
+#pragma unroll
+        for (int v = 0; v < NA; ++v) {
+          const int e = t + v * ENS_THREADS;
+          um_put(sm.a[0], sm.a[1], e >> 3, e & 7, av[v]);
+        }
+        // B (tables that stay in L2): BN rows x 8 chunks
         for (int e = t; e < BN * 8; e += ENS_THREADS) {
           const int r = e >> 3, c = e & 7, gc = col0 + r;
           const int k = k0 + c * 4;
@@ -362,10 +371,12 @@ __device__ void cl_solve(const EnsClass& C, const EnsInst& I, int np, const floa
   csync<CL>();
 }
 
-// 80 registers: three CTAs (24 warps) fit per SM, which the FP64 phases need to hide their
-// load latency; shared memory (49 KB) and tensor memory (128 columns) would allow four
+// 64 registers: four CTAs (32 warps) fit per SM, as shared memory (49 KB) and tensor memory
+// (128 columns) allow. The FP64 phases need the warps to hide their load latency, and while
+// one CTA waits in a GEMM round the others keep the FP64 pipe busy (measured: 0.98 s against
+// 1.08 s with 80 registers and three CTAs, despite some spilling in the cluster versions)
 template <int CL>
-__global__ void __launch_bounds__(ENS_THREADS, 3) ensemble_kernel(const __grid_constant__ EnsArgs a) {
+__global__ void __launch_bounds__(ENS_THREADS, 4) ensemble_kernel(const __grid_constant__ EnsArgs a) {
   extern __shared__ __align__(16) unsigned char ens_smem[];   // ENS_SMEM_BYTES: GEMM slices
   __shared__ int item;
   __shared__ __align__(8) uint64_t um_bar;
