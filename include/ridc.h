@@ -69,9 +69,10 @@ typedef enum {
        plus n_refine refinement passes against the FP64 residual; right-hand sides,
        quadrature sums and solution accumulation stay FP64                                   */
     RIDC_MIXED_BF16X3 = 1,
-    /* batched ensembles only: solves in FP32 on the CUDA cores, right-hand sides, quadrature
-       sums and solution accumulation in FP64, plus n_refine refinement passes against the
-       FP64 residual                                                                         */
+    /* batched ensembles only: solves at FP32 accuracy on the tensor cores (FP32 operands
+       split into TF32 hi + lo, three products, FP32 accumulation), right-hand sides,
+       quadrature sums and solution accumulation in FP64, plus n_refine refinement passes
+       against the FP64 residual                                                             */
     RIDC_FP32_SOLVE = 2,
     /* as RIDC_MIXED_BF16X3 with FP16 hi/lo operands: 22 significant bits per split instead
        of 16. A pass of either form is also limited by the tensor cores' FP32 accumulation,

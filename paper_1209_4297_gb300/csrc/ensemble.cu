@@ -10,10 +10,10 @@
 // visible to the others); different clusters never wait on one another. Per pipeline step of
 // an instance, for every advancing level (Section III, eq. (pred) / eq. (corr)):
 //   1. right-hand side in delta form, FP64 (defect + Lagrange quadrature, Section III-C);
-//   2. (I - dt nu L) delta = r by fast diagonalisation in FP32: four transforms with the sine
-//      eigenvectors of the cell-centred Dirichlet Laplacian (tables per grid side), each a
-//      parity-split pair of FP32 SIMT products of half size, in 64 x 32 or 128 x 64 tiles of
-//      half-columns (the autotuner picks one per side);
+//   2. (I - dt nu L) delta = r by fast diagonalisation at FP32 accuracy: four transforms with
+//      the sine eigenvectors of the cell-centred Dirichlet Laplacian (tables per grid side),
+//      each a parity-split pair of half-size products on the tensor cores (TF32 hi/lo split,
+//      dual_umma below), in tiles of 128 rows by up to 64 half-columns;
 //   3. optional refinement: FP64 residual r - (I - dt nu L) delta, FP32 solve, FP64 update;
 //   4. eta = base + delta in FP64, then f^N = -a u_x - b u_y and f = f^N + nu L eta (FP64).
 // FP64 work uses integer bit operations for conversions and sign flips (GB300's FP64 pipe is
