@@ -272,6 +272,7 @@ def run_ensemble(args):
     b = Batch(ws, n_refine=args.ens_refine, stream=stream.cuda_stream)
     b.set_initial(u0s)
     choice, tune_ms = b.autotune(8)
+    tiles = {str(side): b.tile_width(side) for side in sorted({w.n for w in ws})}
     cells = b.cells()
     for _ in range(args.warmup):
         b.set_initial(u0s)
@@ -350,6 +351,7 @@ def run_ensemble(args):
             "cpu_baseline": None if args.no_cpu else cpu, "clocks": clk.summary(),
             "config": {"workload": f"ensemble_{count}_dirichlet_adv_diff", "instances": count,
                        "steps": nst, "n_refine": args.ens_refine, "autotune_choice": choice,
+                       "tile_widths": tiles,
                        "launch": "one CUDA graph per advance (counter reset + persistent "
                                  "cluster launch)",
                        "cells_per_step": cells},

@@ -267,12 +267,23 @@ int ridc_batch_get_solution(ridc_batch b, int i, double* out, size_t count, int 
 long ridc_batch_cells(ridc_batch b);
 
 /* Autotuner: picks the cluster size (1, 2 or 4 CTAs cooperating on each instance) and the
- * CTAs per SM (1 to 4) that run the whole batch fastest (the tensor-core tile, 128 rows by the
- * widest multiple of 16 up to 64 that divides side/2, follows from each grid side); each trial
- * advances `nsteps` steps of the real batch. The choice is kept for later advances. Requires
- * an initial state and leaves the state undefined: call ridc_batch_set_initial afterwards.
+ * CTAs per SM (1 to 4) that run the whole batch fastest, then, at that launch shape, the
+ * tile width of each grid side's tensor-core products: tiles are 128 rows by a multiple of 16
+ * up to 64 half-columns that divides side/2 (narrow tiles give a cluster more tiles to share
+ * on small grids, wide ones reuse each staged row more). Each trial advances `nsteps` steps
+ * of the real batch. The choices are kept for later advances. Requires an initial state and
+ * leaves the state undefined: call ridc_batch_set_initial afterwards.
  * *choice = CTAs per SM * 16 + cluster size; *best_ms = the fastest whole-batch trial.     */
 int ridc_batch_autotune(ridc_batch b, long nsteps, int* choice, float* best_ms);
+
+/* Tile width (half-columns per tensor-core tile) of the products for grid side `side`, or
+ * RIDC_ERR_ARG if no instance of the batch has that side. Before any autotuning: the widest
+ * multiple of 16 up to 64 that divides side/2.                                              */
+int ridc_batch_tile_width(ridc_batch b, int side);
+
+/* Set that tile width: a multiple of 16 up to 64 that divides side/2, else RIDC_ERR_ARG.
+ * Stream-ordered after the advances already issued. Results do not depend on it.          */
+int ridc_batch_set_tile_width(ridc_batch b, int side, int width);
 
 /* Use launch shape `choice` (CTAs per SM * 16 + cluster size, as ridc_batch_autotune reports
  * it: 1 to 4 CTAs per SM, clusters of 1, 2 or 4 CTAs) for later advances, e.g. one tuned

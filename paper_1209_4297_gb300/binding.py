@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         "ridc_batch_cells": (lg, [vp]),
         "ridc_batch_autotune": (i, [vp, lg, POINTER(c_int), POINTER(ctypes.c_float)]),
         "ridc_batch_set_launch": (i, [vp, i]),
+        "ridc_batch_tile_width": (i, [vp, i]),
+        "ridc_batch_set_tile_width": (i, [vp, i, i]),
         "ridc_batch_graph_launches": (lg, [vp]),
         "ridc_batch_destroy": (None, [vp]),
         "ridc_set_allocator": (i, [ALLOC_FN, FREE_FN, vp]),
@@ -424,6 +426,16 @@ class Batch:
     def graph_launches(self) -> int:
         """CUDA graphs launched so far (one per advance or autotuner trial)."""
         return lib().ridc_batch_graph_launches(self._h)
+
+    def tile_width(self, side: int) -> int:
+        """Half-columns per tensor-core tile of the products for grid side `side`."""
+        rc = lib().ridc_batch_tile_width(self._h, side)
+        _check(min(rc, 0), "ridc_batch_tile_width")
+        return rc
+
+    def set_tile_width(self, side: int, width: int) -> None:
+        """Set that width: a multiple of 16 up to 64 that divides side/2."""
+        _check(lib().ridc_batch_set_tile_width(self._h, side, width), "ridc_batch_set_tile_width")
 
     def set_launch(self, choice: int) -> None:
         """Launch shape CTAs per SM * 16 + cluster size, as autotune() reports it."""

@@ -87,6 +87,8 @@ struct EnsClass {
   const float* Qs;   // [s][s]  Qs[x][c] = Q[x][k]: Q with its columns in split order
   const float* lam;  // [s]     eigenvalues in split order
   int s;
+  int bn;            // tile width (half-columns) of this size's products, chosen by the
+                     // autotuner: a multiple of 16 up to 64 that divides s/2
 };
 
 struct EnsArgs {
@@ -152,12 +154,16 @@ struct UmmaState {
   int* err;
 };
 
-// tile column width: the largest multiple of 16 up to 64 that divides H (H = s/2, s a
-// multiple of 32)
-__device__ __forceinline__ int um_bn(int H) {
+// default tile column width: the largest multiple of 16 up to 64 that divides H (H = s/2,
+// s a multiple of 32); narrower tiles give a cluster more tiles to share on small grids
+__host__ __device__ __forceinline__ int um_bn(int H) {
   for (int bn = UM_MAXBN; bn >= 16; bn -= 16)
     if (H % bn == 0) return bn;
   return 16;
+}
+
+static bool um_bn_valid(int s, int bn) {
+  return bn >= 16 && bn <= UM_MAXBN && bn % 16 == 0 && (s / 2) % bn == 0;
 }
 
 // v ~= hi + lo, both TF32 values in FP32 words
@@ -194,10 +200,10 @@ __device__ __forceinline__ bool um_wait(UmmaState& st) {
 
 template <bool FWD>
 __device__ void dual_umma(const float* __restrict__ A, const float* __restrict__ B,
-                          float* __restrict__ out, int s, int rows, const float* lam,
+                          float* __restrict__ out, int s, int BN, int rows, const float* lam,
                           float dtnu, bool scale, UmmaSmem& sm, UmmaState& st, int rank, int CL) {
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int H = s / 2, BN = um_bn(H);
+  const int H = s / 2;
   const int nrt = (rows + UM_BM - 1) / UM_BM, nct = H / BN;
   const int KS = (H + UM_BK - 1) / UM_BK;
   // instruction descriptor, kind::tf32: FP32 accumulator (bits 4-5 = 1), A and B TF32 (bits
@@ -361,13 +367,13 @@ template <int CL>
 __device__ void cl_solve(const EnsClass& C, const EnsInst& I, int np, const float* rf, float* t1,
                          float* t2, float* df, UmmaSmem& sm, UmmaState& st, int rank) {
   const int s = C.s, rows = np * s;
-  dual_umma<true>(rf, C.Qts, t1, s, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
+  dual_umma<true>(rf, C.Qts, t1, s, C.bn, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
   csync<CL>();
-  dual_umma<true>(t1, C.Qts, t2, s, rows, C.lam, I.dtnu, true, sm, st, rank, CL);
+  dual_umma<true>(t1, C.Qts, t2, s, C.bn, rows, C.lam, I.dtnu, true, sm, st, rank, CL);
   csync<CL>();
-  dual_umma<false>(t2, C.Qs, t1, s, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
+  dual_umma<false>(t2, C.Qs, t1, s, C.bn, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
   csync<CL>();
-  dual_umma<false>(t1, C.Qs, df, s, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
+  dual_umma<false>(t1, C.Qs, df, s, C.bn, rows, C.lam, I.dtnu, false, sm, st, rank, CL);
   csync<CL>();
 }
 
@@ -814,6 +820,7 @@ extern "C" int ridc_batch_create(int count, const ridc_problem* problems, const 
     }
     EnsClass C{};
     C.s = s;
+    C.bn = um_bn(s / 2);
     void* p;
     if ((rc = b_alloc(b, &p, Qs.size() * 4)) != RIDC_OK) return fail(rc);
     cudaMemcpy(p, Qs.data(), Qs.size() * 4, cudaMemcpyHostToDevice);
@@ -1022,10 +1029,11 @@ extern "C" long ridc_batch_cells(ridc_batch h) {
   return b ? b->cells_per_step : -1;
 }
 
-// Autotuner: the cluster size (1, 2 or 4 CTAs per instance) and the CTAs per SM (1 to 4) that
-// run the whole batch fastest (the tensor-core tile follows from each grid side). Each trial
-// advances `nsteps` top-level steps from the current state. The choice is kept for later
-// advances; *choice = CTAs per SM * 16 + cluster size.
+// Autotuner: first the cluster size (1, 2 or 4 CTAs per instance) and the CTAs per SM (1 to 4)
+// that run the whole batch fastest, then, at that launch shape, the tile width of each grid
+// side's tensor-core products (a multiple of 16 up to 64 that divides side/2) one side at a
+// time. Each trial advances `nsteps` top-level steps of the whole batch from the current state.
+// The choices are kept for later advances; *choice = CTAs per SM * 16 + cluster size.
 // The state is scrambled: call ridc_batch_set_initial afterwards.
 extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float* best_ms) {
   BatchCtx* b = bctx(h);
@@ -1063,6 +1071,25 @@ extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float
       rc = timed(cl, per_sm, b->order_dev, b->n, &ms);
       if (ms < best) { best = ms; bcl = cl; bps = per_sm; }
     }
+  // then, at that launch shape, the tile width of each grid side's products in turn
+  auto upload = [&]() {
+    return cudaMemcpyAsync(b->cls_dev, b->cls.data(), b->cls.size() * sizeof(EnsClass),
+                           cudaMemcpyHostToDevice, b->stream);
+  };
+  for (size_t c = 0; c < b->cls.size() && rc == RIDC_OK; ++c) {
+    const int s = b->cls[c].s, keep = b->cls[c].bn;
+    int best_bn = keep;
+    for (int bn = 16; bn <= UM_MAXBN && rc == RIDC_OK; bn += 16) {
+      if (bn == keep || !um_bn_valid(s, bn)) continue;
+      b->cls[c].bn = bn;
+      if (upload() != cudaSuccess) { rc = RIDC_ERR_CUDA; break; }
+      float ms = 0.f;
+      rc = timed(bcl, bps, b->order_dev, b->n, &ms);
+      if (rc == RIDC_OK && ms < best) { best = ms; best_bn = bn; }
+    }
+    b->cls[c].bn = best_bn;
+    if (upload() != cudaSuccess && rc == RIDC_OK) rc = RIDC_ERR_CUDA;
+  }
   restore();
   cudaStreamSynchronize(b->stream);
   cudaEventDestroy(e0);
@@ -1074,6 +1101,29 @@ extern "C" int ridc_batch_autotune(ridc_batch h, long nsteps, int* choice, float
   if (choice) *choice = bps * 16 + bcl;
   if (best_ms) *best_ms = best;
   return RIDC_OK;
+}
+
+extern "C" int ridc_batch_tile_width(ridc_batch h, int side) {
+  BatchCtx* b = bctx(h);
+  if (!b) return RIDC_ERR_ARG;
+  for (const EnsClass& C : b->cls)
+    if (C.s == side) return C.bn;
+  return RIDC_ERR_ARG;
+}
+
+extern "C" int ridc_batch_set_tile_width(ridc_batch h, int side, int width) {
+  BatchCtx* b = bctx(h);
+  if (!b) return RIDC_ERR_ARG;
+  DeviceGuard dg(b->device);
+  for (EnsClass& C : b->cls) {
+    if (C.s != side) continue;
+    if (!um_bn_valid(side, width)) return RIDC_ERR_ARG;
+    C.bn = width;
+    // stream-ordered after every advance already issued
+    return cuda_status(cudaMemcpyAsync(b->cls_dev, b->cls.data(), b->cls.size() * sizeof(EnsClass),
+                                       cudaMemcpyHostToDevice, b->stream));
+  }
+  return RIDC_ERR_ARG;
 }
 
 extern "C" int ridc_batch_set_launch(ridc_batch h, int choice) {

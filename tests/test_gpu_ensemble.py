@@ -122,6 +122,41 @@ def test_launch_shape_can_be_set_and_does_not_change_results():
                 b.set_launch(bad)
 
 
+def test_tile_widths_are_tunable_and_do_not_change_results():
+    """Every tile width a grid side allows (multiples of 16 up to 64 dividing side/2) gives
+    the same bits: a tile's width does not change any element's sum over K. The autotuner
+    picks one per side; widths a side does not allow are refused."""
+    ws = _mixed_set(5)
+    ref = _run_batch(ws, 5, 1)
+    widths = {64: (16, 32), 96: (16, 48), 128: (16, 32, 64), 192: (16, 32, 48), 256: (16, 32, 64)}
+    need_cuda()
+    for k in range(3):
+        with Batch(ws, n_refine=1) as b:
+            for side, ok in widths.items():
+                assert b.tile_width(side) == max(ok)      # the default: the widest
+                b.set_tile_width(side, ok[min(k, len(ok) - 1)])
+                assert b.tile_width(side) == ok[min(k, len(ok) - 1)]
+            b.set_initial([w.u0[0].copy() for w in ws])
+            b.advance(2)
+            b.advance(3)
+            for i in range(len(ws)):
+                np.testing.assert_array_equal(b.solution(i), ref[i])
+    with Batch(ws, n_refine=1) as b:
+        for side, bad in ((64, 64), (96, 32), (128, 48), (256, 80), (256, 8), (100, 16)):
+            with pytest.raises(RidcError):
+                b.set_tile_width(side, bad)
+        with pytest.raises(RidcError):
+            b.tile_width(100)
+        b.set_initial([w.u0[0].copy() for w in ws])
+        b.autotune(2)
+        for side, ok in widths.items():
+            assert b.tile_width(side) in ok
+        b.set_initial([w.u0[0].copy() for w in ws])
+        b.advance(5)
+        for i in range(len(ws)):
+            np.testing.assert_array_equal(b.solution(i), ref[i])
+
+
 def test_every_advance_is_one_cuda_graph_launch():
     ws = inputs.ensemble(6, nsteps=5)
     ref = _run_batch(ws, 5)
