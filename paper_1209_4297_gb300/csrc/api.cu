@@ -608,18 +608,19 @@ static int create_impl(Ctx* c, const ridc_problem* pr, const ridc_grid* g, const
     if (is_mixed(c->prec)) {
       const long rows = (long)order * c->S * n, H = n / 2;
       c->grows = rows;
-      RIDC_TRY(make_tensor_map(&c->tm_Xh, c->xh, 2 * rows, H, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Xl, c->xl, 2 * rows, H, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Yh, c->yh, 2 * rows, H, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Yl, c->yl, 2 * rows, H, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Wh, c->xh, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Wl, c->xl, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Zh, c->yh, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Zl, c->yl, rows, n, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Bfh, c->Bfh, n, H, gemm_sym_fwd_bn(n)));
-      RIDC_TRY(make_tensor_map(&c->tm_Bfl, c->Bfl, n, H, gemm_sym_fwd_bn(n)));
-      RIDC_TRY(make_tensor_map(&c->tm_Bbh, c->Bbh, n, H, 128));
-      RIDC_TRY(make_tensor_map(&c->tm_Bbl, c->Bbl, n, H, 128));
+      // forward operands (X, Y, forward tables) and inverse ones (W, Z, inverse tables)
+      RIDC_TRY(make_tensor_map(&c->tm_Xh, c->xh, 2 * rows, H, 128, true));
+      RIDC_TRY(make_tensor_map(&c->tm_Xl, c->xl, 2 * rows, H, 128, true));
+      RIDC_TRY(make_tensor_map(&c->tm_Yh, c->yh, 2 * rows, H, 128, true));
+      RIDC_TRY(make_tensor_map(&c->tm_Yl, c->yl, 2 * rows, H, 128, true));
+      RIDC_TRY(make_tensor_map(&c->tm_Wh, c->xh, rows, n, 128, false));
+      RIDC_TRY(make_tensor_map(&c->tm_Wl, c->xl, rows, n, 128, false));
+      RIDC_TRY(make_tensor_map(&c->tm_Zh, c->yh, rows, n, 128, false));
+      RIDC_TRY(make_tensor_map(&c->tm_Zl, c->yl, rows, n, 128, false));
+      RIDC_TRY(make_tensor_map(&c->tm_Bfh, c->Bfh, n, H, gemm_sym_fwd_bn(n), true));
+      RIDC_TRY(make_tensor_map(&c->tm_Bfl, c->Bfl, n, H, gemm_sym_fwd_bn(n), true));
+      RIDC_TRY(make_tensor_map(&c->tm_Bbh, c->Bbh, n, H, 128, false));
+      RIDC_TRY(make_tensor_map(&c->tm_Bbl, c->Bbl, n, H, 128, false));
     }
   }
   RIDC_CUDA(cudaDeviceSynchronize());

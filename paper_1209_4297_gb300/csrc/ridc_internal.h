@@ -334,7 +334,10 @@ int launch_gemm_f64(Ctx* c, const double* A, const double* B, double* out, int n
 int launch_gemm_sym(Ctx* c, const CUtensorMap* ah, const CUtensorMap* al, const CUtensorMap* bh,
                     const CUtensorMap* bl, int plane0, int nplanes, int mode, __nv_bfloat16* oh,
                     __nv_bfloat16* ol, float* o32, int pass);
-int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows);
+// fwd: operands of the forward products (32-value K slices, 64B swizzle); else 64-value
+// slices with 128B swizzle
+int make_tensor_map(CUtensorMap* tm, const void* base, long rows, long cols, int box_rows,
+                    bool fwd);
 // column-tile width of the forward parity-split products for side n (the B box height)
 int gemm_sym_fwd_bn(int n);
 int launch_1d(Ctx* c, long nsteps_pipe, int init_only);
