@@ -130,8 +130,8 @@ class ClockSampler:
 # DRAM traffic of one full (8-plane) gemm_sym launch from one ncu capture
 # (profiles/gemm_sym_gray_scott_2048_mixed.md: dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the four modes), valid only for the kernel source it was taken on.
-GEMM_TRAFFIC = {"bytes": 2.319e8,
-                "source_sha256": "e1b7af6e50ca55e1a1f441125b63638a65ecfede4af675122ed6692b059a9632"}
+GEMM_TRAFFIC = {"bytes": 2.3186e8,
+                "source_sha256": "04f824db85932070ed0507afae62ae4893e1183ec26bed1aa57c393238153959"}
 
 
 def gemm_traffic():
