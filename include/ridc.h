@@ -116,6 +116,12 @@ typedef struct {
                              batch requires RIDC_PRED_FBE).                                  */
 } ridc_problem;
 
+/* 1D solves factor I - mu (S - 2 + S^T), mu = nu dt / h^2, into two first-order recurrences
+ * run as block-wide scans. Measured against a long-double evaluation (n = 1024, one FBE step),
+ * they are as accurate as an FP64 LU solve up to mu ~ 100; beyond, their relative error
+ * grows about linearly with mu (1.8e-13 at mu = 1e4, 4.5e-10 at mu = 1e6, against 1.7e-14
+ * and 2.0e-12 for LU), within the operator's conditioning bound (1 + 4 mu) x 2^-52
+ * (tests/test_gpu_1d_stiff.py). The paper's 1D runs have mu = 0.5 to 10.                    */
 typedef struct {
     int dim;              /* 1 or 2; must match the kind                                     */
     int n;                /* unknowns per side: 1D n >= 8 with (L + 1) n256 + L n + 1 <=
