@@ -43,7 +43,8 @@ class _Solve1D:
     def _solve64(self, r: np.ndarray, dt: float) -> np.ndarray:
         # dense LU with partial pivoting of I - dt D, factored once per dt (in FP64)
         if dt not in self._lu:
-            self._lu[dt] = scipy.linalg.lu_factor(np.eye(self.n) - dt * self.matrix_D())
+            m = np.eye(self.n) - dt * self.matrix_D()   # long double for extended problems
+            self._lu[dt] = scipy.linalg.lu_factor(np.asarray(m, dtype=np.float64))
         return scipy.linalg.lu_solve(self._lu[dt], r)
 
     def solve(self, r: np.ndarray, dt: float) -> np.ndarray:
