@@ -36,7 +36,7 @@ def _run_batch(ws, nsteps, n_refine=0, splits=None, autotune=False):
         return [b.solution(i) for i in range(len(ws))]
 
 
-@pytest.mark.parametrize("n_refine,bar", [(0, 1e-6), (1, 1e-10)])
+@pytest.mark.parametrize("n_refine,bar", [(0, 1e-6), (1, 1e-10), (2, 1e-12), (4, 1e-12)])
 def test_batch_matches_oracle_per_instance(n_refine, bar):
     ws = _mixed_set(10)
     got = _run_batch(ws, 10, n_refine)
