@@ -77,23 +77,29 @@ __device__ __forceinline__ void eval_state(const OneDArgs& a, const double* e, d
   }
 }
 
-// Solve of (I - dt nu L) x = r for one level by the whole block, in place on r[0, npad).
+// Solve of (I - dt nu L) x = r for one level by the whole block, in place on r[0, npad); the
+// result is x / s with s = rho / mu (the caller applies s in the FMA that consumes x).
 // With the shift S and rho = 2mu / (1 + 2mu + sqrt(1 + 4mu)) < 1,
 // M = (mu/rho)(1 - rho S)(1 - rho S^T):
 //   z = (1 - rho S)^-1 r      : z_j = r_j + rho z_{j+1},  z_n = 0           (backward)
-//   y = (rho/mu)(1 - rho S^T)^-1 z : y_j = (rho/mu) z_j + rho y_{j-1},  y_{-1} = 0  (forward)
+//   y = (rho/mu)(1 - rho S^T)^-1 z = s y' : y'_j = z_j + rho y'_{j-1},  y'_{-1} = 0  (forward)
 // Each first-order recurrence is a scan over the block: every thread runs its chunk of
 // m = npad / blockDim values, a 5-step shuffle scan combines the chunk carries of a warp with
 // weights rho^(m 2^k), and the warps' totals are chained through shared memory. Entries
 // past n are zero on entry, so the backward scan ends with z_n = 0 and the forward scan only
 // leaves values past n, which nothing reads. Then
 //   periodic  (cyclic S, M is the matrix): exact wrap terms make both recurrences cyclic,
-//             z_j += rho^(n-j) z_0 / (1 - rho^n),  y_j += rho^(j+1) y_{n-1} / (1 - rho^n);
+//             z_j += rho^(n-j) z_0 / (1 - rho^n),  y'_j += rho^(j+1) y'_{n-1} / (1 - rho^n);
 //   Dirichlet (the matrix is M + mu rho e_{n-1} e_{n-1}^T): Sherman-Morrison,
-//             x_j = y_j - kappa y_{n-1} g_j with the tabulated g = M^-1 e_{n-1}.
+//             x'_j = y'_j - kappa y'_{n-1} g_j with the tabulated g = M^-1 e_{n-1}.
+// The solve runs on one SM's FP64 pipe, so its operations per cell set its time. A chunk's
+// carry terms share a factor: rho^(n-j) = rho^(m-i) rho^(n-j0-m) and rho^(j+1) =
+// rho^(i+1) rho^j0 for cell j = j0 + i. So each wrap term is folded into the thread's carry
+// (one FMA per thread instead of one per cell). The forward wrap needs y'_{n-1}, which the
+// thread holding it forms first, so carry and wrap are applied in one sweep.
 // Spreading the chunks over all warps uses the FP64 pipes of all four SM partitions.
 __device__ void tri_solve_block(double* r, int n, int npad, const double* rp, double corr,
-                                double s, const double* gvec, bool cyclic, double* scratch) {
+                                const double* gvec, bool cyclic, double* scratch) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NW = blockDim.x >> 5;
   const int m = npad / blockDim.x;
   const int j0 = tid * m;
@@ -123,17 +129,23 @@ __device__ void tri_solve_block(double* r, int n, int npad, const double* rp, do
   double Cnext = __shfl_down_sync(0xffffffffu, C, 1);
   if (lane == 31) Cnext = Z;
   __syncthreads();
-  const double z0 = scratch[NW] * corr;         // cyclic z_0 (periodic only)
+  // periodic wrap, folded into the carry for chunks that lie inside [0, n)
+  const bool inside = j0 + m <= n;
+  double z0 = 0.0;
+  if (cyclic) {
+    z0 = scratch[NW] * corr;
+    if (inside) Cnext = fma(rp[n - j0 - m], z0, Cnext);
+  }
   for (int i = 0; i < m; ++i) {
     const int j = j0 + i;
     double v = fma(rp[m - i], Cnext, r[j]);
-    if (cyclic && j < n) v = fma(rp[n - j], z0, v);
+    if (cyclic && !inside && j < n) v = fma(rp[n - j], z0, v);
     r[j] = v;
   }
-  // ---- forward recurrence, local part: t_j = s z_j + rho t_{j-1}, t_{j0-1} = 0
+  // ---- forward recurrence, local part: t_j = z_j + rho t_{j-1}, t_{j0-1} = 0
   t = 0.0;
   for (int i = 0; i < m; ++i) {
-    t = fma(rho, t, s * r[j0 + i]);
+    t = fma(rho, t, r[j0 + i]);
     r[j0 + i] = t;
   }
   // carries within the warp: D_l = t_{(l+1)m-1} + rho^m D_{l-1} (inclusive scan)
@@ -145,27 +157,28 @@ __device__ void tri_solve_block(double* r, int n, int npad, const double* rp, do
   }
   if (lane == 31) scratch[w] = D;
   __syncthreads();
-  // y at the last index of warp w-1: Y = D_{w-1} + rho^(32m) Y_{w-2}
+  // y' at the last index of warp w-1: Y = D_{w-1} + rho^(32m) Y_{w-2}
   double Y = 0.0;
   for (int v = 0; v < w; ++v) Y = fma(rho_w, Y, scratch[v]);
-  D = fma(rp[m * (lane + 1)], Y, D);            // full carry: y at this thread's last index
+  D = fma(rp[m * (lane + 1)], Y, D);            // full carry: y' at this thread's last index
   double Dprev = __shfl_up_sync(0xffffffffu, D, 1);
   if (lane == 0) Dprev = Y;
-  for (int i = 0; i < m; ++i) r[j0 + i] = fma(rp[i + 1], Dprev, r[j0 + i]);
+  // y'_{n-1} without its wrap or Sherman-Morrison term, from the thread that holds it
+  if (j0 <= n - 1 && n - 1 < j0 + m) scratch[NW + 1] = fma(rp[n - j0], Dprev, r[n - 1]);
   __syncthreads();
-  const double yl = r[n - 1];   // y_{n-1}, written by another thread
-  __syncthreads();
+  const double yl = scratch[NW + 1];
   if (cyclic) {
-    const double wv = yl * corr;
-    for (int i = 0; i < m; ++i) {
-      const int j = j0 + i;
-      if (j < n) r[j] = fma(rp[j + 1], wv, r[j]);
-    }
+    // y'_j += rho^(i+1) (Dprev + rho^j0 y'_{n-1} corr); cells past n get a finite value that
+    // nothing reads
+    const double Dw = fma(rp[j0], yl * corr, Dprev);
+    for (int i = 0; i < m; ++i) r[j0 + i] = fma(rp[i + 1], Dw, r[j0 + i]);
   } else {
     const double wv = -corr * yl;
     for (int i = 0; i < m; ++i) {
       const int j = j0 + i;
-      if (j < n) r[j] = fma(wv, gvec[j], r[j]);
+      double v = fma(rp[i + 1], Dprev, r[j]);
+      if (j < n) v = fma(wv, gvec[j], v);
+      r[j] = v;
     }
   }
   __syncthreads();
@@ -250,7 +263,8 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
   __shared__ long p[kMaxOrder];
   __shared__ int lev[kMaxOrder];
   __shared__ int na;
-  __shared__ double scratch[ONED_THREADS / 32 + 1];
+  __shared__ double scratch[ONED_THREADS / 32 + 2];
+  __shared__ double s_last;             // ARK predictor: s of its last stage's operator
 
   if (a.init_only) {
     if (rank == 0) eval_state(a, a.eta[0], a.fN[0], a.F[0]);
@@ -309,11 +323,14 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
           }
           __syncthreads();
           tri_solve_block(r, n, npad, rq, a.tri[S.coef * T + npad + 1],
-                          a.tri[S.coef * T + npad + 2], a.tri + S.coef * T + npad + 3, cyclic,
-                          scratch);
-          if (si == a.nstages - 1) break;
+                          a.tri + S.coef * T + npad + 3, cyclic, scratch);
+          const double ss = a.tri[S.coef * T + npad + 2];   // the solve leaves delta / s
+          if (si == a.nstages - 1) {
+            if (threadIdx.x == 0) s_last = ss;
+            break;
+          }
           // stage value Y = y_n + delta, then F and f^N of it (read back by this CTA only)
-          for (int i = threadIdx.x; i < n; i += blockDim.x) Y[i] = e[i] + r[i];
+          for (int i = threadIdx.x; i < n; i += blockDim.x) Y[i] = fma(ss, r[i], e[i]);
           __syncthreads();
           eval_state(a, Y, a.scratch + (size_t)(2 * si + 1) * n, a.scratch + (size_t)2 * si * n);
           __syncthreads();
@@ -378,11 +395,14 @@ __global__ void __launch_bounds__(ONED_THREADS) ridc1d_kernel(const __grid_const
     __syncthreads();
     for (int q = 0; q < na; ++q)
       if (!(ark && lev[q] == 0))   // an ARK predictor's last stage is solved already
-        tri_solve_block(R + (size_t)q * npad, n, npad, rp, corr, sfac, gvec, cyclic, scratch);
-    // new states: base + delta (each thread updates the entries it stored the base of)
-    for (int q = 0; q < na; ++q)
+        tri_solve_block(R + (size_t)q * npad, n, npad, rp, corr, gvec, cyclic, scratch);
+    // new states: base + s (delta / s) (each thread updates the entries it stored the base
+    // of; s_last was set before the barrier that ends the ARK stages' last solve)
+    for (int q = 0; q < na; ++q) {
+      const double sq = (ark && lev[q] == 0) ? s_last : sfac;
       for (int i = threadIdx.x; i < n; i += blockDim.x)
-        E[(size_t)q * n + i] += R[(size_t)q * npad + i];
+        E[(size_t)q * n + i] = fma(sq, R[(size_t)q * npad + i], E[(size_t)q * n + i]);
+    }
     __syncthreads();
     for (int q = 0; q < na; ++q) {
       const int j = lev[q];
